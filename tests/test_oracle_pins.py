@@ -1,0 +1,470 @@
+"""Pins of the FP64 oracle to things other than itself (runs on CPU, no GPU).
+
+Each test checks the oracle against a value the paper prints, a closed form, an invariant the
+paper states, or a textbook special case, chosen so that a dropped term, a wrong sign or index, or
+a transposed operand in the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_15654_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+CS2 = 1.0 / 3.0
+
+
+def run(params, flds, steps):
+    s = oracle.Sim(params)
+    s.init(**flds)
+    if steps:
+        s.step(steps)
+    return s
+
+
+# --------------------------------------------------------------------------------------------
+# Lattice and moment-space operators (Sec. 4 preamble; Appendix A conditions on Lambda)
+# --------------------------------------------------------------------------------------------
+
+def test_moment_matrix_is_the_printed_one():
+    """M equals the natural transformation matrix printed in Sec. 4."""
+    golden = np.loadtxt(os.path.join(GOLDEN, "natural_moment_matrix.txt"))
+    np.testing.assert_array_equal(oracle.moment_matrix(), golden)
+
+
+def test_lattice_matches_moment_rows_and_is_isotropic():
+    """Rows 2-3 of the printed M are c_x and c_y of each direction; the weights give the D2Q9
+    isotropy relations with cs2 = 1/3 (Sec. 4: cs2 = c^2/3)."""
+    cx, cy, w = oracle.lattice()
+    M = np.loadtxt(os.path.join(GOLDEN, "natural_moment_matrix.txt"))
+    np.testing.assert_array_equal(cx, M[1])
+    np.testing.assert_array_equal(cy, M[2])
+    c = np.stack([cx, cy]).astype(float)
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    np.testing.assert_allclose(np.einsum("i,ai->a", w, c), 0.0, atol=1e-15)
+    np.testing.assert_allclose(np.einsum("i,ai,bi->ab", w, c, c), CS2 * np.eye(2), atol=1e-15)
+    d = np.eye(2)
+    iso4 = CS2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                       + np.einsum("ad,bc->abcd", d, d))
+    np.testing.assert_allclose(np.einsum("i,ai,bi,ci,di->abcd", w, c, c, c, c), iso4, atol=1e-15)
+    # K = w0 / (c^2 - cs2) = 2/3 for D2Q9 (Sec. 4)
+    assert w[0] / (1.0 - CS2) == pytest.approx(2.0 / 3.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("s5", [(1.0, 1.0, 1.0, 1.0, 1.0), (0.7, 1.3, 0.9, 1.1, 1.6)])
+def test_collision_operator_conditions(s5):
+    """Appendix A: sum_i e_i Lambda_ij = s0 e_j and sum_i c_i Lambda_ij = s1 c_j; every moment
+    row of M is an eigenvector of Lambda with its rate, and the source operator carries 1 - s/2."""
+    lam, src = oracle.operators(s5)
+    M = oracle.moment_matrix()
+    cx, cy, _ = oracle.lattice()
+    np.testing.assert_allclose(lam.sum(axis=0), s5[0] * np.ones(9), atol=1e-14)
+    np.testing.assert_allclose(cx @ lam, s5[1] * cx, atol=1e-14)
+    np.testing.assert_allclose(cy @ lam, s5[1] * cy, atol=1e-14)
+    sdiag = np.array([s5[0], s5[1], s5[1], s5[2], s5[2], s5[2], s5[3], s5[3], s5[4]])
+    np.testing.assert_allclose(M @ lam, sdiag[:, None] * M, atol=1e-13)
+    np.testing.assert_allclose(M @ src, (1 - sdiag / 2)[:, None] * M, atol=1e-13)
+
+
+# --------------------------------------------------------------------------------------------
+# Equilibria and sources: moment conditions (Appendix A for g; same structure for f; Sec. 3.3)
+# --------------------------------------------------------------------------------------------
+
+def _random_cell(rng):
+    return dict(phi=rng.uniform(0.05, 0.95), psi=rng.uniform(0.0, 0.6), ux=rng.uniform(-0.05, 0.05),
+                uy=rng.uniform(-0.05, 0.05), P=rng.uniform(-1e-3, 1e-3), rho=rng.uniform(0.5, 2.0),
+                nx=math.cos(a := rng.uniform(0, 2 * math.pi)), ny=math.sin(a),
+                Fx=rng.uniform(-1e-4, 1e-4), Fy=rng.uniform(-1e-4, 1e-4),
+                Sx=rng.uniform(-1e-3, 1e-3), Sy=rng.uniform(-1e-3, 1e-3),
+                drho_x=rng.uniform(-0.1, 0.1), drho_y=rng.uniform(-0.1, 0.1),
+                dt_phiux=rng.uniform(-1e-4, 1e-4), dt_phiuy=rng.uniform(-1e-4, 1e-4),
+                dt_psiux=rng.uniform(-1e-4, 1e-4), dt_psiuy=rng.uniform(-1e-4, 1e-4),
+                dt_m2_xx=rng.uniform(-1e-5, 1e-5), dt_m2_xy=rng.uniform(-1e-5, 1e-5),
+                dt_m2_yy=rng.uniform(-1e-5, 1e-5))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("phiA,phiB,W_", [(1.0, 0.0, 4.0), (1.0, -1.0, 5.0)])
+def test_phase_and_surfactant_moment_conditions(seed, phiA, phiB, W_):
+    """Appendix A conditions for g (and the analogous ones for f):
+    sum g_eq = psi, sum c g_eq = psi u, sum c c g_eq = psi cs2 I, sum G = 0,
+    sum c G = d_t(psi u) + cs2 * 4 psi (phiA + phiB - 2 phi) / (W dphi) n
+    (the main-text G_i of Sec. 3.2 gives the factor cs2; the appendix's extra 1/D is read as a typo)."""
+    rng = np.random.default_rng(seed)
+    cell = _random_cell(rng)
+    p = W.base_params(8, 8, phiA=phiA, phiB=phiB, W=W_)
+    cell["phi"] = phiB + (phiA - phiB) * rng.uniform(0.05, 0.95)
+    d = oracle.cell_distributions(p, **cell)
+    cx, cy, _ = oracle.lattice()
+    c = np.stack([cx, cy]).astype(float)
+    u = np.array([cell["ux"], cell["uy"]])
+    n = np.array([cell["nx"], cell["ny"]])
+    dphi = phiA - phiB
+    A = 4 * (phiA - cell["phi"]) * (cell["phi"] - phiB) / (W_ * dphi)
+    B = 4 * cell["psi"] * (phiA + phiB - 2 * cell["phi"]) / (W_ * dphi)
+    for eq, src, rho_like, dtv, coef in (
+            (d["geq"], d["G"], cell["psi"], (cell["dt_psiux"], cell["dt_psiuy"]), B),
+            (d["feq"], d["F"], cell["phi"], (cell["dt_phiux"], cell["dt_phiuy"]), A)):
+        assert eq.sum() == pytest.approx(rho_like, abs=1e-15)
+        np.testing.assert_allclose(c @ eq, rho_like * u, atol=1e-15)
+        np.testing.assert_allclose(np.einsum("ai,bi,i->ab", c, c, eq), rho_like * CS2 * np.eye(2), atol=1e-15)
+        assert abs(src.sum()) < 1e-17
+        np.testing.assert_allclose(c @ src, np.array(dtv) + CS2 * coef * n, atol=1e-17)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_flow_moment_conditions(seed):
+    """Moments of h_eq and H (Sec. 3.3) by isotropy: sum h_eq = rho0, sum c h_eq = rho u,
+    sum c c h_eq = P I + sym((rho u - S) u); sum H = u.grad rho, sum c H = F,
+    sum c c H = cs2 (u.grad rho) I + sym(m2H)."""
+    rng = np.random.default_rng(seed)
+    cell = _random_cell(rng)
+    p = W.base_params(8, 8, rho0=1.3)
+    d = oracle.cell_distributions(p, **cell)
+    cx, cy, _ = oracle.lattice()
+    c = np.stack([cx, cy]).astype(float)
+    rho, P = cell["rho"], cell["P"]
+    u = np.array([cell["ux"], cell["uy"]])
+    S = np.array([cell["Sx"], cell["Sy"]])
+    gr = np.array([cell["drho_x"], cell["drho_y"]])
+    F = np.array([cell["Fx"], cell["Fy"]])
+    Q = np.outer(rho * u - S, u)
+    dt2 = np.array([[cell["dt_m2_xx"], cell["dt_m2_xy"]], [cell["dt_m2_xy"], cell["dt_m2_yy"]]])
+    m2H = dt2 + CS2 * (np.outer(u, gr) + np.outer(gr, u))
+    assert d["heq"].sum() == pytest.approx(1.3, abs=1e-14)
+    np.testing.assert_allclose(c @ d["heq"], rho * u, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("ai,bi,i->ab", c, c, d["heq"]), P * np.eye(2) + 0.5 * (Q + Q.T), atol=1e-16)
+    assert d["H"].sum() == pytest.approx(u @ gr, abs=1e-16)
+    np.testing.assert_allclose(c @ d["H"], F, atol=1e-17)
+    np.testing.assert_allclose(np.einsum("ai,bi,i->ab", c, c, d["H"]),
+                               CS2 * (u @ gr) * np.eye(2) + 0.5 * (m2H + m2H.T), atol=1e-16)
+
+
+def test_velocity_and_pressure_recovery_from_equilibrium():
+    """With h = h_eq(P, u) and no force, the velocity and pressure equations of Sec. 3.3 return the
+    u and P the populations were built from (the coefficients of the pressure equation, including
+    K = w0/(c^2 - cs2), must cancel the equilibrium's second-order term exactly)."""
+    rng = np.random.default_rng(7)
+    nx, ny = 9, 7
+    p = W.base_params(nx, ny, sigma0=0.0)
+    phi = rng.uniform(0.0, 1.0, (ny, nx))
+    ux = rng.uniform(-0.05, 0.05, (ny, nx))
+    uy = rng.uniform(-0.05, 0.05, (ny, nx))
+    P = rng.uniform(-1e-3, 1e-3, (ny, nx))
+    s = run(p, W.fields(phi, 0.1, ux=ux, uy=uy, P=P), 0)
+    m = s.moments()
+    np.testing.assert_allclose(m["ux"], ux, atol=1e-16)
+    np.testing.assert_allclose(m["uy"], uy, atol=1e-16)
+    np.testing.assert_allclose(m["P"], P, atol=1e-16)
+    np.testing.assert_allclose(m["phi"], phi, atol=1e-15)
+
+
+# --------------------------------------------------------------------------------------------
+# Stencils and the surface-tension force (Sec. 2.3)
+# --------------------------------------------------------------------------------------------
+
+def test_stencils_exact_on_quadratics():
+    """The isotropic gradient and Laplacian stencils are exact for quadratic fields (interior)."""
+    nx, ny = 16, 12
+    x, y = W.grid(nx, ny)
+    phi = 0.3 + 0.01 * x - 0.02 * y + 0.0007 * x * x + 0.0011 * x * y - 0.0005 * y * y
+    psi = 0.2 - 0.003 * x + 0.004 * y + 0.0002 * x * y
+    s = run(W.base_params(nx, ny, sigma0=0.0), W.fields(phi, psi), 0)
+    f = s.fields()
+    sl = (slice(1, ny - 1), slice(1, nx - 1))
+    np.testing.assert_allclose(f["gpx"][sl], (0.01 + 0.0014 * x + 0.0011 * y)[sl], atol=1e-14)
+    np.testing.assert_allclose(f["gpy"][sl], (-0.02 + 0.0011 * x - 0.001 * y)[sl], atol=1e-14)
+    np.testing.assert_allclose(f["lap"][sl], 2 * 0.0007 - 2 * 0.0005, atol=1e-14)
+    np.testing.assert_allclose(f["gsx"][sl], (-0.003 + 0.0002 * y)[sl], atol=1e-14)
+    np.testing.assert_allclose(f["gsy"][sl], (0.004 + 0.0002 * x)[sl], atol=1e-14)
+
+
+@pytest.mark.parametrize("phiA,phiB", [(1.0, 0.0), (2.0, 0.0)])
+def test_marangoni_force_integrates_to_surface_tension_gradient(phiA, phiB):
+    """Across a flat interface along x, the Marangoni term of F_s (Sec. 2.3) is tangential and its
+    integral over the interface normal equals the tension gradient:  int F_M,x dy =
+    (3W/2 dphi^2) int phi_y^2 d_x sigma dy.  With psi = psi0(x) sech^2 and the linear EOS this is
+    0.8 d_x sigma at the interface centre (int sech^6 / int sech^4 = 4/5)."""
+    nx, ny, Wd, sig0, E0 = 64, 64, 8.0, 1e-3, 0.5
+    p = W.base_params(nx, ny, W=Wd, sigma0=sig0, E0=E0, phiA=phiA, phiB=phiB)
+    x, y = W.grid(nx, ny)
+    band = 0.5 * (np.tanh(2 * (y - 16) / Wd) - np.tanh(2 * (y - 48) / Wd))
+    phi = phiB + (phiA - phiB) * band
+    psi0x = 0.3 + 0.1 * np.cos(2 * np.pi * x / nx)
+    psi = psi0x * W.interface_weight(band)
+    f = run(p, W.fields(phi, psi), 0).fields()
+    lower = y < 32
+    integral = (f["Fmx"] * lower).sum(axis=0)
+    dsig = sig0 * E0 * 0.1 * 2 * np.pi / nx * np.sin(2 * np.pi * x[0] / nx)
+    k = [4, 9, 13, 20, 41, 50]
+    np.testing.assert_allclose(integral[k], 0.8 * dsig[k], rtol=0.05)
+    assert np.abs(f["Fmy"]).max() < 1e-18
+
+
+# --------------------------------------------------------------------------------------------
+# Whole-step invariants and special cases
+# --------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_conservation_of_phi_and_psi(walls):
+    """Sum phi and sum psi are conserved: sum F = sum G = 0 and sum f_eq = phi, sum g_eq = psi
+    (Secs. 3.1-3.2), streaming and bounce-back move populations without loss."""
+    if walls:
+        p, f = W.shear_drop(96, 48, R=12)
+        f = W.perturbed(p, f, seed=3)
+    else:
+        p, f = W.stationary_drop(64, 48, R=14)
+        f = W.perturbed(p, f, seed=4)
+    s = run(p, f, 0)
+    t_phi, t_psi = s.total("phi"), s.total("psi")
+    s.step(600)
+    assert s.status == 0
+    assert abs(s.total("phi") - t_phi) <= 1e-12 * abs(t_phi)
+    assert abs(s.total("psi") - t_psi) <= 1e-12 * abs(t_psi)
+
+
+def test_rest_state_is_exact():
+    """With sigma0 = 0 and no body force a drop at rest stays at rest to round-off: F = 0, the time
+    derivatives vanish and h stays at its equilibrium."""
+    p, f = W.stationary_drop(48, 48, R=12, sigma0=0.0)
+    s = run(p, f, 500)
+    m = s.moments()
+    assert np.abs(m["ux"]).max() < 1e-15 and np.abs(m["uy"]).max() < 1e-15
+    assert np.abs(m["P"]).max() < 1e-15
+
+
+def test_centred_drop_symmetry():
+    """A drop centred in a periodic square box keeps the symmetries of the square: reflections in
+    x and y and the x <-> y exchange (catches swapped or mis-signed velocity components)."""
+    p, f = W.stationary_drop(40, 40, R=11, sigma0=2e-3)
+    x, y = W.grid(40, 40)
+    f["psi"] = f["psi"] * (1.0 + 0.5 * np.cos(2 * np.pi * (x - 19.5) / 40) * np.cos(2 * np.pi * (y - 19.5) / 40))
+    s = run(p, f, 300)
+    m = s.moments()
+    np.testing.assert_allclose(m["phi"], m["phi"][:, ::-1], atol=1e-13)
+    np.testing.assert_allclose(m["phi"], m["phi"][::-1, :], atol=1e-13)
+    np.testing.assert_allclose(m["phi"], m["phi"].T, atol=1e-13)
+    np.testing.assert_allclose(m["ux"], -m["ux"][:, ::-1], atol=1e-15)
+    np.testing.assert_allclose(m["uy"], -m["uy"][::-1, :], atol=1e-15)
+    np.testing.assert_allclose(m["ux"], m["uy"].T, atol=1e-15)
+    assert np.abs(m["ux"]).max() > 1e-9  # the check above is not vacuous
+
+
+def test_planar_interface_and_surfactant_profiles_are_stationary():
+    """The tanh profile (Eq. for phi_eq) and psi_eq = psi0 sech^2 (Eq. for psi_eq) are the steady
+    states of the phase-field and surfactant equations; the discrete solution stays close to them
+    and no surfactant leaks into the bulk (Sec. 2.2)."""
+    nx, ny, Wd = 4, 64, 4.0
+    p = W.base_params(nx, ny, W=Wd, sigma0=1e-3, E0=0.5, D=0.05)
+    _, y = W.grid(nx, ny)
+    phi = 0.5 * (np.tanh(2 * (y - 15.5) / Wd) - np.tanh(2 * (y - 47.5) / Wd))
+    psi = 0.3 * W.interface_weight(phi)
+    m = run(p, W.fields(phi, psi), 4000).moments()
+    assert np.abs(m["phi"] - phi).max() < 1e-2
+    assert np.abs(m["psi"] - psi).max() < 0.05 * 0.3
+    far = (np.abs(y - 15.5) > 12) & (np.abs(y - 47.5) > 12)
+    assert m["psi"][far].max() < 1e-4 * 0.3
+
+
+def test_uniform_surfactant_is_swept_to_the_interface():
+    """The sharpening flux of the surfactant equation (Sec. 2.2) drives bulk surfactant onto the
+    interface: starting from a uniform psi the bulk empties while the total is conserved."""
+    nx, ny, Wd = 4, 64, 4.0
+    p = W.base_params(nx, ny, W=Wd, sigma0=0.0, D=0.05)
+    _, y = W.grid(nx, ny)
+    phi = 0.5 * (np.tanh(2 * (y - 15.5) / Wd) - np.tanh(2 * (y - 47.5) / Wd))
+    s = run(p, W.fields(phi, 0.1), 0)
+    tot = s.total("psi")
+    s.step(4000)
+    m = s.moments()
+    far = (np.abs(y - 15.5) > 12) & (np.abs(y - 47.5) > 12)
+    assert m["psi"][far].max() < 1e-3 * 0.1
+    assert m["psi"].max() > 0.5
+    assert abs(s.total("psi") - tot) < 1e-12 * tot
+
+
+def test_surface_diffusion_mode_decay():
+    """Sec. 4.1: a cos(theta) surfactant mode on a circle of radius R decays as exp(-D t / R^2).
+    The projected amplitude a(t) = sum psi cos(theta) / sum 4 phi (1 - phi) cos^2(theta) follows
+    the analytic rate within 3 % at R = 16 (the diffuse band shifts 1/R^2 by about 1 %)."""
+    R, n, D, steps = 16.0, 64, 0.05, 2000
+    p, f = W.surface_diffusion(n=n, R=R, D=D)
+    th = W.polar_angle(n, n)
+    s = run(p, f, 0)
+
+    def amp(m):
+        wgt = W.interface_weight(m["phi"])
+        return (m["psi"] * np.cos(th)).sum() / (wgt * np.cos(th) ** 2).sum()
+
+    a0 = amp(s.moments())
+    s.step(steps)
+    rate = -math.log(amp(s.moments()) / a0) / steps
+    assert rate == pytest.approx(D / R ** 2, rel=0.03)
+
+
+def test_convection_diffusion_mode_without_interface():
+    """With phi uniform there is no interface (grad phi = 0, n = 0) and the surfactant equation is
+    the plain convection-diffusion equation: a sine mode carried by a uniform flow u0 decays as
+    exp(-D k^2 t) and its phase moves by k u0 t."""
+    nx, ny, k_, u0, D, steps = 64, 4, 2 * np.pi / 64, 0.05, 0.05, 1000
+    p = W.base_params(nx, ny, sigma0=0.0, D=D)
+    x, _ = W.grid(nx, ny)
+    s = run(p, W.fields(np.zeros((ny, nx)), 0.2 + 0.1 * np.sin(k_ * x), ux=u0), steps)
+    m = s.moments()
+    c = ((m["psi"][0] - 0.2) * np.exp(-1j * k_ * x[0])).sum() * 2 / nx
+    assert abs(c) / 0.1 == pytest.approx(math.exp(-D * k_ * k_ * steps), rel=2e-3)
+    phase = np.angle(c)
+    expect = -np.pi / 2 - k_ * u0 * steps
+    assert abs(np.angle(np.exp(1j * (phase - expect)))) < 5e-3
+    np.testing.assert_allclose(m["ux"], u0, atol=1e-15)
+
+
+def test_laplace_pressure_jump():
+    """Pressure jump of a drop = effective tension / R.  For psi = psi0 sech^2 across the interface
+    and the linear EOS the capillary force of Sec. 2.3 weights sigma(psi) with sech^4, giving
+    sigma_eff = sigma0 (1 - 0.8 E0 psi0); the clean interface gives sigma0 / R."""
+    R, n = 16.0, 64
+    x, y = W.grid(n, n)
+    r = np.hypot(x - n / 2 + 0.5, y - n / 2 + 0.5)
+    for E0 in (0.5, 0.0):
+        p, f = W.stationary_drop(n, n, R=R, E0=E0)
+        m = run(p, f, 3000).moments()
+        dP = m["P"][r < R - 12].mean() - m["P"][r > R + 12].mean()
+        assert dP == pytest.approx(1e-3 * (1 - 0.8 * E0 * 0.3) / R, rel=0.02)
+
+
+def test_couette_flow_is_exact_with_moving_walls():
+    """Plane Couette flow between half-way bounce-back walls moving at +/-U is a steady state of
+    the flow model to round-off (Sec. 4: half-way bounce-back for velocity boundaries)."""
+    nx, ny, U = 4, 16, 0.02
+    p = W.base_params(nx, ny, walls=True, u_top=U, u_bot=-U, sigma0=0.0, muA=0.5, muB=0.5)
+    _, y = W.grid(nx, ny)
+    lin = -U + 2 * U * (y + 0.5) / ny
+    m = run(p, W.fields(np.zeros((ny, nx)), 0.0, ux=lin), 3000).moments()
+    np.testing.assert_allclose(m["ux"], lin, atol=1e-15)
+    assert np.abs(m["uy"]).max() < 1e-15
+
+
+def test_couette_develops_from_rest():
+    """Walls set impulsively into motion drive the fluid to the linear profile (wall term sign)."""
+    nx, ny, U = 4, 16, 0.02
+    p = W.base_params(nx, ny, walls=True, u_top=U, u_bot=-U, sigma0=0.0, muA=0.5, muB=0.5)
+    _, y = W.grid(nx, ny)
+    m = run(p, W.fields(np.zeros((ny, nx)), 0.0), 6000).moments()
+    np.testing.assert_allclose(m["ux"], -U + 2 * U * (y + 0.5) / ny, atol=1e-9)
+
+
+def test_shear_wave_viscous_decay():
+    """A shear wave u_x = U sin(k y) decays as exp(-nu k^2 t) with nu = mu / rho fixed by s2^h
+    (Sec. 3.3: 1/s2^h = mu/(rho cs2 dt) + 1/2)."""
+    nx, ny, mu, U, steps = 4, 64, 0.1, 1e-3, 2000
+    p = W.base_params(nx, ny, sigma0=0.0, muA=mu, muB=mu)
+    _, y = W.grid(nx, ny)
+    k_ = 2 * np.pi / ny
+    m = run(p, W.fields(np.zeros((ny, nx)), 0.0, ux=U * np.sin(k_ * y)), steps).moments()
+    a = (m["ux"][:, 0] * np.sin(k_ * y[:, 0])).sum() * 2 / ny
+    assert a / U == pytest.approx(math.exp(-mu * k_ * k_ * steps), rel=2e-3)
+
+
+def test_body_force_poiseuille_profile():
+    """A body force between walls at rest gives the parabolic Poiseuille profile
+    u(y) = g (y + 1/2)(H - 1/2 - y) / (2 nu) (force enters u as F/2 and H_i as c_i.F/cs2)."""
+    nx, ny, mu, g = 4, 16, 0.1, 1e-6
+    p = W.base_params(nx, ny, walls=True, sigma0=0.0, muA=mu, muB=mu, gx=g)
+    _, y = W.grid(nx, ny)
+    m = run(p, W.fields(np.zeros((ny, nx)), 0.0), 20000).moments()
+    yy = y[:, 0]
+    exact = g / (2 * mu) * (yy + 0.5) * (ny - 0.5 - yy)
+    np.testing.assert_allclose(m["ux"][:, 0], exact, rtol=0, atol=5e-3 * exact.max())
+
+
+def test_langmuir_flags_surfactant_at_or_above_one():
+    """ln(1 - psi) in the Langmuir EOS is undefined for psi >= 1: the step reports it."""
+    p, f = W.stationary_drop(24, 24, R=6, eos="langmuir")
+    f["psi"] = f["psi"] * 0 + 1.2 * W.interface_weight(f["phi"])
+    s = run(p, f, 2)
+    assert s.status != 0
+
+
+def test_uniform_acceleration_velocity_and_pressure_closed_form():
+    """Homogeneous flow under a uniform body force g in a periodic box (streaming is then the
+    identity).  The first moment after collision is rho u + F/2 for any s1, so u(t) = g (t + 1/2).
+    Summing the zeroth to fourth moments of the collision with s4 = s2 and the pressure equation of
+    Sec. 3.3 (with K = 2/3 and d_t by backward difference) gives P(t+1) - P(t) =
+    (D(t) - D(t+1)) / 5 with D = d_t(rho |u|^2), so from rest P(N) = -rho g^2 (2N/5 + 1/10)."""
+    g = 1e-4
+    p = W.base_params(4, 4, sigma0=0.0, gx=g)
+    s = run(p, W.fields(np.zeros((4, 4)), 0.0), 0)
+    for N in (1, 7, 60):
+        s.step(N - s.steps)
+        m = s.moments()
+        np.testing.assert_allclose(m["ux"], g * (N + 0.5), rtol=1e-13)
+        np.testing.assert_allclose(m["P"], -g * g * (0.4 * N + 0.1), rtol=1e-9)
+        assert np.abs(m["uy"]).max() == 0.0
+
+
+def test_wall_channel_equals_mirrored_periodic_domain():
+    """For fields that do not vary along the walls and walls at rest, half-way bounce-back acts as
+    a mirror: a channel of height H equals the periodic domain of height 2H holding the mirrored
+    data.  This pins the bounce-back of f, g, h and the wall rule of the stencils (the cell beyond
+    the wall takes the value of the adjacent fluid cell)."""
+    nx, ny, Wd = 4, 24, 4.0
+    kw = dict(W=Wd, sigma0=1e-3, E0=0.5, D=0.05)
+    _, y = W.grid(nx, ny)
+    phi = 0.5 * (1 - np.tanh(2 * (y - 6.3) / Wd))
+    psi = 0.3 * W.interface_weight(phi) * (1 + 0.1 * np.cos(y))
+    m = run(W.base_params(nx, ny, walls=True, **kw), W.fields(phi, psi), 500).moments()
+    m2 = run(W.base_params(nx, 2 * ny, **kw),
+             W.fields(np.concatenate([phi[::-1], phi]), np.concatenate([psi[::-1], psi])), 500).moments()
+    for k in ("phi", "psi", "ux", "uy", "P"):
+        np.testing.assert_allclose(m[k], m2[k][ny:], atol=1e-14)
+    assert np.abs(m["uy"]).max() > 1e-8  # the flow part of the comparison is not vacuous
+
+
+def test_capillary_force_vanishes_on_equilibrium_interface():
+    """The capillary term of Sec. 2.3 is the chemical potential times grad phi; the chemical
+    potential (16/W)(phiA-phi)(phi-phiB)(phiA+phiB-2phi) - W lap phi is zero on the tanh profile,
+    so on a flat equilibrium interface only the discretisation residual remains."""
+    nx, ny, Wd, sig0 = 4, 64, 8.0, 1e-3
+    p = W.base_params(nx, ny, W=Wd, sigma0=sig0, E0=0.0)
+    _, y = W.grid(nx, ny)
+    phi = 0.5 * (np.tanh(2 * (y - 16) / Wd) - np.tanh(2 * (y - 48) / Wd))
+    f = run(p, W.fields(phi, 0.0), 0).fields()
+    assert np.abs(f["Fy"]).max() < 0.1 * sig0 / Wd ** 2
+    assert np.abs(f["Fx"]).max() == 0.0
+
+
+def _sech(s):
+    return 1.0 / np.cosh(s)
+
+
+def test_langmuir_marangoni_and_laplace():
+    """Langmuir EOS (Sec. 2.3): sigma = sigma0 [1 + E0 ln(1 - psi)], d sigma/d psi =
+    -sigma0 E0 / (1 - psi).  (a) The Marangoni integral across a flat interface equals
+    (3/4) int sech^4 d_x sigma ds, evaluated by quadrature of the continuum profile.  (b) The
+    Laplace jump of a drop is sigma_eff / R with sigma_eff = (3/4) int sigma(psi0 sech^2) sech^4 ds."""
+    from scipy.integrate import quad
+    nx, ny, Wd, sig0, E0 = 64, 64, 8.0, 1e-3, 0.4
+    p = W.base_params(nx, ny, W=Wd, sigma0=sig0, E0=E0, eos="langmuir")
+    x, y = W.grid(nx, ny)
+    band = 0.5 * (np.tanh(2 * (y - 16) / Wd) - np.tanh(2 * (y - 48) / Wd))
+    a0, a1 = 0.5, 0.2
+    psi0x = a0 + a1 * np.cos(2 * np.pi * x / nx)
+    f = run(p, W.fields(band, psi0x * W.interface_weight(band)), 0).fields()
+    integral = (f["Fmx"] * (y < 32)).sum(axis=0)
+    for k in (5, 13, 22, 47):
+        q0 = a0 + a1 * math.cos(2 * math.pi * k / nx)
+        dq = -a1 * 2 * math.pi / nx * math.sin(2 * math.pi * k / nx)
+        wgt = quad(lambda s: 0.75 * _sech(s) ** 6 / (1 - q0 * _sech(s) ** 2), -20, 20)[0]
+        assert integral[k] == pytest.approx(-sig0 * E0 * dq * wgt, rel=0.05)
+    # (b) Laplace with Langmuir
+    R, n, psi0 = 16.0, 64, 0.3
+    p, flds = W.stationary_drop(n, n, R=R, E0=0.2, psi0=psi0, eos="langmuir")
+    m = run(p, flds, 3000).moments()
+    r = np.hypot(x - n / 2 + 0.5, y - n / 2 + 0.5)
+    dP = m["P"][r < R - 12].mean() - m["P"][r > R + 12].mean()
+    seff = quad(lambda s: 0.75 * 1e-3 * (1 + 0.2 * math.log(1 - psi0 * _sech(s) ** 2)) * _sech(s) ** 4, -20, 20)[0]
+    assert dP == pytest.approx(seff / R, rel=0.02)
