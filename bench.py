@@ -1,0 +1,299 @@
+"""Throughput of the fused three-population lattice-Boltzmann step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: the sheared drop on a 2048 x 1024 grid (walls at +/-0.01, R = 160, Re = 1, Ca = 0.2,
+Langmuir EOS E0 = 0.2, psi0 = 0.3), populations stored in FP32, synthetic seeded fields.  A step is
+one lbm_step(1): one launch of the fused collide-stream kernel over the whole grid.  The metric is
+MLUPS (million lattice updates per second; one update advances f, g and h of one cell).  The
+populations (436 MB) exceed the 129 MB L2, so no flush is needed between steps.
+
+Printed (one JSON line on rank 0): the device-timed throughput, the end-to-end throughput through
+the C ABI with host buffers, the roofline of the step kernel against the measured HBM bandwidth,
+the FP64 CPU oracle on the host cores as a baseline, and the SM clocks sampled during the run.
+With --gpus N > 1 (under torchrun) every rank runs its own replica; the value is the sum of the
+lattice updates of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY = 2048, 1024
+BYTES_PER_LUP = 26 * 4 * 2 + 2 * 4 * 2  # 26 live float populations and 2 history floats, read + written
+METRIC = "MLUPS (3 lattices) and % HBM roofline, FP32 vs half-store; serving p50/p99"
+WORKLOAD = "sheared drop 2048x1024 (R=160, Re=1, Ca=0.2, Langmuir E0=0.2, psi0=0.3), FP32 storage"
+PROFILE = os.path.join(ROOT, "profiles", "step_kernel_2048x1024_fp32.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_2408_15654_gb300", "csrc", "lbm_kernels.cuh")
+
+
+def kernel_hash() -> str:
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    try:
+        with open(PROFILE) as f:
+            prof = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if prof.get("kernel_hash") != kernel_hash():
+        return None
+    return prof.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    QUERY = ("index,utilization.gpu,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append(dict(util=float(parts[1]), sm=float(parts[2]), smmax=float(parts[3]),
+                                 hw=parts[6], hwt=parts[7], swt=parts[8], pcap=parts[9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        loaded = [r for r in rows if r["util"] >= 50] or rows
+        reasons = set()
+        for r in loaded:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                            ("pcap", "sw_power_cap")):
+                if r[k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in loaded), "sm_max_mhz": max(r["smmax"] for r in loaded),
+                "reasons": sorted(reasons), "samples": len(loaded)}
+
+
+def dist_setup(n_gpus: int):
+    import torch
+    rank, world, local = 0, 1, 0
+    if n_gpus > 1 or "WORLD_SIZE" in os.environ:
+        import torch.distributed as dist
+        rank = int(os.environ.get("RANK", 0))
+        world = int(os.environ.get("WORLD_SIZE", 1))
+        local = int(os.environ.get("LOCAL_RANK", 0))
+        if world > 1:
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier_max(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The FP64 oracle on the host cores, on a bounded sample of the same workload: whole steps of
+    the 2048 x 1024 grid until about budget_s seconds of CPU time have been spent."""
+    import oracle
+    from paper_2408_15654_gb300 import workloads as W
+    p, f = W.shear_drop_large(NX, NY)
+    cores = oracle.set_threads(0)
+    s = oracle.Sim(p)
+    s.init(**f)
+    t0 = time.perf_counter()
+    s.step(1)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(200, int(budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    s.step(n)
+    dt = time.perf_counter() - t0
+    s.close()
+    return {"value": NX * NY * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{n} FP64 oracle steps of the 2048x1024 sheared drop after 1 untimed step, "
+                      f"OpenMP over rows ({cores} threads)"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle as it stands on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2408_15654_gb300 import workloads as W
+    p, f = W.shear_drop_large(NX, NY)
+    cores = oracle.set_threads(0)
+    s = oracle.Sim(p)
+    s.init(**f)
+    t0 = time.perf_counter()
+    s.step(min(args.warmup, 1) or 1)
+    t_step = time.perf_counter() - t0
+    budget = 90.0
+    k = max(1, min(args.steps, int(budget / max(t_step, 1e-6))))
+    t0 = time.perf_counter()
+    s.step(k)
+    dt = time.perf_counter() - t0
+    value = NX * NY * k / dt / 1e6
+    sample = (f"{k} of the {args.steps} requested FP64 oracle steps of the 2048x1024 sheared drop "
+              f"(bounded to ~{budget:.0f} s), {cores} OpenMP threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": k, "warmup": 1, "ms_per_step": dt / k * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [NX, NY], "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2408_15654_gb300 import lbm
+    from paper_2408_15654_gb300 import workloads as W
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    lbm.load()
+    p, f = W.shear_drop_large(NX, NY)
+    stream = torch.cuda.current_stream()
+    sim = lbm.Lattice(p, stream=stream)
+    sim.init(**f)
+    cells = NX * NY
+
+    # warm-up
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # device-timed region: exactly K steps, inputs already resident in HBM
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    start.record(stream)
+    sim.step(args.steps)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    ms = start.elapsed_time(stop)
+    ms_max = barrier_max(ms, world)
+    st = sim.status
+    if st != lbm.LBM_OK:
+        raise RuntimeError(f"unstable state during the benchmark: {lbm.lbm_last_error()}")
+    value = cells * args.steps * world / (ms_max * 1e-3) / 1e6
+
+    # roofline of the step kernel (one launch per step, so launch duration = step time)
+    peak, peak_kind = measured_peak()
+    launch_s = ms / args.steps * 1e-3
+    achieved = cells * BYTES_PER_LUP / launch_s / 1e9
+    traffic = profiled_traffic()
+
+    # end to end through the C ABI with pinned host buffers: upload the fields, K steps, read back
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for k, v in f.items()}
+    host_out = [torch.empty((NY, NX), dtype=torch.float64).pin_memory().numpy() for _ in range(5)]
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    lbm.lbm_init_fields(sim.handle, *[host_in[k] for k in lbm.FIELDS], mem=lbm.LBM_MEM_HOST)
+    sim.step(args.steps)
+    lbm.lbm_get_moments(sim.handle, 31, host_out, lbm.LBM_MEM_HOST)
+    e2e_s = barrier_max(time.perf_counter() - t0, world)
+    e2e = cells * args.steps * world / e2e_s / 1e6
+    io_bytes = 5 * cells * 8
+
+    if rank == 0:
+        base = cpu_baseline() if (world == 1 and not args.no_cpu_baseline) else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [NX, NY], "storage": "fp32",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (2 x 218 MB population buffers), no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "algorithmic_bytes_per_lup": BYTES_PER_LUP},
+            "cpu_baseline": base,
+            "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": io_bytes / args.steps,
+                    "d2h_bytes_per_step": io_bytes / args.steps,
+                    "job": f"lbm_init_fields(host) + lbm_step({args.steps}) + lbm_get_moments(host, all 5)"},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

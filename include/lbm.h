@@ -1,0 +1,162 @@
+/*
+ * lbm.h - C ABI of the GB300 library for the three-population phase-field lattice-Boltzmann
+ * method of Zhan, Liang, Chai & Shi, "Phase-field-based lattice Boltzmann method for the
+ * transport of insoluble surfactant in two-phase flows" (arXiv 2408.15654).
+ *
+ * One time step advances, on one 2-D D2Q9 grid, three coupled populations:
+ *   f -> phi   conservative Allen-Cahn phase field                  (Sec. 3.1)
+ *   g -> psi   interface-confined surfactant (Jain's equation)     (Sec. 3.2)
+ *   h -> u, P  consistent incompressible flow with the capillary and
+ *              Marangoni forces of the surfactant EOS sigma(psi)    (Sec. 3.3, Sec. 2.3)
+ * with moment-space MRT collision (Sec. 4) and streaming, periodic in x, periodic or bounded by
+ * half-way bounce-back walls in y.  Every step runs in hand-written sm_103a CUDA kernels; there
+ * is no CPU fallback.
+ *
+ * Conventions shared by all calls
+ *   - Lattice units: dx = dt = c = 1, cs^2 = 1/3.  Cells sit at integer (x, y), 0 <= x < nx,
+ *     0 <= y < ny.  Walls (bc_y = LBM_BC_WALLS) lie half a cell below row 0 and above row ny-1.
+ *   - Host fields are row-major double arrays of ny * nx values, index y * nx + x.
+ *   - Every call returns an int status: LBM_OK (0) or one of the LBM_E* codes below.  No C++
+ *     exception crosses the ABI.  lbm_last_error() gives a message for the calling thread.
+ *   - All device work is enqueued on the CUDA stream given to lbm_create.  Calls marked
+ *     "synchronous" wait for that stream before returning.
+ *   - A handle is not thread safe; use one handle per host thread or serialise the calls.
+ */
+#ifndef GB300_LBM_H
+#define GB300_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define LBM_OK 0
+#define LBM_EINVAL 1    /* invalid argument or unsupported parameter combination            */
+#define LBM_ENOMEM 2    /* workspace too small                                               */
+#define LBM_ECUDA 3     /* a CUDA runtime call failed (message in lbm_last_error)            */
+#define LBM_EUNSTABLE 4 /* the device flagged a non-finite value, |u| >= 0.3, or psi >= 1
+                           under the Langmuir EOS (sticky until the next lbm_init_fields)    */
+#define LBM_ETIMEOUT 5  /* a bounded device wait gave up                                     */
+#define LBM_ESTATE 6    /* call out of order (e.g. lbm_step before lbm_init_fields)          */
+
+/* ---- enumerations ---------------------------------------------------------------------- */
+#define LBM_BC_PERIODIC 0   /* periodic in y (x is always periodic)                          */
+#define LBM_BC_WALLS 1      /* half-way bounce-back walls below row 0 and above row ny-1      */
+
+#define LBM_EOS_LINEAR 0    /* sigma = sigma0 (1 - E0 psi)            (Sec. 2.3, linear EOS)  */
+#define LBM_EOS_LANGMUIR 1  /* sigma = sigma0 [1 + E0 ln(1 - psi)]    (Sec. 2.3, Langmuir EOS) */
+
+#define LBM_STORE_FP32 0    /* populations stored as float                                   */
+
+#define LBM_MEM_HOST 0      /* pointer arguments are host memory (pageable or pinned)        */
+#define LBM_MEM_DEVICE 1    /* pointer arguments are device memory on the handle's device    */
+
+#define LBM_PHI 1u          /* moment masks for lbm_get_moments                              */
+#define LBM_PSI 2u
+#define LBM_UX 4u
+#define LBM_UY 8u
+#define LBM_P 16u
+
+#define LBM_SUM_PHI 0       /* lbm_reduce selectors                                          */
+#define LBM_SUM_PSI 1
+
+/* ---- parameters (plain data, copied by lbm_create) --------------------------------------
+ * Physical constants in lattice units.  The relaxation rates s_f, s_g, s_h are (s0..s4) of the
+ * diagonal S = diag(s0, s1, s1, s2, s2, s2, s3, s3, s4) (Sec. 4); the transport entries are
+ * recomputed by the library and ignored here:
+ *   1/s1^f = M_phi/cs2 + 1/2,  1/s1^g = D/cs2 + 1/2 (Eq. for s1^g),  1/s2^h = mu/(rho cs2) + 1/2.
+ * A value s_h[4] <= 0 means s4^h = s2^h (recommended: keeps plane Couette flow exact).
+ * Requirements: nx >= 2, ny >= 2, phiA != phiB, W > 0, M_phi > 0, D > 0, rhoA = rhoB > 0,
+ * muA, muB > 0, all rates in (0, 2) (s_h[4] may be <= 0), storage = LBM_STORE_FP32.
+ * (Density ratio != 1 is not supported by this build: lbm_create returns LBM_EINVAL.)        */
+typedef struct lbm_params {
+    int32_t nx, ny;         /* grid size                                                     */
+    int32_t bc_y;           /* LBM_BC_PERIODIC or LBM_BC_WALLS                               */
+    int32_t eos;            /* LBM_EOS_LINEAR or LBM_EOS_LANGMUIR                            */
+    int32_t storage;        /* LBM_STORE_FP32                                                */
+    int32_t reserved;       /* must be 0                                                     */
+    double u_top, u_bot;    /* x velocity of the top and bottom wall (LBM_BC_WALLS)          */
+    double phiA, phiB;      /* order parameter of the pure phases (Sec. 2.1)                 */
+    double rhoA, rhoB;      /* densities (Sec. 2.3, linear in phi)                           */
+    double muA, muB;        /* dynamic viscosities (Sec. 2.3, linear in phi)                 */
+    double W;               /* interface width (Sec. 2.1)                                    */
+    double M_phi;           /* phase-field mobility (Sec. 2.1)                               */
+    double D;               /* surfactant diffusivity (Sec. 2.2)                             */
+    double sigma0, E0;      /* clean-interface tension and elasticity number (Sec. 2.3)      */
+    double gx, gy;          /* body-force acceleration, F_b = rho g                          */
+    double n_eps;           /* n = grad phi/|grad phi| if |grad phi| > n_eps, else n = 0     */
+    double s_f[5], s_g[5], s_h[5];
+} lbm_params;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Bytes of device workspace lbm_create needs for these parameters: two population buffers of
+ * 26 float planes (f0..f8, g0..g8, h1..h8; h0 never influences the step), the 2-plane velocity
+ * history, a status word and the reduction partials.  Returns LBM_EINVAL for bad parameters. */
+int lbm_workspace_bytes(const lbm_params* p, size_t* bytes);
+
+/* Create a handle on the current CUDA device.
+ *   d_workspace: device memory of at least lbm_workspace_bytes bytes, 256-byte aligned, owned
+ *                by the caller, kept alive until lbm_destroy (the library never frees it).
+ *   cuda_stream: cudaStream_t on which all work of this handle is enqueued (NULL = legacy
+ *                default stream).
+ *   out:         receives the handle (host memory owned by the library).
+ * The handle holds no state until lbm_init_fields. */
+int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_stream,
+               lbm_handle** out);
+
+/* Set all populations to the equilibria of the given fields (f_eq of Sec. 3.1, g_eq of Sec. 3.2,
+ * h_eq of Sec. 3.3 with S = 0) and clear the status word and the time-derivative history (the
+ * first step after this call uses zero time derivatives).  Each pointer is a row-major array of
+ * ny * nx doubles in `mem` (LBM_MEM_HOST or LBM_MEM_DEVICE); all five are required.
+ * Values are checked for finiteness (and psi < 1 under the Langmuir EOS) on the device.
+ * Synchronous: the caller may free or reuse the arrays when it returns. */
+int lbm_init_fields(lbm_handle* h, const double* phi, const double* psi, const double* ux,
+                    const double* uy, const double* P, int mem);
+
+/* Advance n >= 0 time steps: one fused collide-stream kernel launch per step (pull streaming,
+ * stencils on halo tiles in shared memory, moment-space collision of f, g and h).
+ * Asynchronous: errors found by the device surface at the next synchronous call. */
+int lbm_step(lbm_handle* h, int64_t n);
+
+/* Macroscopic fields at the current time level (phi = sum f, psi = sum g, u from
+ * rho u = sum c h + F/2, P from the pressure equation of Sec. 3.3).  For every bit set in mask
+ * (LBM_PHI, LBM_PSI, LBM_UX, LBM_UY, LBM_P, in that order of out[0..4]) out[k] must point to ny * nx
+ * doubles in `mem`.  Synchronous.  Returns LBM_EUNSTABLE if the status word is set. */
+int lbm_get_moments(lbm_handle* h, unsigned mask, double* const out[5], int mem);
+
+/* Sum over the grid of phi (LBM_SUM_PHI) or psi (LBM_SUM_PSI) in FP64: each cell's populations
+ * are summed in FP64 by warp shuffles, then blocks, then one final block (deterministic order).
+ * Both sums are conserved by the method (sum F_i = sum G_i = 0).  *out is host memory.
+ * Synchronous. */
+int lbm_reduce(lbm_handle* h, int what, double* out);
+
+/* LBM_OK, or LBM_EUNSTABLE if the device has flagged an unstable state since lbm_init_fields.
+ * Synchronous. */
+int lbm_status(lbm_handle* h);
+
+/* Checkpoint: the populations, the velocity history and the step bookkeeping, as an opaque
+ * blob of lbm_state_bytes bytes in host memory.  lbm_set_state restores a blob taken from a
+ * handle with identical parameters.  Both synchronous.  n steps, a checkpoint, then n more
+ * steps give bitwise the same state as 2n steps. */
+int lbm_state_bytes(const lbm_handle* h, size_t* bytes);
+int lbm_get_state(lbm_handle* h, void* host_blob, size_t bytes);
+int lbm_set_state(lbm_handle* h, const void* host_blob, size_t bytes);
+
+/* Number of steps taken since lbm_init_fields (or restored by lbm_set_state). */
+int lbm_steps_taken(const lbm_handle* h, int64_t* steps);
+
+/* Free the handle (not the workspace).  Waits for the handle's stream.  NULL is allowed. */
+int lbm_destroy(lbm_handle* h);
+
+/* Message describing the last failing call on this host thread ("" if none).  The pointer is
+ * valid until the next call on the same thread. */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_LBM_H */

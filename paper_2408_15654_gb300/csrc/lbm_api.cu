@@ -1,0 +1,436 @@
+// Host implementation of the C ABI declared in include/lbm.h.
+//
+// The library owns no device memory: the caller passes one workspace, carved here into
+//   [pops A | pops B | u history | status word | reduction partials]
+// every part 256-byte aligned.  Between steps the population buffer that is not current is dead
+// (the next step overwrites all of it), so host transfers stage through it.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define LBM_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) return fail(LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    int pitch;
+    size_t plane;       // floats per plane
+    size_t pops_bytes;  // one population buffer
+    size_t off_pops[2], off_hist, off_status, off_partials, total;
+};
+
+bool rate_ok(double s) { return s > 0.0 && s < 2.0; }
+
+int validate(const lbm_params* p) {
+    if (!p) return fail(LBM_EINVAL, "params is NULL");
+    if (p->nx < 2 || p->ny < 2) return fail(LBM_EINVAL, "nx and ny must be >= 2 (got %d x %d)", p->nx, p->ny);
+    if ((long long)p->nx * p->ny > (1LL << 30)) return fail(LBM_EINVAL, "grid too large");
+    if (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_WALLS) return fail(LBM_EINVAL, "bad bc_y");
+    if (p->eos != LBM_EOS_LINEAR && p->eos != LBM_EOS_LANGMUIR) return fail(LBM_EINVAL, "bad eos");
+    if (p->storage != LBM_STORE_FP32) return fail(LBM_EINVAL, "storage mode %d not supported", p->storage);
+    if (p->reserved != 0) return fail(LBM_EINVAL, "reserved must be 0");
+    if (!(p->phiA != p->phiB) || !(p->W > 0) || !(p->M_phi > 0) || !(p->D > 0))
+        return fail(LBM_EINVAL, "need phiA != phiB, W > 0, M_phi > 0, D > 0");
+    if (!(p->rhoA > 0) || p->rhoA != p->rhoB)
+        return fail(LBM_EINVAL, "density ratio != 1 is not supported by this build (rhoA = rhoB > 0 required)");
+    if (!(p->muA > 0) || !(p->muB > 0)) return fail(LBM_EINVAL, "viscosities must be > 0");
+    const double* rs[3] = {p->s_f, p->s_g, p->s_h};
+    for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 5; ++j) {
+            if ((k == 0 || k == 1) && j == 1) continue;  // transport rates of f, g: recomputed
+            if (k == 2 && j == 2) continue;              // viscous rate of h: recomputed
+            if (k == 2 && (j == 0)) continue;            // s0^h acts only on the dead h_0
+            if (k == 2 && j == 4 && p->s_h[4] <= 0.0) continue;  // tied to s2^h
+            if ((k == 0 || k == 1) && j == 0) continue;  // conserved zeroth moment
+            if (!rate_ok(rs[k][j])) return fail(LBM_EINVAL, "relaxation rate %d of population %d outside (0, 2)", j, k);
+        }
+    const double s1f = 1.0 / (3.0 * p->M_phi + 0.5), s1g = 1.0 / (3.0 * p->D + 0.5);
+    if (!rate_ok(s1f) || !rate_ok(s1g)) return fail(LBM_EINVAL, "M_phi or D gives a rate outside (0, 2)");
+    if (!std::isfinite(p->sigma0) || !std::isfinite(p->E0) || !std::isfinite(p->gx) || !std::isfinite(p->gy) ||
+        !std::isfinite(p->u_top) || !std::isfinite(p->u_bot) || !(p->n_eps >= 0))
+        return fail(LBM_EINVAL, "non-finite physical parameter");
+    return LBM_OK;
+}
+
+Layout layout_of(const lbm_params* p) {
+    Layout L;
+    L.pitch = (p->nx + 31) / 32 * 32;
+    L.plane = (size_t)p->ny * L.pitch;
+    L.pops_bytes = align_up(L.plane * lbm::kPlanes * sizeof(float));
+    size_t off = 0;
+    L.off_pops[0] = off; off += L.pops_bytes;
+    L.off_pops[1] = off; off += L.pops_bytes;
+    L.off_hist = off; off += align_up(2 * L.plane * sizeof(float));
+    L.off_status = off; off += kAlign;
+    L.off_partials = off; off += align_up(lbm::kMaxPartials * sizeof(double) + sizeof(double));
+    L.total = off;
+    return L;
+}
+
+lbm::Phys make_phys(const lbm_params* p, const Layout& L) {
+    lbm::Phys f;
+    std::memset(&f, 0, sizeof(f));
+    const double dphi = p->phiA - p->phiB;
+    f.nx = p->nx;
+    f.ny = p->ny;
+    f.pitch = L.pitch;
+    f.plane = (long long)L.plane;
+    f.first = 1;
+    f.phiA = (float)p->phiA;
+    f.phiB = (float)p->phiB;
+    f.inv_dphi = (float)(1.0 / dphi);
+    f.cA = (float)(4.0 / (p->W * dphi));
+    f.cap_k = (float)(3.0 / (2.0 * dphi * dphi));
+    f.c16W = (float)(16.0 / p->W);
+    f.W = (float)p->W;
+    f.mar_k = (float)(3.0 * p->W / (2.0 * dphi * dphi));
+    f.sigma0 = (float)p->sigma0;
+    f.E0 = (float)p->E0;
+    f.rho = (float)p->rhoA;
+    f.inv_rho = (float)(1.0 / p->rhoA);
+    f.muB = (float)p->muB;
+    f.dmu = (float)(p->muA - p->muB);
+    f.gx = (float)p->gx;
+    f.gy = (float)p->gy;
+    f.s1f = (float)(1.0 / (3.0 * p->M_phi + 0.5));
+    f.s2f = (float)p->s_f[2];
+    f.s3f = (float)p->s_f[3];
+    f.s4f = (float)p->s_f[4];
+    f.s1g = (float)(1.0 / (3.0 * p->D + 0.5));
+    f.s2g = (float)p->s_g[2];
+    f.s3g = (float)p->s_g[3];
+    f.s4g = (float)p->s_g[4];
+    f.s1h = (float)p->s_h[1];
+    f.s3h = (float)p->s_h[3];
+    f.s4h = (float)p->s_h[4];
+    f.tie_s4h = p->s_h[4] <= 0.0 ? 1 : 0;
+    f.u_top = (float)p->u_top;
+    f.u_bot = (float)p->u_bot;
+    f.n_eps2 = (float)(p->n_eps * p->n_eps);
+    return f;
+}
+
+}  // namespace
+
+struct lbm_handle {
+    lbm_params prm;
+    Layout L;
+    lbm::Phys phys;
+    cudaStream_t stream;
+    char* ws;
+    float* pops[2];
+    float* hist;
+    unsigned* status;
+    double* partials;
+    int cur;          // buffer holding the current state
+    int initialized;
+    int first;        // 1 until the first step after lbm_init_fields
+    int64_t steps;
+};
+
+namespace {
+
+int launch_step(lbm_handle* h, int mode, double* const out[5]) {
+    lbm::StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.p = h->phys;
+    a.p.first = h->first;
+    a.src = h->pops[h->cur];
+    a.dst = h->pops[h->cur ^ 1];
+    a.hist = h->hist;
+    a.status = h->status;
+    if (out)
+        for (int k = 0; k < 5; ++k) a.out[k] = out[k];
+    const dim3 grid((h->prm.nx + lbm::TX - 1) / lbm::TX, (h->prm.ny + lbm::TY - 1) / lbm::TY);
+    const dim3 block(lbm::NT);
+    const bool walls = h->prm.bc_y == LBM_BC_WALLS, lang = h->prm.eos == LBM_EOS_LANGMUIR;
+    using namespace lbm;
+#define LBM_LAUNCH(W_, L_)                                                                        \
+    do {                                                                                          \
+        if (mode == kStep) step_kernel<W_, L_, kStep><<<grid, block, 0, h->stream>>>(a);          \
+        else step_kernel<W_, L_, kMoments><<<grid, block, 0, h->stream>>>(a);                     \
+    } while (0)
+    if (walls && lang) LBM_LAUNCH(true, true);
+    else if (walls) LBM_LAUNCH(true, false);
+    else if (lang) LBM_LAUNCH(false, true);
+    else LBM_LAUNCH(false, false);
+#undef LBM_LAUNCH
+    LBM_CUDA(cudaGetLastError());
+    return LBM_OK;
+}
+
+int read_status(lbm_handle* h, unsigned* st) {
+    LBM_CUDA(cudaMemcpyAsync(st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_workspace_bytes(const lbm_params* p, size_t* bytes) {
+    g_err.clear();
+    int rc = validate(p);
+    if (rc) return rc;
+    if (!bytes) return fail(LBM_EINVAL, "bytes is NULL");
+    *bytes = layout_of(p).total;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_stream, lbm_handle** out) {
+    g_err.clear();
+    int rc = validate(p);
+    if (rc) return rc;
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d_workspace) return fail(LBM_EINVAL, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) return fail(LBM_EINVAL, "workspace not 256-byte aligned");
+    const Layout L = layout_of(p);
+    if (bytes < L.total) return fail(LBM_ENOMEM, "workspace of %zu bytes < %zu needed", bytes, L.total);
+    cudaPointerAttributes attr;
+    LBM_CUDA(cudaPointerGetAttributes(&attr, d_workspace));
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return fail(LBM_EINVAL, "workspace is not device memory");
+    lbm_handle* h = new (std::nothrow) lbm_handle;
+    if (!h) return fail(LBM_ENOMEM, "host allocation failed");
+    std::memset(h, 0, sizeof(*h));
+    h->prm = *p;
+    h->L = L;
+    h->phys = make_phys(p, L);
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->ws = static_cast<char*>(d_workspace);
+    h->pops[0] = reinterpret_cast<float*>(h->ws + L.off_pops[0]);
+    h->pops[1] = reinterpret_cast<float*>(h->ws + L.off_pops[1]);
+    h->hist = reinterpret_cast<float*>(h->ws + L.off_hist);
+    h->status = reinterpret_cast<unsigned*>(h->ws + L.off_status);
+    h->partials = reinterpret_cast<double*>(h->ws + L.off_partials);
+    cudaError_t e = cudaMemsetAsync(h->ws, 0, L.total, h->stream);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(LBM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_handle* h, const double* phi, const double* psi, const double* ux, const double* uy,
+                    const double* P, int mem) {
+    g_err.clear();
+    if (!h) return fail(LBM_EINVAL, "handle is NULL");
+    if (!phi || !psi || !ux || !uy || !P) return fail(LBM_EINVAL, "all five fields are required");
+    if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return fail(LBM_EINVAL, "bad mem kind");
+    const size_t n = (size_t)h->prm.nx * h->prm.ny;
+    const double* d[5] = {phi, psi, ux, uy, P};
+    const int tgt = 0;
+    if (mem == LBM_MEM_HOST) {
+        // stage through the buffer that becomes dead (5 doubles per cell fit in 26 floats)
+        double* stage = reinterpret_cast<double*>(h->pops[tgt ^ 1]);
+        for (int k = 0; k < 5; ++k) {
+            LBM_CUDA(cudaMemcpyAsync(stage + k * n, d[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            d[k] = stage + k * n;
+        }
+    }
+    LBM_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    LBM_CUDA(cudaMemsetAsync(h->pops[tgt], 0, h->L.pops_bytes, h->stream));
+    lbm::InitArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.p = h->phys;
+    a.phi = d[0]; a.psi = d[1]; a.ux = d[2]; a.uy = d[3]; a.P = d[4];
+    a.dst = h->pops[tgt];
+    a.hist = h->hist;
+    a.status = h->status;
+    a.langmuir = h->prm.eos == LBM_EOS_LANGMUIR;
+    a.walls = h->prm.bc_y == LBM_BC_WALLS;
+    const dim3 block(32, 8), grid((h->prm.nx + 31) / 32, (h->prm.ny + 7) / 8);
+    lbm::init_kernel<<<grid, block, 0, h->stream>>>(a);
+    LBM_CUDA(cudaGetLastError());
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    h->cur = tgt;
+    h->first = 1;
+    h->steps = 0;
+    h->initialized = 0;
+    unsigned st = 0;
+    int rc = read_status(h, &st);
+    if (rc) return rc;
+    if (st) return fail(LBM_EINVAL, "initial fields contain non-finite values (or psi >= 1 with the Langmuir EOS)");
+    h->initialized = 1;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle* h, int64_t n) {
+    g_err.clear();
+    if (!h) return fail(LBM_EINVAL, "handle is NULL");
+    if (!h->initialized) return fail(LBM_ESTATE, "lbm_step before lbm_init_fields");
+    if (n < 0) return fail(LBM_EINVAL, "negative step count");
+    for (int64_t k = 0; k < n; ++k) {
+        int rc = launch_step(h, lbm::kStep, nullptr);
+        if (rc) return rc;
+        h->cur ^= 1;
+        h->first = 0;
+        h->steps++;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_moments(lbm_handle* h, unsigned mask, double* const out[5], int mem) {
+    g_err.clear();
+    if (!h) return fail(LBM_EINVAL, "handle is NULL");
+    if (!h->initialized) return fail(LBM_ESTATE, "lbm_get_moments before lbm_init_fields");
+    if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return fail(LBM_EINVAL, "bad mem kind");
+    if (mask & ~31u) return fail(LBM_EINVAL, "bad mask");
+    if (!out && mask) return fail(LBM_EINVAL, "out is NULL");
+    const size_t n = (size_t)h->prm.nx * h->prm.ny;
+    double* dev_out[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    double* stage = reinterpret_cast<double*>(h->pops[h->cur ^ 1]);
+    for (int k = 0; k < 5; ++k) {
+        if (!(mask & (1u << k))) continue;
+        if (!out[k]) return fail(LBM_EINVAL, "out[%d] is NULL but requested by mask", k);
+        dev_out[k] = mem == LBM_MEM_DEVICE ? out[k] : stage + k * n;
+    }
+    int rc = launch_step(h, lbm::kMoments, dev_out);
+    if (rc) return rc;
+    if (mem == LBM_MEM_HOST)
+        for (int k = 0; k < 5; ++k)
+            if (mask & (1u << k))
+                LBM_CUDA(cudaMemcpyAsync(out[k], dev_out[k], n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    unsigned st = 0;
+    rc = read_status(h, &st);
+    if (rc) return rc;
+    if (st) return fail(LBM_EUNSTABLE, "the device flagged an unstable state");
+    return LBM_OK;
+}
+
+int lbm_reduce(lbm_handle* h, int what, double* out) {
+    g_err.clear();
+    if (!h) return fail(LBM_EINVAL, "handle is NULL");
+    if (!h->initialized) return fail(LBM_ESTATE, "lbm_reduce before lbm_init_fields");
+    if (what != LBM_SUM_PHI && what != LBM_SUM_PSI) return fail(LBM_EINVAL, "bad reduction selector");
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    const float* planes = h->pops[h->cur] + (what == LBM_SUM_PSI ? (size_t)lbm::kPlaneG * h->L.plane : 0);
+    const int blocks = h->prm.ny < lbm::kMaxPartials ? h->prm.ny : lbm::kMaxPartials;
+    lbm::reduce_partial_kernel<<<blocks, lbm::kReduceThreads, 0, h->stream>>>(
+        planes, h->prm.nx, h->prm.ny, h->L.pitch, (long long)h->L.plane, h->partials);
+    LBM_CUDA(cudaGetLastError());
+    double* dres = h->partials + lbm::kMaxPartials;
+    lbm::reduce_final_kernel<<<1, lbm::kReduceThreads, 0, h->stream>>>(h->partials, blocks, dres);
+    LBM_CUDA(cudaGetLastError());
+    LBM_CUDA(cudaMemcpyAsync(out, dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    unsigned st = 0;
+    int rc = read_status(h, &st);
+    if (rc) return rc;
+    if (st) return fail(LBM_EUNSTABLE, "the device flagged an unstable state");
+    return LBM_OK;
+}
+
+int lbm_status(lbm_handle* h) {
+    g_err.clear();
+    if (!h) return fail(LBM_EINVAL, "handle is NULL");
+    unsigned st = 0;
+    int rc = read_status(h, &st);
+    if (rc) return rc;
+    return st ? fail(LBM_EUNSTABLE, "the device flagged an unstable state") : LBM_OK;
+}
+
+// State blob: header, then the current population buffer, then the u history.
+struct StateHeader {
+    uint64_t magic;
+    int32_t nx, ny, pitch, first;
+    int64_t steps;
+};
+static const uint64_t kStateMagic = 0x4c424d3253544154ull;  // "LBM2STAT"
+
+int lbm_state_bytes(const lbm_handle* h, size_t* bytes) {
+    g_err.clear();
+    if (!h || !bytes) return fail(LBM_EINVAL, "NULL argument");
+    *bytes = sizeof(StateHeader) + h->L.plane * lbm::kPlanes * sizeof(float) + 2 * h->L.plane * sizeof(float);
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_handle* h, void* host_blob, size_t bytes) {
+    g_err.clear();
+    if (!h || !host_blob) return fail(LBM_EINVAL, "NULL argument");
+    if (!h->initialized) return fail(LBM_ESTATE, "no state before lbm_init_fields");
+    size_t need = 0;
+    lbm_state_bytes(h, &need);
+    if (bytes < need) return fail(LBM_EINVAL, "blob of %zu bytes < %zu needed", bytes, need);
+    StateHeader hd{kStateMagic, h->prm.nx, h->prm.ny, h->L.pitch, h->first, h->steps};
+    char* b = static_cast<char*>(host_blob);
+    std::memcpy(b, &hd, sizeof(hd));
+    const size_t pb = h->L.plane * lbm::kPlanes * sizeof(float);
+    LBM_CUDA(cudaMemcpyAsync(b + sizeof(hd), h->pops[h->cur], pb, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(cudaMemcpyAsync(b + sizeof(hd) + pb, h->hist, 2 * h->L.plane * sizeof(float), cudaMemcpyDeviceToHost,
+                             h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_handle* h, const void* host_blob, size_t bytes) {
+    g_err.clear();
+    if (!h || !host_blob) return fail(LBM_EINVAL, "NULL argument");
+    size_t need = 0;
+    lbm_state_bytes(h, &need);
+    if (bytes < need) return fail(LBM_EINVAL, "blob of %zu bytes < %zu needed", bytes, need);
+    StateHeader hd;
+    const char* b = static_cast<const char*>(host_blob);
+    std::memcpy(&hd, b, sizeof(hd));
+    if (hd.magic != kStateMagic || hd.nx != h->prm.nx || hd.ny != h->prm.ny || hd.pitch != h->L.pitch)
+        return fail(LBM_EINVAL, "state blob does not match this handle");
+    const size_t pb = h->L.plane * lbm::kPlanes * sizeof(float);
+    LBM_CUDA(cudaMemcpyAsync(h->pops[0], b + sizeof(hd), pb, cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA(cudaMemcpyAsync(h->hist, b + sizeof(hd) + pb, 2 * h->L.plane * sizeof(float), cudaMemcpyHostToDevice,
+                             h->stream));
+    LBM_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    h->cur = 0;
+    h->first = hd.first;
+    h->steps = hd.steps;
+    h->initialized = 1;
+    return LBM_OK;
+}
+
+int lbm_steps_taken(const lbm_handle* h, int64_t* steps) {
+    g_err.clear();
+    if (!h || !steps) return fail(LBM_EINVAL, "NULL argument");
+    *steps = h->steps;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle* h) {
+    g_err.clear();
+    if (!h) return LBM_OK;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    delete h;
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

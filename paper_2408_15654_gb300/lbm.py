@@ -1,0 +1,238 @@
+"""Thin ctypes binding of the C ABI in ``include/lbm.h`` (same names, argument marshalling only).
+
+Every step of the method runs in the CUDA library ``liblbm.so``; this module only converts
+arguments.  PyTorch supplies device memory (the workspace and optional device field arrays) and
+the CUDA stream.  If the library cannot be built or loaded, every call raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = range(7)
+LBM_BC_PERIODIC, LBM_BC_WALLS = 0, 1
+LBM_EOS_LINEAR, LBM_EOS_LANGMUIR = 0, 1
+LBM_STORE_FP32 = 0
+LBM_MEM_HOST, LBM_MEM_DEVICE = 0, 1
+LBM_PHI, LBM_PSI, LBM_UX, LBM_UY, LBM_P = 1, 2, 4, 8, 16
+LBM_SUM_PHI, LBM_SUM_PSI = 0, 1
+FIELDS = ("phi", "psi", "ux", "uy", "P")
+
+# Symbols declared in include/lbm.h (checked by the tests against the header and the library).
+EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_init_fields", "lbm_step", "lbm_get_moments",
+           "lbm_reduce", "lbm_status", "lbm_state_bytes", "lbm_get_state", "lbm_set_state",
+           "lbm_steps_taken", "lbm_destroy", "lbm_last_error")
+
+
+class lbm_params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("bc_y", C.c_int32), ("eos", C.c_int32),
+        ("storage", C.c_int32), ("reserved", C.c_int32),
+        ("u_top", C.c_double), ("u_bot", C.c_double),
+        ("phiA", C.c_double), ("phiB", C.c_double), ("rhoA", C.c_double), ("rhoB", C.c_double),
+        ("muA", C.c_double), ("muB", C.c_double), ("W", C.c_double), ("M_phi", C.c_double),
+        ("D", C.c_double), ("sigma0", C.c_double), ("E0", C.c_double), ("gx", C.c_double),
+        ("gy", C.c_double), ("n_eps", C.c_double),
+        ("s_f", C.c_double * 5), ("s_g", C.c_double * 5), ("s_h", C.c_double * 5),
+    ]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lbm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load liblbm.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    lib = C.CDLL(path or _build.build())
+    vp, dp, sz = C.c_void_p, C.POINTER(C.c_double), C.c_size_t
+    P = C.POINTER(lbm_params)
+    sig = {
+        "lbm_workspace_bytes": [P, C.POINTER(sz)],
+        "lbm_create": [P, vp, sz, vp, C.POINTER(vp)],
+        "lbm_init_fields": [vp, vp, vp, vp, vp, vp, C.c_int],
+        "lbm_step": [vp, C.c_int64],
+        "lbm_get_moments": [vp, C.c_uint, C.POINTER(vp), C.c_int],
+        "lbm_reduce": [vp, C.c_int, dp],
+        "lbm_status": [vp],
+        "lbm_state_bytes": [vp, C.POINTER(sz)],
+        "lbm_get_state": [vp, vp, sz],
+        "lbm_set_state": [vp, vp, sz],
+        "lbm_steps_taken": [vp, C.POINTER(C.c_int64)],
+        "lbm_destroy": [vp],
+        "lbm_last_error": [],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_char_p if name == "lbm_last_error" else C.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def lbm_last_error() -> str:
+    return load().lbm_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != LBM_OK:
+        raise LBMError(rc, lbm_last_error())
+
+
+def make_params(p: dict) -> lbm_params:
+    """Marshal a workload parameter dict into ``lbm_params``."""
+    q = lbm_params()
+    q.nx, q.ny = int(p["nx"]), int(p["ny"])
+    q.bc_y = LBM_BC_WALLS if p.get("walls", False) else LBM_BC_PERIODIC
+    q.eos = LBM_EOS_LANGMUIR if p.get("eos", "linear") == "langmuir" else LBM_EOS_LINEAR
+    q.storage = int(p.get("storage", LBM_STORE_FP32))
+    q.reserved = 0
+    for k in ("u_top", "u_bot", "phiA", "phiB", "rhoA", "rhoB", "muA", "muB", "W", "M_phi", "D",
+              "sigma0", "E0", "gx", "gy", "n_eps"):
+        setattr(q, k, float(p[k]))
+    for k in ("s_f", "s_g", "s_h"):
+        arr = getattr(q, k)
+        for i, v in enumerate(p[k]):
+            arr[i] = float(v)
+    return q
+
+
+def lbm_workspace_bytes(params: lbm_params) -> int:
+    n = C.c_size_t()
+    _check(load().lbm_workspace_bytes(C.byref(params), C.byref(n)))
+    return n.value
+
+
+def lbm_create(params: lbm_params, workspace_ptr: int, nbytes: int, stream_ptr: int) -> int:
+    h = C.c_void_p()
+    _check(load().lbm_create(C.byref(params), C.c_void_p(workspace_ptr), nbytes, C.c_void_p(stream_ptr),
+                             C.byref(h)))
+    return h.value
+
+
+def _ptr(a, mem: int):
+    if mem == LBM_MEM_HOST:
+        assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+        return C.c_void_p(a.ctypes.data)
+    return C.c_void_p(a.data_ptr())
+
+
+def lbm_init_fields(h: int, phi, psi, ux, uy, P, mem: int = LBM_MEM_HOST):
+    _check(load().lbm_init_fields(C.c_void_p(h), *[_ptr(a, mem) for a in (phi, psi, ux, uy, P)], mem))
+
+
+def lbm_step(h: int, n: int):
+    _check(load().lbm_step(C.c_void_p(h), int(n)))
+
+
+def lbm_get_moments(h: int, mask: int, outs, mem: int = LBM_MEM_HOST):
+    arr = (C.c_void_p * 5)(*[(_ptr(o, mem) if o is not None else None) for o in outs])
+    _check(load().lbm_get_moments(C.c_void_p(h), mask, arr, mem))
+
+
+def lbm_reduce(h: int, what: int) -> float:
+    v = C.c_double()
+    _check(load().lbm_reduce(C.c_void_p(h), what, C.byref(v)))
+    return v.value
+
+
+def lbm_status(h: int) -> int:
+    return load().lbm_status(C.c_void_p(h))
+
+
+def lbm_state_bytes(h: int) -> int:
+    n = C.c_size_t()
+    _check(load().lbm_state_bytes(C.c_void_p(h), C.byref(n)))
+    return n.value
+
+
+def lbm_get_state(h: int) -> bytes:
+    n = lbm_state_bytes(h)
+    buf = C.create_string_buffer(n)
+    _check(load().lbm_get_state(C.c_void_p(h), buf, n))
+    return buf.raw
+
+
+def lbm_set_state(h: int, blob: bytes):
+    _check(load().lbm_set_state(C.c_void_p(h), C.c_char_p(blob), len(blob)))
+
+
+def lbm_steps_taken(h: int) -> int:
+    v = C.c_int64()
+    _check(load().lbm_steps_taken(C.c_void_p(h), C.byref(v)))
+    return v.value
+
+
+def lbm_destroy(h: int):
+    _check(load().lbm_destroy(C.c_void_p(h)))
+
+
+class Lattice:
+    """One simulation on the current CUDA device: a torch-allocated workspace plus a handle.
+
+    ``params`` is a workload dict (see ``workloads``); ``stream`` a torch CUDA stream (default:
+    the current stream)."""
+
+    def __init__(self, params: dict, stream=None):
+        import torch
+
+        self.params = dict(params)
+        self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        self._p = make_params(params)
+        nbytes = lbm_workspace_bytes(self._p)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = lbm_create(self._p, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, phi, psi, ux, uy, P):
+        arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (self.ny, self.nx)))
+                for a in (phi, psi, ux, uy, P)]
+        lbm_init_fields(self.handle, *arrs, mem=LBM_MEM_HOST)
+
+    def step(self, n: int = 1):
+        lbm_step(self.handle, n)
+
+    def moments(self, mask: int = 31) -> dict:
+        outs = [np.zeros((self.ny, self.nx)) if mask & (1 << k) else None for k in range(5)]
+        lbm_get_moments(self.handle, mask, outs, LBM_MEM_HOST)
+        return {FIELDS[k]: outs[k] for k in range(5) if outs[k] is not None}
+
+    def total(self, what: str) -> float:
+        return lbm_reduce(self.handle, LBM_SUM_PHI if what == "phi" else LBM_SUM_PSI)
+
+    @property
+    def status(self) -> int:
+        return lbm_status(self.handle)
+
+    def state(self) -> bytes:
+        return lbm_get_state(self.handle)
+
+    def restore(self, blob: bytes):
+        lbm_set_state(self.handle, blob)
+
+    @property
+    def steps(self) -> int:
+        return lbm_steps_taken(self.handle)

@@ -142,7 +142,7 @@ def perturbed(params: dict, flds: dict, seed: int, amp_phi=0.02, amp_psi=0.01, a
 
     f = dict(flds)
     f["phi"] = flds["phi"] + amp_phi * smooth()
-    f["psi"] = np.clip(flds["psi"] + amp_psi * (1 + smooth()) * 0.5, 0.0, 0.9)
+    f["psi"] = np.clip(flds["psi"] + amp_psi * (1 + smooth()) * 0.5, 0.0, 0.9) if amp_psi else flds["psi"]
     f["ux"] = flds["ux"] + amp_u * smooth()
     f["uy"] = flds["uy"] + amp_u * smooth()
     f["P"] = flds["P"] + amp_P * smooth()

@@ -1,0 +1,75 @@
+"""The C-ABI library builds for sm_103a, loads, and exports what include/lbm.h declares (no GPU)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2408_15654_gb300 import lbm
+from paper_2408_15654_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(lbm_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lbm.load()
+    names = declared_functions()
+    assert len(names) >= 12
+    assert sorted(lbm.EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", lbm._build.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(lbm_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_params_struct_layout_matches_header(tmp_path):
+    """Compile a probe against the header with gcc and compare sizeof/offsetof with ctypes."""
+    fields = [f[0] for f in lbm.lbm_params._fields_]
+    src = tmp_path / "probe.c"
+    body = "\n".join(f'printf("{f} %zu\\n", offsetof(lbm_params, {f}));' for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm.h"\nint main(void){'
+                   f'printf("size %zu\\n", sizeof(lbm_params));{body}return 0;}}\n')
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), "-o", str(exe), str(src)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n") if line)
+    assert int(got["size"]) == C.sizeof(lbm.lbm_params)
+    for f in fields:
+        assert int(got[f]) == getattr(lbm.lbm_params, f).offset, f
+
+
+def test_workspace_bytes_without_gpu():
+    p, _ = W.shear_drop(512, 256)
+    n = lbm.lbm_workspace_bytes(lbm.make_params(p))
+    pitch = 512
+    # two buffers of 26 float planes, the u history, status and partials
+    assert n >= 2 * 26 * 256 * pitch * 4 + 2 * 256 * pitch * 4
+    assert n < 2 * 26 * 256 * pitch * 4 + 2 * 256 * pitch * 4 + 64 * 1024
+
+
+@pytest.mark.parametrize("bad", [dict(nx=1), dict(ny=0), dict(rhoA=2.0), dict(W=0.0), dict(M_phi=-1.0),
+                                 dict(D=0.0), dict(muA=0.0), dict(s_f=(1, 1, 2.5, 1, 1)),
+                                 dict(sigma0=float("nan")), dict(storage=7)])
+def test_parameter_validation(bad):
+    p, _ = W.stationary_drop(32, 32, R=8)
+    p.update(bad)
+    q = lbm.make_params(p)
+    n = C.c_size_t()
+    rc = lbm.load().lbm_workspace_bytes(C.byref(q), C.byref(n))
+    assert rc == lbm.LBM_EINVAL
+    assert lbm.lbm_last_error()
+
+
+def test_calls_reject_null_handle():
+    lib = lbm.load()
+    assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_reduce(None, 0, None) == lbm.LBM_EINVAL
+    assert lib.lbm_destroy(None) == lbm.LBM_OK
