@@ -35,6 +35,71 @@ int fail(int code, const char* fmt, ...) {
         if (e_ != cudaSuccess) return fail(LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no -lcuda).
+int get_encoder(EncodeTiledFn* fn) {
+    static EncodeTiledFn cached = nullptr;
+    if (!cached) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !ptr)
+            return fail(LBM_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        cached = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    *fn = cached;
+    return LBM_OK;
+}
+
+// 3-D tensor map {nx, ny, planes} of 4-byte floats or 8-byte (f, g) pairs; pitch and plane
+// stride counted in elements.
+int encode_map(CUtensorMap* tm, void* base, bool pairs, int nx, int ny, int planes, int pitch, size_t plane,
+               unsigned bw, unsigned bh, unsigned bp) {
+    EncodeTiledFn enc;
+    int rc = get_encoder(&enc);
+    if (rc) return rc;
+    const cuuint64_t es = pairs ? 8 : 4;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * es, (cuuint64_t)plane * es};
+    const cuuint32_t box[3] = {bw, bh, bp};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(tm, pairs ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(LBM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return LBM_OK;
+}
+
+template <bool W_, bool L_, int M_>
+cudaError_t prepare_kernel(int* blocks_per_sm) {
+    auto k = lbm::step_kernel<W_, L_, M_>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lbm::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, lbm::NT, lbm::kSmemBytes);
+}
+
+// Opt every step-kernel instance into its dynamic shared memory; resident CTAs per SM.
+int prepare_kernels(int* blocks_per_sm) {
+    int b[8];
+    cudaError_t e = prepare_kernel<false, false, lbm::kStep>(&b[0]);
+    if (e == cudaSuccess) e = prepare_kernel<false, true, lbm::kStep>(&b[1]);
+    if (e == cudaSuccess) e = prepare_kernel<true, false, lbm::kStep>(&b[2]);
+    if (e == cudaSuccess) e = prepare_kernel<true, true, lbm::kStep>(&b[3]);
+    if (e == cudaSuccess) e = prepare_kernel<false, false, lbm::kMoments>(&b[4]);
+    if (e == cudaSuccess) e = prepare_kernel<false, true, lbm::kMoments>(&b[5]);
+    if (e == cudaSuccess) e = prepare_kernel<true, false, lbm::kMoments>(&b[6]);
+    if (e == cudaSuccess) e = prepare_kernel<true, true, lbm::kMoments>(&b[7]);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "kernel setup: %s", cudaGetErrorString(e));
+    int m = b[0];
+    for (int k = 1; k < 8; ++k) m = b[k] < m ? b[k] : m;
+    if (m < 1) return fail(LBM_ECUDA, "the step kernel does not fit on an SM");
+    *blocks_per_sm = m;
+    return LBM_OK;
+}
+
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -116,19 +181,30 @@ lbm::Phys make_phys(const lbm_params* p, const Layout& L) {
     f.inv_rho = (float)(1.0 / p->rhoA);
     f.muB = (float)p->muB;
     f.dmu = (float)(p->muA - p->muB);
+    f.s2h = (float)(1.0 / (3.0 * p->muB / p->rhoA + 0.5));
     f.gx = (float)p->gx;
     f.gy = (float)p->gy;
-    f.s1f = (float)(1.0 / (3.0 * p->M_phi + 0.5));
-    f.s2f = (float)p->s_f[2];
-    f.s3f = (float)p->s_f[3];
-    f.s4f = (float)p->s_f[4];
-    f.s1g = (float)(1.0 / (3.0 * p->D + 0.5));
-    f.s2g = (float)p->s_g[2];
-    f.s3g = (float)p->s_g[3];
-    f.s4g = (float)p->s_g[4];
+    const double s1f = 1.0 / (3.0 * p->M_phi + 0.5), s1g = 1.0 / (3.0 * p->D + 0.5);
+    const double sf[4] = {s1f, p->s_f[2], p->s_f[3], p->s_f[4]}, sg[4] = {s1g, p->s_g[2], p->s_g[3], p->s_g[4]};
+    float* nS[4] = {f.nS1, f.nS2, f.nS3, f.nS4};
+    for (int k = 0; k < 4; ++k) {
+        nS[k][0] = (float)(-sf[k]);
+        nS[k][1] = (float)(-sg[k]);
+    }
+    f.K1[0] = (float)(1.0 - 0.5 * sf[0]);
+    f.K1[1] = (float)(1.0 - 0.5 * sg[0]);
+    f.K3[0] = (float)(1.0 - 0.5 * sf[2]);
+    f.K3[1] = (float)(1.0 - 0.5 * sg[2]);
+    const double s2h = 1.0 / (3.0 * p->muB / p->rhoA + 0.5);
+    const double s4h = p->s_h[4] <= 0.0 ? s2h : p->s_h[4];
     f.s1h = (float)p->s_h[1];
     f.s3h = (float)p->s_h[3];
     f.s4h = (float)p->s_h[4];
+    f.k1h = (float)(1.0 - 0.5 * p->s_h[1]);
+    f.k3h = (float)(1.0 - 0.5 * p->s_h[3]);
+    f.k2h = (float)(1.0 - 0.5 * s2h);
+    f.s4h_eff = (float)s4h;
+    f.k4h = (float)(1.0 - 0.5 * s4h);
     f.tie_s4h = p->s_h[4] <= 0.0 ? 1 : 0;
     f.u_top = (float)p->u_top;
     f.u_bot = (float)p->u_bot;
@@ -148,6 +224,10 @@ struct lbm_handle {
     float* hist;
     unsigned* status;
     double* partials;
+    CUtensorMap tm_fg[2];    // TMA descriptors of the (f, g) pair planes of each buffer
+    CUtensorMap tm_h[2];     // TMA descriptors of the h planes of each buffer
+    CUtensorMap tm_hist;     // TMA descriptor of the u history
+    int tiles_x, tiles_y;    // step-kernel grid: one TX x TY tile per CTA
     int cur;          // buffer holding the current state
     int initialized;
     int first;        // 1 until the first step after lbm_init_fields
@@ -159,6 +239,9 @@ namespace {
 int launch_step(lbm_handle* h, int mode, double* const out[5]) {
     lbm::StepArgs a;
     std::memset(&a, 0, sizeof(a));
+    a.tm_fg = h->tm_fg[h->cur];
+    a.tm_h = h->tm_h[h->cur];
+    a.tm_hist = h->tm_hist;
     a.p = h->phys;
     a.p.first = h->first;
     a.src = h->pops[h->cur];
@@ -167,14 +250,14 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
     a.status = h->status;
     if (out)
         for (int k = 0; k < 5; ++k) a.out[k] = out[k];
-    const dim3 grid((h->prm.nx + lbm::TX - 1) / lbm::TX, (h->prm.ny + lbm::TY - 1) / lbm::TY);
-    const dim3 block(lbm::NT);
+    const dim3 grid(h->tiles_x, h->tiles_y), block(lbm::NT);
+    const size_t smem = lbm::kSmemBytes;
     const bool walls = h->prm.bc_y == LBM_BC_WALLS, lang = h->prm.eos == LBM_EOS_LANGMUIR;
     using namespace lbm;
 #define LBM_LAUNCH(W_, L_)                                                                        \
     do {                                                                                          \
-        if (mode == kStep) step_kernel<W_, L_, kStep><<<grid, block, 0, h->stream>>>(a);          \
-        else step_kernel<W_, L_, kMoments><<<grid, block, 0, h->stream>>>(a);                     \
+        if (mode == kStep) step_kernel<W_, L_, kStep><<<grid, block, smem, h->stream>>>(a);       \
+        else step_kernel<W_, L_, kMoments><<<grid, block, smem, h->stream>>>(a);                  \
     } while (0)
     if (walls && lang) LBM_LAUNCH(true, true);
     else if (walls) LBM_LAUNCH(true, false);
@@ -188,6 +271,13 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
 int read_status(lbm_handle* h, unsigned* st) {
     LBM_CUDA(cudaMemcpyAsync(st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+// LBM_OK, LBM_ETIMEOUT (a staging copy did not arrive within its bounded wait) or LBM_EUNSTABLE.
+int status_code(unsigned st) {
+    if (st & lbm::kStatusTimeout) return fail(LBM_ETIMEOUT, "a bounded wait for a tile copy gave up");
+    if (st & lbm::kStatusUnstable) return fail(LBM_EUNSTABLE, "the device flagged an unstable state");
     return LBM_OK;
 }
 
@@ -231,6 +321,21 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
     h->hist = reinterpret_cast<float*>(h->ws + L.off_hist);
     h->status = reinterpret_cast<unsigned*>(h->ws + L.off_status);
     h->partials = reinterpret_cast<double*>(h->ws + L.off_partials);
+    int bps = 0;
+    rc = prepare_kernels(&bps);
+    for (int b = 0; b < 2 && !rc; ++b) {
+        rc = encode_map(&h->tm_fg[b], h->pops[b], true, p->nx, p->ny, lbm::kPairs, L.pitch, L.plane, lbm::BW, lbm::BH, 1);
+        if (!rc)
+            rc = encode_map(&h->tm_h[b], h->pops[b] + (size_t)lbm::kPlaneH * L.plane, false, p->nx, p->ny, 8, L.pitch,
+                            L.plane, lbm::BW, lbm::TY, 1);
+    }
+    if (!rc) rc = encode_map(&h->tm_hist, h->hist, false, p->nx, p->ny, 2, L.pitch, L.plane, lbm::TX, lbm::TY, 2);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    h->tiles_x = (p->nx + lbm::TX - 1) / lbm::TX;
+    h->tiles_y = (p->ny + lbm::TY - 1) / lbm::TY;
     cudaError_t e = cudaMemsetAsync(h->ws, 0, L.total, h->stream);
     if (e != cudaSuccess) {
         delete h;
@@ -323,8 +428,7 @@ int lbm_get_moments(lbm_handle* h, unsigned mask, double* const out[5], int mem)
     unsigned st = 0;
     rc = read_status(h, &st);
     if (rc) return rc;
-    if (st) return fail(LBM_EUNSTABLE, "the device flagged an unstable state");
-    return LBM_OK;
+    return status_code(st);
 }
 
 int lbm_reduce(lbm_handle* h, int what, double* out) {
@@ -333,10 +437,10 @@ int lbm_reduce(lbm_handle* h, int what, double* out) {
     if (!h->initialized) return fail(LBM_ESTATE, "lbm_reduce before lbm_init_fields");
     if (what != LBM_SUM_PHI && what != LBM_SUM_PSI) return fail(LBM_EINVAL, "bad reduction selector");
     if (!out) return fail(LBM_EINVAL, "out is NULL");
-    const float* planes = h->pops[h->cur] + (what == LBM_SUM_PSI ? (size_t)lbm::kPlaneG * h->L.plane : 0);
     const int blocks = h->prm.ny < lbm::kMaxPartials ? h->prm.ny : lbm::kMaxPartials;
     lbm::reduce_partial_kernel<<<blocks, lbm::kReduceThreads, 0, h->stream>>>(
-        planes, h->prm.nx, h->prm.ny, h->L.pitch, (long long)h->L.plane, h->partials);
+        h->pops[h->cur], what == LBM_SUM_PSI ? 1 : 0, h->prm.nx, h->prm.ny, h->L.pitch, (long long)h->L.plane,
+        h->partials);
     LBM_CUDA(cudaGetLastError());
     double* dres = h->partials + lbm::kMaxPartials;
     lbm::reduce_final_kernel<<<1, lbm::kReduceThreads, 0, h->stream>>>(h->partials, blocks, dres);
@@ -345,8 +449,7 @@ int lbm_reduce(lbm_handle* h, int what, double* out) {
     unsigned st = 0;
     int rc = read_status(h, &st);
     if (rc) return rc;
-    if (st) return fail(LBM_EUNSTABLE, "the device flagged an unstable state");
-    return LBM_OK;
+    return status_code(st);
 }
 
 int lbm_status(lbm_handle* h) {
@@ -355,7 +458,7 @@ int lbm_status(lbm_handle* h) {
     unsigned st = 0;
     int rc = read_status(h, &st);
     if (rc) return rc;
-    return st ? fail(LBM_EUNSTABLE, "the device flagged an unstable state") : LBM_OK;
+    return status_code(st);
 }
 
 // State blob: header, then the current population buffer, then the u history.

@@ -1,19 +1,22 @@
 // Device code of the fused three-population lattice-Boltzmann step (arXiv 2408.15654).
 //
-// Data layout in HBM (one population buffer): 26 float planes of ny rows x `pitch` floats,
-//   planes 0..8   f_0..f_8   phase field        (Sec. 3.1)
-//   planes 9..17  g_0..g_8   surfactant         (Sec. 3.2)
-//   planes 18..25 h_1..h_8   flow; h_0 is never stored: column 0 of M^-1 is e_0 and rows 1..8
-//                            of M do not see h_0, so h_0 feeds only itself (Sec. 3.3, Sec. 4).
+// Data layout in HBM (one population buffer, ny rows x `pitch` cells per plane):
+//   9 pair planes  (f_i, g_i), i = 0..8, as float2   phase field (Sec. 3.1) and surfactant (Sec. 3.2)
+//   8 float planes h_1..h_8                           flow (Sec. 3.3)
+// f_i and g_i stream along the same link, so they travel and collide together as one float2:
+// one 64-bit load and store per pair, and Blackwell's packed FP32x2 arithmetic runs both
+// collisions at once.  h_0 is never stored: column 0 of M^-1 is e_0 and rows 1..8 of M do not
+// see h_0, so h_0 feeds only itself (Sec. 3.3, Sec. 4).
 // A buffer holds the post-collision populations of the previous step at the cell that produced
-// them; a step pulls f_i(x) = f*_i(x - c_i) ("pull" streaming), so it writes only its own cell
-// and two buffers alternate.  At a wall the missing link is the cell's own opposite slot, into
-// which the previous step already folded the moving-wall term (half-way bounce-back, Sec. 4).
+// them; a step pulls q_i(x) = q*_i(x - c_i) ("pull" streaming), so it writes only its own cell
+// and two buffers alternate.  Across a wall the missing link is the cell's own opposite slot,
+// into which the previous step already folded the moving-wall term (half-way bounce-back, Sec. 4).
 //
 // Velocity order (the columns of the printed moment matrix M, Sec. 4):
 //   0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace lbm {
@@ -26,14 +29,14 @@ __host__ __device__ constexpr float wgt(int i) { return i == 0 ? 4.f / 9.f : (i 
 static_assert(opp(1) == 3 && opp(3) == 1 && opp(2) == 4 && opp(4) == 2, "axis opposites");
 static_assert(opp(5) == 7 && opp(7) == 5 && opp(6) == 8 && opp(8) == 6, "diagonal opposites");
 
-constexpr int kPlanes = 26;   // f0..f8, g0..g8, h1..h8
-constexpr int kPlaneG = 9;
-constexpr int kPlaneH = 18;   // plane of h_1
+constexpr int kPlanes = 26;     // float planes per buffer: 9 pair planes (18) + 8 h planes
+constexpr int kPairs = 9;       // (f_i, g_i) planes, float2
+constexpr int kPlaneH = 18;     // float-plane index of h_1
 
 // Physical constants in FP32, precomputed on the host from lbm_params.
 struct Phys {
     int nx, ny, pitch, first;
-    long long plane;          // floats per plane (ny * pitch)
+    long long plane;          // cells per plane (ny * pitch)
     float phiA, phiB, inv_dphi;
     float cA;                 // 4 / (W dphi):  A = cA (phiA - phi)(phi - phiB), B = cA psi (phiA + phiB - 2 phi)
     float cap_k, c16W, W;     // capillary: cap_k sigma [c16W (phiA-phi)(phi-phiB)(phiA+phiB-2phi) - W lap phi]
@@ -41,10 +44,12 @@ struct Phys {
     float sigma0, E0;
     float rho, inv_rho;
     float muB, dmu;           // mu(phi) = muB + (phi - phiB)/dphi * dmu
+    float s2h;                // 1/s2^h when the viscosity is uniform (dmu == 0)
     float gx, gy;
-    float s1f, s2f, s3f, s4f;
-    float s1g, s2g, s3g, s4g;
-    float s1h, s3h, s4h;
+    float nS1[2], nS2[2], nS3[2], nS4[2];  // -s_k of (f, g) for k = 1..4
+    float K1[2], K3[2];                    // 1 - s_k/2 of (f, g) for k = 1, 3
+    float s1h, s3h, s4h, k1h, k3h;         // flow rates and 1 - s/2
+    float k2h, s4h_eff, k4h;               // with uniform viscosity: 1 - s2/2, s4, 1 - s4/2
     int tie_s4h;              // 1: s4^h = s2^h
     float u_top, u_bot;
     float n_eps2;             // n_eps^2
@@ -52,7 +57,39 @@ struct Phys {
 
 enum Mode { kStep = 0, kMoments = 1 };
 
+// Tile geometry.  A CTA of NT threads owns a TX x TY tile, one cell per thread.  TMA stages:
+//   pair plane i: box of BW x BH pairs,  row r, col c <-> (x0 - 4 + c, y0 - 1 - cy(i) + r)
+//   h plane i:    box of BW x TY floats, row r, col c <-> (x0 - 4 + c, y0 - cy(i) + r)
+// so extended-tile cell (ex, ey) (global (x0 - 1 + ex, y0 - 1 + ey)) pulls pair i from
+// [ey][ex + 3 - cx(i)], the own cell (tx, ty) pulls h_i from [ty][tx + 4 - cx(i)], and the own
+// cell's unshifted post-collision pair i sits at [ty + 1 + cy(i)][tx + 4].  Boxes start 4 cells
+// left of the tile so that every x coordinate is a multiple of 16 bytes.
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int BW = TX + 8, BH = TY + 2;
+constexpr int FG_BOX = BW * BH;            // pairs per pair-plane box (3200 B)
+constexpr int H_BOX = BW * TY;             // floats per h box (1280 B)
+constexpr int HIST_BOX = 2 * TX * TY;      // u_x, u_y of the tile
+constexpr int EX = TX + 2, EY = TY + 2, NE = EX * EY;
+constexpr int NRING = 2 * EX + 2 * TY;
+constexpr int SM_FG = 0;                                       // byte offsets in shared memory
+constexpr int SM_H = SM_FG + kPairs * FG_BOX * 8;
+constexpr int SM_HIST = SM_H + 8 * H_BOX * 4;
+constexpr int SM_PP = SM_HIST + HIST_BOX * 4;
+constexpr int SM_BAR = SM_PP + NE * 8;
+constexpr size_t kSmemBytes = SM_BAR + 16 + 128;               // + mbarrier + alignment slack
+constexpr unsigned kTileBytes = (unsigned)(kPairs * FG_BOX * 8 + 8 * H_BOX * 4 + HIST_BOX * 4);
+constexpr unsigned kSuspendNs = 200000;                        // sleep hint of one wait attempt
+constexpr unsigned kWaitLimit = 5000;                          // attempts: the wait ends within ~1 s
+constexpr unsigned kStatusUnstable = 1u, kStatusTimeout = 2u;
+
+static_assert((FG_BOX * 8) % 128 == 0 && (H_BOX * 4) % 128 == 0 && SM_H % 128 == 0 && SM_HIST % 128 == 0,
+              "TMA destinations are 128-byte aligned");
+static_assert(NRING <= NT, "one thread per ring cell");
+
 struct StepArgs {
+    CUtensorMap tm_fg;            // {nx, ny, 9} 8-byte pairs, box {BW, BH, 1}
+    CUtensorMap tm_h;             // {nx, ny, 8} floats, box {BW, TY, 1}
+    CUtensorMap tm_hist;          // {nx, ny, 2} floats, box {TX, TY, 2}
     Phys p;
     const float* __restrict__ src;
     float* __restrict__ dst;
@@ -61,186 +98,249 @@ struct StepArgs {
     double* __restrict__ out[5];  // kMoments: phi, psi, ux, uy, P (dense ny x nx), may be null
 };
 
-constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int EX = TX + 2, EY = TY + 2, NE = EX * EY;
-
-__device__ __forceinline__ int wrap1(int a, int n) {
-    a += (a < 0) ? n : 0;
-    a -= (a >= n) ? n : 0;
-    return min(max(a, 0), n - 1);  // only cells no valid cell reads can still be out of range
+__device__ __forceinline__ int wrapg(int a, int n) {
+    const int r = a % n;
+    return r < 0 ? r + n : r;
 }
 
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+// packed FP32x2 arithmetic (one instruction for both lanes)
+__device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+__device__ __forceinline__ void mbar_init(unsigned long long* m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+// One bounded wait attempt: the thread may sleep until the phase completes or kSuspendNs pass.
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* m, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2, %3;\n selp.u32 %0, 1, 0, P1;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity), "n"(kSuspendNs)
+        : "memory");
+    return ok != 0;
+}
+// Wait for a phase of the mbarrier with an iteration limit; false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* m, uint32_t parity) {
+    for (unsigned it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(m, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            unsigned long long* m) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(m))
+        : "memory");
 }
 
-// Moment-space MRT collision of a scalar-transport population (f or g), applied as an
-// increment so that FP32 rounding stays at the scale of the populations' departure from
-// equilibrium (in a uniform bulk the increment is zero and the populations are unchanged):
+// Moment-space MRT collision of the (f, g) pair, applied as an increment so that FP32 rounding
+// stays at the scale of the departure from equilibrium (in a uniform bulk nothing changes):
 //   m = M q;  dm_k = -s_k (m_k - m_eq_k) + (1 - s_k/2) m_src_k;  q* = q + M^-1 dm.
-// Equilibrium w_i s (1 + c_i.u/cs2) has moments (s, s ux, s uy, s/3, s/3, 0, s ux/3, s uy/3, s/9);
-// the source w_i c_i.V has moments (0, cs2 Vx, cs2 Vy, 0, 0, 0, Vx/9, Vy/9, 0) with
-// cs2 V = (vx, vy) passed in.  dm_0 = 0: the zeroth moment is conserved.
-__device__ __forceinline__ void collide_scalar(float q[9], float s, float ux, float uy, float vx, float vy,
-                                               float s1, float s2, float s3, float s4) {
-    const float third = 1.f / 3.f;
-    const float m1 = q[1] - q[3] + q[5] - q[6] - q[7] + q[8];
-    const float m2 = q[2] - q[4] + q[5] + q[6] - q[7] - q[8];
-    const float m3 = q[1] + q[3] + q[5] + q[6] + q[7] + q[8];
-    const float m4 = q[2] + q[4] + q[5] + q[6] + q[7] + q[8];
-    const float m5 = q[5] - q[6] + q[7] - q[8];
-    const float m6 = q[5] - q[6] - q[7] + q[8];
-    const float m7 = q[5] + q[6] - q[7] - q[8];
-    const float m8 = q[5] + q[6] + q[7] + q[8];
-    const float d1 = -s1 * (m1 - s * ux) + (1.f - 0.5f * s1) * vx;
-    const float d2 = -s1 * (m2 - s * uy) + (1.f - 0.5f * s1) * vy;
-    const float d3 = -s2 * (m3 - s * third);
-    const float d4 = -s2 * (m4 - s * third);
-    const float d5 = -s2 * m5;
-    const float d6 = -s3 * (m6 - s * ux * third) + (1.f - 0.5f * s3) * vx * third;
-    const float d7 = -s3 * (m7 - s * uy * third) + (1.f - 0.5f * s3) * vy * third;
-    const float d8 = -s4 * (m8 - s * (1.f / 9.f));
-    q[0] += -d3 - d4 + d8;
-    q[1] += 0.5f * (d1 + d3 - d6 - d8);
-    q[2] += 0.5f * (d2 + d4 - d7 - d8);
-    q[3] += 0.5f * (-d1 + d3 + d6 - d8);
-    q[4] += 0.5f * (-d2 + d4 + d7 - d8);
-    q[5] += 0.25f * (d5 + d6 + d7 + d8);
-    q[6] += 0.25f * (-d5 - d6 + d7 + d8);
-    q[7] += 0.25f * (d5 - d6 - d7 + d8);
-    q[8] += 0.25f * (-d5 + d6 - d7 + d8);
+// For a scalar s (phi or psi) the equilibrium w_i s (1 + c_i.u/cs2) has moments
+// (s, s ux, s uy, s/3, s/3, 0, s ux/3, s uy/3, s/9); the source w_i c_i.V has moments
+// (0, cs2 Vx, cs2 Vy, 0, 0, 0, Vx/9, Vy/9, 0) with cs2 V = (vx, vy).  dm_0 = 0.
+// nS_k = -s_k and K_k = 1 - s_k/2 per lane (f, g).
+__device__ __forceinline__ void collide_pair(float2 q[9], float2 s, float ux, float uy, float2 vx, float2 vy,
+                                             float2 nS1, float2 nS2, float2 nS3, float2 nS4, float2 K1, float2 K3) {
+    const float2 third = bc(1.f / 3.f);
+    const float2 a = add2(q[5], q[7]), b = add2(q[6], q[8]), c = sub2(q[5], q[7]), d = sub2(q[6], q[8]);
+    const float2 m5 = sub2(a, b), m8 = add2(a, b), m6 = sub2(c, d), m7 = add2(c, d);
+    const float2 m1 = add2(sub2(q[1], q[3]), m6), m2 = add2(sub2(q[2], q[4]), m7);
+    const float2 m3 = add2(add2(q[1], q[3]), m8), m4 = add2(add2(q[2], q[4]), m8);
+    const float2 su = mul2(s, bc(ux)), sv = mul2(s, bc(uy)), s3 = mul2(s, third);
+    const float2 d1 = fma2(nS1, sub2(m1, su), mul2(K1, vx));
+    const float2 d2 = fma2(nS1, sub2(m2, sv), mul2(K1, vy));
+    const float2 d3 = mul2(nS2, sub2(m3, s3));
+    const float2 d4 = mul2(nS2, sub2(m4, s3));
+    const float2 d5 = mul2(nS2, m5);
+    const float2 d6 = fma2(nS3, fma2(su, bc(-1.f / 3.f), m6), mul2(K3, mul2(vx, third)));
+    const float2 d7 = fma2(nS3, fma2(sv, bc(-1.f / 3.f), m7), mul2(K3, mul2(vy, third)));
+    const float2 d8 = mul2(nS4, fma2(s, bc(-1.f / 9.f), m8));
+    const float2 A = sub2(d1, d6), B = sub2(d3, d8), C = sub2(d2, d7), D = sub2(d4, d8);
+    const float2 E = add2(d8, d5), F = sub2(d8, d5), G = add2(d6, d7), H = sub2(d7, d6);
+    const float2 half = bc(0.5f), quarter = bc(0.25f);
+    q[0] = add2(q[0], sub2(sub2(d8, d3), d4));
+    q[1] = fma2(half, add2(A, B), q[1]);
+    q[3] = fma2(half, sub2(B, A), q[3]);
+    q[2] = fma2(half, add2(C, D), q[2]);
+    q[4] = fma2(half, sub2(D, C), q[4]);
+    q[5] = fma2(quarter, add2(E, G), q[5]);
+    q[7] = fma2(quarter, sub2(E, G), q[7]);
+    q[6] = fma2(quarter, add2(F, H), q[6]);
+    q[8] = fma2(quarter, sub2(F, H), q[8]);
 }
 
-// One fused step (kStep) or the macroscopic fields of the current level (kMoments) for a
-// TX x TY tile.  The pulled f and g of the tile and of a one-cell ring around it are staged in
-// shared memory by cp.async; phi and psi of the ring give the 9-point stencils; the same window
-// also holds the own cell's unshifted post-collision values, whose sums are phi and psi of the
-// previous level (m*_0 = phi exactly, Sec. 3.1), so only u of the previous level is stored.
+// Tiles whose boxes reach outside the grid: replace every staged value whose source lies outside
+// by the one the pull really reads there -- the periodic image, or across a wall the pulling
+// cell's own opposite slot (bounce-back).  Only the out-of-grid strips of each box are visited
+// (one warp per plane); entries no valid pull reads are left as loaded.
+template <bool WALLS>
+__device__ void patch_edges(const StepArgs& a, float2* FG, float* Hs, int x0, int y0) {
+    const Phys& p = a.p;
+    const float2* __restrict__ srcFG = reinterpret_cast<const float2*>(a.src);
+    const float* __restrict__ srcH = a.src + (size_t)kPlaneH * p.plane;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cL = min(BW, max(0, 4 - x0));             // box columns [0, cL) lie left of x = 0
+    const int cR = max(cL, min(BW, p.nx - x0 + 4));     // box columns [cR, BW) lie right of nx - 1
+    for (int pl = warp; pl < kPairs + 8; pl += NT / 32) {
+        const bool isfg = pl < kPairs;
+        const int i = isfg ? pl : pl - kPairs + 1;       // direction
+        const int rows = isfg ? BH : TY;
+        const int gy0 = (isfg ? y0 - 1 : y0) - cy(i);    // global row of box row 0
+        const int rB = min(rows, max(0, -gy0));          // box rows [0, rB) lie below y = 0
+        const int rT = max(rB, min(rows, p.ny - gy0));   // box rows [rT, rows) lie above ny - 1
+        const int ncol = cL + (BW - cR), w = cR - cL;
+        const int n1 = rows * ncol, n2 = (rB + rows - rT) * w;
+        for (int k = lane; k < n1 + n2; k += 32) {
+            int r, c;
+            if (k < n1) {
+                r = k / ncol;
+                const int j = k - r * ncol;
+                c = j < cL ? j : cR + (j - cL);
+            } else {
+                const int kk = k - n1, rr = kk / w;
+                c = cL + (kk - rr * w);
+                r = rr < rB ? rr : rT + (rr - rB);
+            }
+            const int gx = x0 - 4 + c, gy = gy0 + r;
+            const bool yin = gy >= 0 && gy < p.ny;
+            // the cell that pulls this entry must be one the tile uses
+            const int ex = c - 3 + cx(i);
+            if (isfg ? (ex < 0 || ex >= EX) : (ex - 1 < 0 || ex - 1 >= TX)) continue;
+            const int px = gx + cx(i), py = gy + cy(i);
+            int si = i, sx, sy;
+            if (WALLS) {
+                if (py < 0 || py >= p.ny) continue;  // puller is a ring cell beyond a wall (mirrored)
+                if (!yin) {
+                    si = opp(i);
+                    sx = wrapg(px, p.nx);
+                    sy = py;
+                } else {
+                    sx = wrapg(gx, p.nx);
+                    sy = gy;
+                }
+            } else {
+                sx = wrapg(gx, p.nx);
+                sy = wrapg(gy, p.ny);
+            }
+            const size_t cell = (size_t)sy * p.pitch + sx;
+            if (isfg) FG[pl * FG_BOX + r * BW + c] = srcFG[(size_t)si * p.plane + cell];
+            else Hs[(pl - kPairs) * H_BOX + r * BW + c] = srcH[(size_t)(si - 1) * p.plane + cell];
+        }
+    }
+}
+
+// One fused step (kStep) or the macroscopic fields of the current level (kMoments) for one tile.
+// One elected thread stages the tile with TMA (9 pair boxes, 8 h boxes, the u history) on one
+// mbarrier; edge tiles then patch wrapped and bounced entries.  The pulled (f, g) of the tile and
+// of a one-cell ring give (phi, psi) for the 9-point stencils; the same boxes hold the own cell's
+// unshifted post-collision values, whose sums are phi and psi of the previous level
+// (m*_0 = phi exactly, Sec. 3.1), so only u of the previous level is stored.
 template <bool WALLS, bool LANGMUIR, int MODE>
-__global__ void __launch_bounds__(NT, 2) step_kernel(const __grid_constant__ StepArgs a) {
-    __shared__ float sF[9 * NE];
-    __shared__ float sG[9 * NE];
-    __shared__ float sPhi[NE];
-    __shared__ float sPsi[NE];
+__global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ StepArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float2* FG = reinterpret_cast<float2*>(sm + SM_FG);
+    float* Hs = reinterpret_cast<float*>(sm + SM_H);
+    const float* Hist = reinterpret_cast<const float*>(sm + SM_HIST);
+    float2* PP = reinterpret_cast<float2*>(sm + SM_PP);
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + SM_BAR);
     const Phys& p = a.p;
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const float* __restrict__ srcF = a.src;
-    const float* __restrict__ srcG = a.src + (size_t)kPlaneG * p.plane;
 
-    // ---- stage 1: pull f and g of the extended tile into shared memory ----
+    if (t == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        mbar_expect_tx(mbar, kTileBytes);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int e = t + k * NT;
-        if (e < NE) {
-            const int ey = e / EX, ex = e - ey * EX;
-            const int gxx = x0 - 1 + ex, gyy = y0 - 1 + ey;
-            const bool row_in = !WALLS || (gyy >= 0 && gyy < p.ny);
-            if (row_in) {
-                const int cols[3] = {wrap1(gxx - 1, p.nx), wrap1(gxx, p.nx), wrap1(gxx + 1, p.nx)};
-                int rows[3];
-                bool rin[3];
-                if (WALLS) {
-                    rows[0] = gyy - 1; rows[1] = gyy; rows[2] = gyy + 1;
-                    rin[0] = gyy - 1 >= 0; rin[1] = true; rin[2] = gyy + 1 < p.ny;
-                } else {
-                    rows[0] = wrap1(gyy - 1, p.ny); rows[1] = wrap1(gyy, p.ny); rows[2] = wrap1(gyy + 1, p.ny);
-                    rin[0] = rin[1] = rin[2] = true;
-                }
+        for (int i = 0; i < kPairs; ++i) tma_load_3d(FG + i * FG_BOX, &a.tm_fg, x0 - 4, y0 - 1 - cy(i), i, mbar);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    // pull source x - c_i; beyond a wall: the own opposite slot
-                    int plane = i, r = rows[1 - cy(i)], c = cols[1 - cx(i)];
-                    if (WALLS && !rin[1 - cy(i)]) { plane = opp(i); r = rows[1]; c = cols[1]; }
-                    const size_t off = (size_t)plane * p.plane + (size_t)r * p.pitch + c;
-                    cp_async4(&sF[i * NE + e], srcF + off);
-                    cp_async4(&sG[i * NE + e], srcG + off);
-                }
-            }
-        }
+        for (int i = 1; i < 9; ++i) tma_load_3d(Hs + (i - 1) * H_BOX, &a.tm_h, x0 - 4, y0 - cy(i), i - 1, mbar);
+        tma_load_3d(sm + SM_HIST, &a.tm_hist, x0, y0, 0, mbar);
+    }
+    __syncthreads();
+    bool abort = !mbar_wait_bounded(mbar, 0);
+    if (x0 == 0 || x0 + TX + 4 > p.nx || y0 == 0 || y0 + TY + 2 > p.ny) {
+        if (!abort) patch_edges<WALLS>(a, FG, Hs, x0, y0);
+        abort = __syncthreads_or(abort);
     }
 
-    // ---- own cell: h_1..h_8 straight into registers, u of the previous level ----
     const int tx = t % TX, ty = t / TX;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = (x < p.nx) && (y < p.ny);
-    float h[9];
-    float uxp = 0.f, uyp = 0.f;
-    if (active) {
-        const int cols[3] = {wrap1(x - 1, p.nx), x, wrap1(x + 1, p.nx)};
-        int rows[3];
-        bool rin[3];
-        if (WALLS) {
-            rows[0] = y - 1; rows[1] = y; rows[2] = y + 1;
-            rin[0] = y >= 1; rin[1] = true; rin[2] = y + 1 < p.ny;
-        } else {
-            rows[0] = wrap1(y - 1, p.ny); rows[1] = y; rows[2] = wrap1(y + 1, p.ny);
-            rin[0] = rin[1] = rin[2] = true;
-        }
-        const float* __restrict__ srcH = a.src + (size_t)kPlaneH * p.plane;
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            int plane = i, r = rows[1 - cy(i)], c = cols[1 - cx(i)];
-            if (WALLS && !rin[1 - cy(i)]) { plane = opp(i); r = y; c = x; }
-            h[i] = __ldg(srcH + (size_t)(plane - 1) * p.plane + (size_t)r * p.pitch + c);
-        }
-        if (!p.first) {
-            uxp = __ldg(a.hist + (size_t)y * p.pitch + x);
-            uyp = __ldg(a.hist + p.plane + (size_t)y * p.pitch + x);
-        }
-    }
-    cp_async_wait_all();
-    __syncthreads();
 
-    // ---- stage 2: phi and psi on the extended tile (cells beyond a wall mirror the fluid row) ----
+    // ---- (phi, psi) of the extended tile: the own cell (pulled pairs kept for the collision)
+    //      and the ring; cells beyond a wall take the value of the adjacent fluid row ----
+    const int eo = (ty + 1) * EX + (tx + 1);
+    float2 q[9];
+    {
+        int row = ty + 1;
+        if (WALLS && y >= p.ny) row = p.ny - y0;
+        float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int e = t + k * NT;
-        if (e < NE) {
-            int es = e;
-            if (WALLS) {
-                const int ey = e / EX, ex = e - ey * EX;
-                const int gyy = y0 - 1 + ey;
-                if (gyy < 0) es = (1 - y0) * EX + ex;
-                else if (gyy >= p.ny) es = (p.ny - y0) * EX + ex;
-            }
-            float sp = 0.f, ss = 0.f;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                sp += sF[i * NE + es];
-                ss += sG[i * NE + es];
-            }
-            sPhi[e] = sp;
-            sPsi[e] = ss;
+        for (int i = 0; i < 9; ++i) {
+            q[i] = FG[i * FG_BOX + row * BW + tx + 4 - cx(i)];
+            s = add2(s, q[i]);
         }
+        PP[eo] = s;
     }
-    __syncthreads();
+    if (t < NRING) {
+        int ex, ey;
+        if (t < EX) { ex = t; ey = 0; }
+        else if (t < 2 * EX) { ex = t - EX; ey = EY - 1; }
+        else if (t < 2 * EX + TY) { ex = 0; ey = 1 + t - 2 * EX; }
+        else { ex = EX - 1; ey = 1 + t - 2 * EX - TY; }
+        int row = ey;
+        if (WALLS) {
+            const int gy = y0 - 1 + ey;
+            if (gy < 0) row = 1 - y0;
+            else if (gy >= p.ny) row = p.ny - y0;
+        }
+        float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s = add2(s, FG[i * FG_BOX + row * BW + ex + 3 - cx(i)]);
+        PP[ey * EX + ex] = s;
+    }
+    if (__syncthreads_or(abort)) {
+        // a staging copy did not arrive in time: report it, wait (bounded) for it, store nothing
+        if (t == 0) {
+            atomicOr(a.status, kStatusTimeout);
+            mbar_wait_bounded(mbar, 0);
+        }
+        __syncthreads();
+        return;
+    }
     if (!active) return;
 
-    // ---- stage 3: the cell ----
-    const int eo = (ty + 1) * EX + (tx + 1);
-    const float phi = sPhi[eo], psi = sPsi[eo];
-    const float third = 1.f / 3.f, twelfth = 1.f / 12.f, sixth = 1.f / 6.f;
+    const float2 pp = PP[eo];          // (phi, psi)
+    const float phi = pp.x, psi = pp.y;
 
-    // isotropic stencils: d_a = (1/cs2) sum w_i c_ia q(x+c_i);  lap = (2/cs2) sum_{i>0} w_i (q_i - q)
-    float gpx, gpy, lap, gsx, gsy;
+    // isotropic stencils of (phi, psi) at once:
+    //   d_a = (1/cs2) sum w_i c_ia q(x+c_i);  lap = (2/cs2) sum_{i>0} w_i (q_i - q)
+    float2 gX, gY, lap2;
     {
-        const float E = sPhi[eo + 1], Wn = sPhi[eo - 1], N = sPhi[eo + EX], S = sPhi[eo - EX];
-        const float NE_ = sPhi[eo + EX + 1], NW = sPhi[eo + EX - 1], SE = sPhi[eo - EX + 1], SW = sPhi[eo - EX - 1];
-        gpx = (E - Wn) * third + (NE_ + SE - NW - SW) * twelfth;
-        gpy = (N - S) * third + (NE_ + NW - SE - SW) * twelfth;
-        lap = (4.f * (E + Wn + N + S) + (NE_ + NW + SE + SW) - 20.f * phi) * sixth;
+        const float2 E = PP[eo + 1], Wn = PP[eo - 1], N = PP[eo + EX], S_ = PP[eo - EX];
+        const float2 NE_ = PP[eo + EX + 1], NW = PP[eo + EX - 1], SE = PP[eo - EX + 1], SW = PP[eo - EX - 1];
+        const float2 third = bc(1.f / 3.f), twelfth = bc(1.f / 12.f);
+        gX = fma2(sub2(add2(NE_, SE), add2(NW, SW)), twelfth, mul2(sub2(E, Wn), third));
+        gY = fma2(sub2(add2(NE_, NW), add2(SE, SW)), twelfth, mul2(sub2(N, S_), third));
+        const float2 axis = add2(add2(E, Wn), add2(N, S_)), diag = add2(add2(NE_, NW), add2(SE, SW));
+        lap2 = mul2(fma2(bc(4.f), axis, fma2(bc(-20.f), pp, diag)), bc(1.f / 6.f));
     }
-    {
-        const float E = sPsi[eo + 1], Wn = sPsi[eo - 1], N = sPsi[eo + EX], S = sPsi[eo - EX];
-        const float NE_ = sPsi[eo + EX + 1], NW = sPsi[eo + EX - 1], SE = sPsi[eo - EX + 1], SW = sPsi[eo - EX - 1];
-        gsx = (E - Wn) * third + (NE_ + SE - NW - SW) * twelfth;
-        gsy = (N - S) * third + (NE_ + NW - SE - SW) * twelfth;
-    }
+    const float gpx = gX.x, gpy = gY.x, gsx = gX.y, gsy = gY.y, lap = lap2.x;
 
     // interface normal and the delta-function terms (Sec. 2.2, Secs. 3.1-3.2)
     const float g2 = gpx * gpx + gpy * gpy;
@@ -257,8 +357,9 @@ __global__ void __launch_bounds__(NT, 2) step_kernel(const __grid_constant__ Ste
     // EOS and surface-tension force: capillary + Marangoni, expanded form (Sec. 2.3); F_b = rho g
     float sigma, dsig;
     if (LANGMUIR) {
-        sigma = p.sigma0 * (1.f + p.E0 * log1pf(-psi));
-        dsig = -p.sigma0 * p.E0 / (1.f - psi);
+        const float om = 1.f - psi;
+        sigma = p.sigma0 * (1.f + p.E0 * __logf(om));
+        dsig = __fdividef(-p.sigma0 * p.E0, om);
     } else {
         sigma = p.sigma0 * (1.f - p.E0 * psi);
         dsig = -p.sigma0 * p.E0;
@@ -269,34 +370,34 @@ __global__ void __launch_bounds__(NT, 2) step_kernel(const __grid_constant__ Ste
     const float Fx = cap * gpx + p.mar_k * (g2 * gsgx - sdg * gpx) + p.rho * p.gx;
     const float Fy = cap * gpy + p.mar_k * (g2 * gsgy - sdg * gpy) + p.rho * p.gy;
 
+    // flow populations pulled from the staged boxes
+    float h[9];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) h[i] = Hs[(i - 1) * H_BOX + ty * BW + tx + 4 - cx(i)];
+
     // velocity: rho u = sum c_i h_i + F/2 (Sec. 3.3)
-    const float jx = h[1] - h[3] + h[5] - h[6] - h[7] + h[8];
-    const float jy = h[2] - h[4] + h[5] + h[6] - h[7] - h[8];
+    const float h13 = h[1] - h[3], h24 = h[2] - h[4], h57 = h[5] - h[7], h68 = h[6] - h[8];
+    const float jx = h13 + (h57 - h68);
+    const float jy = h24 + (h57 + h68);
     const float ux = (jx + 0.5f * Fx) * p.inv_rho;
     const float uy = (jy + 0.5f * Fy) * p.inv_rho;
 
-    // previous level: phi, psi from the own cell's post-collision populations, u from history
-    float phip = phi, psip = psi;
-    if (p.first) {
-        uxp = ux;
-        uyp = uy;
-    } else {
-        float sp = 0.f, ss = 0.f;
+    // previous level: (phi, psi) from the own cell's post-collision pairs, u from history
+    float2 pprev = pp;
+    float uxp = ux, uyp = uy;
+    if (!p.first) {
+        float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            int idx = i * NE + eo + cy(i) * EX + cx(i);
-            if (WALLS && ((cy(i) == 1 && y == p.ny - 1) || (cy(i) == -1 && y == 0))) idx = opp(i) * NE + eo;
-            sp += sF[idx];
-            ss += sG[idx];
-        }
-        phip = sp;
-        psip = ss;
+        for (int i = 0; i < 9; ++i) s = add2(s, FG[i * FG_BOX + (ty + 1 + cy(i)) * BW + tx + 4]);
+        pprev = s;
+        uxp = Hist[ty * TX + tx];
+        uyp = Hist[TX * TY + ty * TX + tx];
     }
 
-    // time derivatives, backward difference over one step
+    // time derivatives, backward difference over one step: d_t(phi u), d_t(psi u) as pairs
     const float rho = p.rho;
-    const float dt_fx = phi * ux - phip * uxp, dt_fy = phi * uy - phip * uyp;
-    const float dt_gx = psi * ux - psip * uxp, dt_gy = psi * uy - psip * uyp;
+    const float2 dtX = fma2(pp, bc(ux), mul2(pprev, bc(-uxp)));
+    const float2 dtY = fma2(pp, bc(uy), mul2(pprev, bc(-uyp)));
     const float dt_xx = rho * (ux * ux - uxp * uxp);
     const float dt_yy = rho * (uy * uy - uyp * uyp);
     const float dt_xy = rho * (ux * uy - uxp * uyp);
@@ -304,12 +405,12 @@ __global__ void __launch_bounds__(NT, 2) step_kernel(const __grid_constant__ Ste
     // pressure (Eq. for P, Sec. 3.3) with K = w0/(c^2 - cs2) = 2/3:
     //   P = 3/5 [sum_{i>0} h_i - (2/3) rho |u|^2 + (1/3) d_t(rho |u|^2)]
     const float hsum = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
-    const float P = 0.6f * (hsum - (2.f / 3.f) * rho * (ux * ux + uy * uy) + third * (dt_xx + dt_yy));
+    const float P = 0.6f * (hsum - (2.f / 3.f) * rho * (ux * ux + uy * uy) + (1.f / 3.f) * (dt_xx + dt_yy));
 
     {
         bool bad = !(isfinite(phi) && isfinite(psi) && isfinite(P)) || !(fabsf(ux) < 0.3f && fabsf(uy) < 0.3f);
         if (LANGMUIR) bad = bad || !(psi < 1.f);
-        if (bad) atomicOr(a.status, 1u);
+        if (bad) atomicOr(a.status, kStatusUnstable);
     }
 
     const size_t cell = (size_t)y * p.pitch + x;
@@ -321,76 +422,73 @@ __global__ void __launch_bounds__(NT, 2) step_kernel(const __grid_constant__ Ste
         if (a.out[3]) a.out[3][o] = uy;
         if (a.out[4]) a.out[4][o] = P;
     } else {
-
-    // ---- phase field f (Sec. 3.1): source cs2 V = d_t(phi u) + cs2 A n ----
-    {
-        float q[9];
+        // ---- f (Sec. 3.1) and g (Sec. 3.2) together; sources cs2 V = d_t(s u) + cs2 (A or B) n ----
+        {
+            const float2 vx = fma2(make_float2(Aterm, Bterm), bc(nx_ * (1.f / 3.f)), dtX);
+            const float2 vy = fma2(make_float2(Aterm, Bterm), bc(ny_ * (1.f / 3.f)), dtY);
+            collide_pair(q, pp, ux, uy, vx, vy, make_float2(p.nS1[0], p.nS1[1]), make_float2(p.nS2[0], p.nS2[1]),
+                         make_float2(p.nS3[0], p.nS3[1]), make_float2(p.nS4[0], p.nS4[1]),
+                         make_float2(p.K1[0], p.K1[1]), make_float2(p.K3[0], p.K3[1]));
+            float2* __restrict__ dfg = reinterpret_cast<float2*>(a.dst) + cell;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) q[i] = sF[i * NE + eo];
-        collide_scalar(q, phi, ux, uy, dt_fx + third * Aterm * nx_, dt_fy + third * Aterm * ny_,
-                       p.s1f, p.s2f, p.s3f, p.s4f);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) a.dst[(size_t)i * p.plane + cell] = q[i];
-    }
-    // ---- surfactant g (Sec. 3.2): source cs2 V = d_t(psi u) + cs2 B n ----
-    {
-        float q[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) q[i] = sG[i * NE + eo];
-        collide_scalar(q, psi, ux, uy, dt_gx + third * Bterm * nx_, dt_gy + third * Bterm * ny_,
-                       p.s1g, p.s2g, p.s3g, p.s4g);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) a.dst[(size_t)(kPlaneG + i) * p.plane + cell] = q[i];
-    }
-    // ---- flow h (Sec. 3.3) ----
-    {
-        const float mu = p.muB + (phi - p.phiB) * p.inv_dphi * p.dmu;
-        const float s2 = 1.f / (3.f * mu * p.inv_rho + 0.5f);
-        const float s1 = p.s1h, s3 = p.s3h, s4 = p.tie_s4h ? s2 : p.s4h;
+            for (int i = 0; i < 9; ++i) dfg[(size_t)i * p.plane] = q[i];
+        }
+        // ---- flow h (Sec. 3.3) ----
+        float s2, k2, s4, k4;
+        if (p.dmu == 0.f) {
+            s2 = p.s2h;
+            k2 = p.k2h;
+            s4 = p.s4h_eff;
+            k4 = p.k4h;
+        } else {
+            s2 = __frcp_rn(3.f * (p.muB + (phi - p.phiB) * p.inv_dphi * p.dmu) * p.inv_rho + 0.5f);
+            k2 = 1.f - 0.5f * s2;
+            s4 = p.tie_s4h ? s2 : p.s4h;
+            k4 = 1.f - 0.5f * s4;
+        }
+        const float s1 = p.s1h, s3 = p.s3h, k1 = p.k1h, k3 = p.k3h;
         const float Jx = rho * ux, Jy = rho * uy;
         // equilibrium moments: (., Jx, Jy, P + Jx ux, P + Jy uy, Jx uy, Jx/3, Jy/3, P/3 + J.u/3)
         // source moments:      (., Fx, Fy, dt_xx, dt_yy, dt_xy, Fx/3, Fy/3, (dt_xx + dt_yy)/3)
-        const float m3 = h[1] + h[3] + h[5] + h[6] + h[7] + h[8];
-        const float m4 = h[2] + h[4] + h[5] + h[6] + h[7] + h[8];
-        const float m5 = h[5] - h[6] + h[7] - h[8];
-        const float m6 = h[5] - h[6] - h[7] + h[8];
-        const float m7 = h[5] + h[6] - h[7] - h[8];
-        const float m8 = h[5] + h[6] + h[7] + h[8];
+        const float ha = h[5] + h[7], hb = h[6] + h[8];
+        const float m5 = ha - hb, m8 = ha + hb, m6 = h57 - h68, m7 = h57 + h68;
+        const float m3 = (h[1] + h[3]) + m8, m4 = (h[2] + h[4]) + m8;
         // increments dm_k = -s_k (m_k - m_eq_k) + (1 - s_k/2) m_src_k, then h* = h + M^-1 dm
-        const float d1 = -s1 * (jx - Jx) + (1.f - 0.5f * s1) * Fx;
-        const float d2 = -s1 * (jy - Jy) + (1.f - 0.5f * s1) * Fy;
-        const float d3 = -s2 * (m3 - (P + Jx * ux)) + (1.f - 0.5f * s2) * dt_xx;
-        const float d4 = -s2 * (m4 - (P + Jy * uy)) + (1.f - 0.5f * s2) * dt_yy;
-        const float d5 = -s2 * (m5 - Jx * uy) + (1.f - 0.5f * s2) * dt_xy;
-        const float d6 = -s3 * (m6 - Jx * third) + (1.f - 0.5f * s3) * Fx * third;
-        const float d7 = -s3 * (m7 - Jy * third) + (1.f - 0.5f * s3) * Fy * third;
-        const float d8 = -s4 * (m8 - third * (P + Jx * ux + Jy * uy)) + (1.f - 0.5f * s4) * third * (dt_xx + dt_yy);
-        float q[9];
-        q[1] = h[1] + 0.5f * (d1 + d3 - d6 - d8);
-        q[2] = h[2] + 0.5f * (d2 + d4 - d7 - d8);
-        q[3] = h[3] + 0.5f * (-d1 + d3 + d6 - d8);
-        q[4] = h[4] + 0.5f * (-d2 + d4 + d7 - d8);
-        q[5] = h[5] + 0.25f * (d5 + d6 + d7 + d8);
-        q[6] = h[6] + 0.25f * (-d5 - d6 + d7 + d8);
-        q[7] = h[7] + 0.25f * (d5 - d6 - d7 + d8);
-        q[8] = h[8] + 0.25f * (-d5 + d6 - d7 + d8);
+        const float d1 = k1 * Fx - s1 * (jx - Jx);
+        const float d2 = k1 * Fy - s1 * (jy - Jy);
+        const float d3 = k2 * dt_xx - s2 * (m3 - (P + Jx * ux));
+        const float d4 = k2 * dt_yy - s2 * (m4 - (P + Jy * uy));
+        const float d5 = k2 * dt_xy - s2 * (m5 - Jx * uy);
+        const float d6 = (1.f / 3.f) * (k3 * Fx - s3 * (3.f * m6 - Jx));
+        const float d7 = (1.f / 3.f) * (k3 * Fy - s3 * (3.f * m7 - Jy));
+        const float d8 = (1.f / 3.f) * (k4 * (dt_xx + dt_yy) - s4 * (3.f * m8 - (P + Jx * ux + Jy * uy)));
+        const float A = d1 - d6, B = d3 - d8, C = d2 - d7, D = d4 - d8;
+        const float E = d8 + d5, F = d8 - d5, G = d6 + d7, H = d7 - d6;
+        h[1] += 0.5f * (A + B);
+        h[3] += 0.5f * (B - A);
+        h[2] += 0.5f * (C + D);
+        h[4] += 0.5f * (D - C);
+        h[5] += 0.25f * (E + G);
+        h[7] += 0.25f * (E - G);
+        h[6] += 0.25f * (F + H);
+        h[8] += 0.25f * (F - H);
         if (WALLS) {
             // moving-wall term for the links that leave through a wall, folded in before storing:
             // h_ibar(x_b, t+1) = h*_i(x_b, t) - 2 w_i rho c_i.u_w / cs2
             if (y == 0) {
-                q[7] -= 6.f * wgt(7) * rho * (-1.f) * p.u_bot;
-                q[8] -= 6.f * wgt(8) * rho * (1.f) * p.u_bot;
+                h[7] -= 6.f * wgt(7) * rho * (-1.f) * p.u_bot;
+                h[8] -= 6.f * wgt(8) * rho * (1.f) * p.u_bot;
             }
             if (y == p.ny - 1) {
-                q[5] -= 6.f * wgt(5) * rho * (1.f) * p.u_top;
-                q[6] -= 6.f * wgt(6) * rho * (-1.f) * p.u_top;
+                h[5] -= 6.f * wgt(5) * rho * (1.f) * p.u_top;
+                h[6] -= 6.f * wgt(6) * rho * (-1.f) * p.u_top;
             }
         }
+        float* __restrict__ dh = a.dst + (size_t)kPlaneH * p.plane + cell;
 #pragma unroll
-        for (int i = 1; i < 9; ++i) a.dst[(size_t)(kPlaneH + i - 1) * p.plane + cell] = q[i];
-    }
-    a.hist[cell] = ux;
-    a.hist[p.plane + cell] = uy;
+        for (int i = 1; i < 9; ++i) dh[(size_t)(i - 1) * p.plane] = h[i];
+        a.hist[cell] = ux;
+        a.hist[p.plane + cell] = uy;
     }
 }
 
@@ -418,9 +516,11 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
     const double phi = a.phi[o], psi = a.psi[o], ux = a.ux[o], uy = a.uy[o], P = a.P[o];
     bool bad = !(isfinite(phi) && isfinite(psi) && isfinite(ux) && isfinite(uy) && isfinite(P));
     if (a.langmuir) bad = bad || !(psi < 1.0);
-    if (bad) atomicOr(a.status, 1u);
+    if (bad) atomicOr(a.status, kStatusUnstable);
     const double rho = p.rho;
     const double uu = ux * ux + uy * uy;
+    float2* fg = reinterpret_cast<float2*>(a.dst);
+    float* hp = a.dst + (size_t)kPlaneH * p.plane;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const double cu = cx(i) * ux + cy(i) * uy;
@@ -430,17 +530,18 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
         const double heq = w * (3.0 * P + 3.0 * rho * cu + 4.5 * rho * (cu * cu - uu / 3.0));
         // the first pull at x for direction i reads slot i of x - c_i, or, across a wall, the
         // opposite slot of x itself
-        int tx_ = x - cx(i), ty_ = y - cy(i), plane = i;
+        int tx_ = x - cx(i), ty_ = y - cy(i), slot = i;
         if (a.walls && (ty_ < 0 || ty_ >= p.ny)) {
-            tx_ = x; ty_ = y; plane = opp(i);
+            tx_ = x;
+            ty_ = y;
+            slot = opp(i);
         } else {
             tx_ = (tx_ + p.nx) % p.nx;
             ty_ = (ty_ + p.ny) % p.ny;
         }
         const size_t cell = (size_t)ty_ * p.pitch + tx_;
-        a.dst[(size_t)plane * p.plane + cell] = (float)feq;
-        a.dst[(size_t)(kPlaneG + plane) * p.plane + cell] = (float)geq;
-        if (plane != 0) a.dst[(size_t)(kPlaneH + plane - 1) * p.plane + cell] = (float)heq;
+        fg[(size_t)slot * p.plane + cell] = make_float2((float)feq, (float)geq);
+        if (slot != 0) hp[(size_t)(slot - 1) * p.plane + cell] = (float)heq;
     }
     const size_t cell = (size_t)y * p.pitch + x;
     a.hist[cell] = (float)ux;
@@ -448,7 +549,7 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
 }
 
 // ---- FP64 sums of phi or psi: every population slot is pulled exactly once per step, so the
-// total of a field is the plain sum of its 9 planes over the valid cells ----
+// total of a field is the plain sum of one lane of the 9 pair planes over the valid cells ----
 constexpr int kReduceThreads = 256;
 constexpr int kMaxPartials = 1024;
 
@@ -467,16 +568,17 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
     return v;
 }
 
-__global__ void __launch_bounds__(kReduceThreads) reduce_partial_kernel(const float* __restrict__ planes, int nx,
-                                                                        int ny, int pitch, long long plane,
+// lane 0 sums f (phi), lane 1 sums g (psi)
+__global__ void __launch_bounds__(kReduceThreads) reduce_partial_kernel(const float* __restrict__ pairs, int lane,
+                                                                        int nx, int ny, int pitch, long long plane,
                                                                         double* __restrict__ partials) {
     __shared__ double smem[32];
     double acc = 0.0;
-    // block b owns rows b, b + gridDim.x, ...; threads stride over (plane, x)
+    // block b owns rows b, b + gridDim.x, ...; threads stride over (pair plane, x)
     for (int y = blockIdx.x; y < ny; y += gridDim.x) {
-        for (int k = threadIdx.x; k < 9 * nx; k += blockDim.x) {
+        for (int k = threadIdx.x; k < kPairs * nx; k += blockDim.x) {
             const int i = k / nx, x = k - i * nx;
-            acc += (double)planes[(size_t)i * plane + (size_t)y * pitch + x];
+            acc += (double)pairs[2 * ((size_t)i * plane + (size_t)y * pitch + x) + lane];
         }
     }
     acc = block_sum(acc, smem);
