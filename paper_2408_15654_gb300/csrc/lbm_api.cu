@@ -506,12 +506,13 @@ int lbm_set_state(lbm_handle* h, const void* host_blob, size_t bytes) {
     if (hd.magic != kStateMagic || hd.nx != h->prm.nx || hd.ny != h->prm.ny || hd.pitch != h->L.pitch)
         return fail(LBM_EINVAL, "state blob does not match this handle");
     const size_t pb = h->L.plane * lbm::kPlanes * sizeof(float);
-    LBM_CUDA(cudaMemcpyAsync(h->pops[0], b + sizeof(hd), pb, cudaMemcpyHostToDevice, h->stream));
+    const int cur = (int)(hd.steps & 1);  // the current state after k steps is buffer k mod 2
+    LBM_CUDA(cudaMemcpyAsync(h->pops[cur], b + sizeof(hd), pb, cudaMemcpyHostToDevice, h->stream));
     LBM_CUDA(cudaMemcpyAsync(h->hist, b + sizeof(hd) + pb, 2 * h->L.plane * sizeof(float), cudaMemcpyHostToDevice,
                              h->stream));
     LBM_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
-    h->cur = 0;
+    h->cur = cur;
     h->first = hd.first;
     h->steps = hd.steps;
     h->initialized = 1;
