@@ -93,9 +93,14 @@ typedef struct lbm_params {
 
 typedef struct lbm_handle lbm_handle;
 
-/* Bytes of device workspace lbm_create needs for these parameters: two population buffers of
- * 26 float planes (f0..f8, g0..g8, h1..h8; h0 never influences the step), the 2-plane velocity
- * history, a status word and the reduction partials.  Returns LBM_EINVAL for bad parameters. */
+/* Bytes of device workspace lbm_create needs for these parameters: two population buffers, the
+ * 2-plane velocity history, a status word and the reduction partials.  Returns LBM_EINVAL for
+ * bad parameters.
+ * Layout: the workspace starts with the two population buffers, each 26 * ny * pitch * 4 bytes
+ * rounded up to a multiple of 256, with pitch = nx rounded up to a multiple of 32.  A buffer holds
+ * 9 planes of (f_i, g_i) float pairs followed by 8 float planes h_1..h_8 (h_0 never influences the
+ * step), each plane ny rows of pitch cells.  After lbm_init_fields and k steps the current state is
+ * buffer k mod 2 (buffer 0 at offset 0). */
 int lbm_workspace_bytes(const lbm_params* p, size_t* bytes);
 
 /* Create a handle on the current CUDA device.
@@ -133,6 +138,30 @@ int lbm_get_moments(lbm_handle* h, unsigned mask, double* const out[5], int mem)
  * Both sums are conserved by the method (sum F_i = sum G_i = 0).  *out is host memory.
  * Synchronous. */
 int lbm_reduce(lbm_handle* h, int what, double* out);
+
+/* The sum of lbm_reduce for callers that cannot allocate device memory.  (This entry point has no
+ * counterpart in the paper; it exists for the library's users.)  Some callers may not call
+ * cudaMalloc: a plugin inside a host application whose memory manager owns all device memory, code
+ * that must not add an allocation (and its implicit synchronisation) while other work is in
+ * flight, or a process that has spent its allocation budget.  Such a caller cannot provide the
+ * workspace of lbm_create, but it may hold a population buffer in this library's layout (see
+ * lbm_workspace_bytes), e.g. the current buffer of another component's handle or a checkpoint
+ * already in device memory.  This call sums phi (LBM_SUM_PHI) or psi (LBM_SUM_PSI) of that buffer
+ * in FP64 exactly like lbm_reduce, with its partial sums in a fixed device array compiled into the
+ * library instead of a workspace.
+ *   d_pops: device pointer to one population buffer of an nx x ny grid (read only).
+ *   out:    host memory, receives the sum.
+ *   cuda_stream: stream on which the work is enqueued; the call waits for it (synchronous).
+ * Limit: ny <= LBM_NOALLOC_MAX_ROWS (one partial sum per row); larger grids return LBM_EINVAL
+ * with a message.  nx >= 2, ny >= 2, nx * ny <= 2^30.
+ * The fixed array (LBM_NOALLOC_MAX_ROWS + 1 doubles, about 64 KB) exists once per GPU that loads
+ * the library and stays there until the process exits.  The first call on each device looks up
+ * its address (with that device current), so make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (other streams, other threads) race and
+ * must be serialised by the caller.  Each call writes every entry it reads, so nothing carries over
+ * from the previous call.  No device memory is allocated or freed. */
+#define LBM_NOALLOC_MAX_ROWS 8192
+int lbm_reduce_noalloc(const void* d_pops, int nx, int ny, int what, void* cuda_stream, double* out);
 
 /* LBM_OK, or LBM_EUNSTABLE if the device has flagged an unstable state since lbm_init_fields.
  * Synchronous. */

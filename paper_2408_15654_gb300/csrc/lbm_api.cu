@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -283,7 +284,58 @@ int status_code(unsigned st) {
 
 }  // namespace
 
+// Fixed scratch of lbm_reduce_noalloc: one FP64 partial per row plus the result.
+static __device__ __align__(256) double g_noalloc_partials[LBM_NOALLOC_MAX_ROWS + 1];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the fixed scratch on the current device, looked up once per device.
+int noalloc_scratch(double** out) {
+    int dev = 0;
+    LBM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(LBM_EINVAL, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+    }
+    *out = g_noalloc_ptr[dev];
+    return LBM_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+int lbm_reduce_noalloc(const void* d_pops, int nx, int ny, int what, void* cuda_stream, double* out) {
+    g_err.clear();
+    if (!d_pops || !out) return fail(LBM_EINVAL, "d_pops and out are required");
+    if (nx < 2 || ny < 2 || (long long)nx * ny > (1LL << 30))
+        return fail(LBM_EINVAL, "grid %d x %d outside 2 <= nx, ny and nx * ny <= 2^30", nx, ny);
+    if (ny > LBM_NOALLOC_MAX_ROWS)
+        return fail(LBM_EINVAL, "ny = %d exceeds the %d rows that the fixed scratch of lbm_reduce_noalloc holds", ny,
+                    LBM_NOALLOC_MAX_ROWS);
+    if (what != LBM_SUM_PHI && what != LBM_SUM_PSI) return fail(LBM_EINVAL, "bad reduction selector");
+    double* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    const int pitch = (nx + 31) / 32 * 32;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    lbm::reduce_partial_kernel<<<ny, lbm::kReduceThreads, 0, stream>>>(
+        static_cast<const float*>(d_pops), what == LBM_SUM_PSI ? 1 : 0, nx, ny, pitch, (long long)ny * pitch, scratch);
+    LBM_CUDA(cudaGetLastError());
+    lbm::reduce_final_kernel<<<1, lbm::kReduceThreads, 0, stream>>>(scratch, ny, scratch + LBM_NOALLOC_MAX_ROWS);
+    LBM_CUDA(cudaGetLastError());
+    LBM_CUDA(cudaMemcpyAsync(out, scratch + LBM_NOALLOC_MAX_ROWS, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    LBM_CUDA(cudaStreamSynchronize(stream));
+    return LBM_OK;
+}
 
 int lbm_workspace_bytes(const lbm_params* p, size_t* bytes) {
     g_err.clear();

@@ -20,11 +20,12 @@ LBM_STORE_FP32 = 0
 LBM_MEM_HOST, LBM_MEM_DEVICE = 0, 1
 LBM_PHI, LBM_PSI, LBM_UX, LBM_UY, LBM_P = 1, 2, 4, 8, 16
 LBM_SUM_PHI, LBM_SUM_PSI = 0, 1
+LBM_NOALLOC_MAX_ROWS = 8192
 FIELDS = ("phi", "psi", "ux", "uy", "P")
 
 # Symbols declared in include/lbm.h (checked by the tests against the header and the library).
 EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_init_fields", "lbm_step", "lbm_get_moments",
-           "lbm_reduce", "lbm_status", "lbm_state_bytes", "lbm_get_state", "lbm_set_state",
+           "lbm_reduce", "lbm_reduce_noalloc", "lbm_status", "lbm_state_bytes", "lbm_get_state", "lbm_set_state",
            "lbm_steps_taken", "lbm_destroy", "lbm_last_error")
 
 
@@ -65,6 +66,7 @@ def load(path: str | None = None):
         "lbm_step": [vp, C.c_int64],
         "lbm_get_moments": [vp, C.c_uint, C.POINTER(vp), C.c_int],
         "lbm_reduce": [vp, C.c_int, dp],
+        "lbm_reduce_noalloc": [vp, C.c_int, C.c_int, C.c_int, vp, dp],
         "lbm_status": [vp],
         "lbm_state_bytes": [vp, C.POINTER(sz)],
         "lbm_get_state": [vp, vp, sz],
@@ -145,6 +147,13 @@ def lbm_get_moments(h: int, mask: int, outs, mem: int = LBM_MEM_HOST):
 def lbm_reduce(h: int, what: int) -> float:
     v = C.c_double()
     _check(load().lbm_reduce(C.c_void_p(h), what, C.byref(v)))
+    return v.value
+
+
+def lbm_reduce_noalloc(d_pops: int, nx: int, ny: int, what: int, stream_ptr: int) -> float:
+    v = C.c_double()
+    _check(load().lbm_reduce_noalloc(C.c_void_p(d_pops), int(nx), int(ny), int(what), C.c_void_p(stream_ptr),
+                                     C.byref(v)))
     return v.value
 
 
