@@ -254,11 +254,24 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
     const dim3 grid(h->tiles_x, h->tiles_y), block(lbm::NT);
     const size_t smem = lbm::kSmemBytes;
     const bool walls = h->prm.bc_y == LBM_BC_WALLS, lang = h->prm.eos == LBM_EOS_LANGMUIR;
+    // Programmatic dependent launch: the step kernel waits (griddepcontrol.wait) for the previous
+    // grid before touching memory, so the next launch may be scheduled during this one's tail.
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     using namespace lbm;
 #define LBM_LAUNCH(W_, L_)                                                                        \
     do {                                                                                          \
-        if (mode == kStep) step_kernel<W_, L_, kStep><<<grid, block, smem, h->stream>>>(a);       \
-        else step_kernel<W_, L_, kMoments><<<grid, block, smem, h->stream>>>(a);                  \
+        if (mode == kStep) LBM_CUDA(cudaLaunchKernelEx(&cfg, step_kernel<W_, L_, kStep>, a));     \
+        else LBM_CUDA(cudaLaunchKernelEx(&cfg, step_kernel<W_, L_, kMoments>, a));                \
     } while (0)
     if (walls && lang) LBM_LAUNCH(true, true);
     else if (walls) LBM_LAUNCH(true, false);

@@ -259,11 +259,21 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + SM_BAR);
     const Phys& p = a.p;
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    // The first and the last tile row (whose boxes need edge patching, and so run longest) are
+    // launched first, so that the last wave holds interior tiles only.
+    const int ntr = gridDim.y;
+    const int tr = blockIdx.y == 0 ? 0 : (blockIdx.y == 1 ? ntr - 1 : (int)blockIdx.y - 1);
+    const int x0 = blockIdx.x * TX, y0 = tr * TY;
 
     if (t == 0) {
         mbar_init(mbar, 1);
         fence_mbar_init();
+    }
+    // Programmatic dependent launch: let the next step's CTAs be scheduled into the slots this
+    // grid frees, and wait here until the previous step's writes are complete and visible.
+    cudaTriggerProgrammaticLaunchCompletion();
+    cudaGridDependencySynchronize();
+    if (t == 0) {
         mbar_expect_tx(mbar, kTileBytes);
 #pragma unroll
         for (int i = 0; i < kPairs; ++i) tma_load_3d(FG + i * FG_BOX, &a.tm_fg, x0 - 4, y0 - 1 - cy(i), i, mbar);
@@ -408,8 +418,10 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     const float P = 0.6f * (hsum - (2.f / 3.f) * rho * (ux * ux + uy * uy) + (1.f / 3.f) * (dt_xx + dt_yy));
 
     {
-        bool bad = !(isfinite(phi) && isfinite(psi) && isfinite(P)) || !(fabsf(ux) < 0.3f && fabsf(uy) < 0.3f);
-        if (LANGMUIR) bad = bad || !(psi < 1.f);
+        // |u| >= 0.3, or a non-finite value (NaN fails every comparison; a NaN anywhere in the
+        // cell reaches u, phi or psi within a step), or psi >= 1 under the Langmuir EOS
+        bool bad = !(fabsf(ux) < 0.3f) | !(fabsf(uy) < 0.3f) | !(fabsf(phi) < 1e30f) | !(fabsf(psi) < 1e30f);
+        if (LANGMUIR) bad |= !(psi < 1.f);
         if (bad) atomicOr(a.status, kStatusUnstable);
     }
 
