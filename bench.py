@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 NX, NY = 2048, 1024
 BYTES_PER_LUP = 26 * 4 * 2 + 2 * 4 * 2  # 26 live float populations and 2 history floats, read + written
+BYTES_PER_LUP_16 = 26 * 2 * 2 + 2 * 4 * 2  # the same populations stored in 16 bits
 METRIC = "MLUPS (3 lattices) and % HBM roofline, FP32 vs half-store; serving p50/p99"
 WORKLOAD = "sheared drop 2048x1024 (R=160, Re=1, Ca=0.2, Langmuir E0=0.2, psi0=0.3), FP32 storage"
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_2048x1024_fp32.json")
@@ -233,6 +234,29 @@ def run_ours(args):
         raise RuntimeError(f"unstable state during the benchmark: {lbm.lbm_last_error()}")
     value = cells * args.steps * world / (ms_max * 1e-3) / 1e6
 
+    # the same workload with 16-bit population storage (FP32 arithmetic)
+    half = {}
+    for st in ("fp16", "bf16"):
+        hs = lbm.Lattice(dict(p, storage=st), stream=stream)
+        hs.init(**f)
+        hs.step(args.warmup)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hs.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        hms = barrier_max(e0.elapsed_time(e1), world)
+        if hs.status != lbm.LBM_OK:
+            raise RuntimeError(f"unstable state in the {st} benchmark: {lbm.lbm_last_error()}")
+        hv = cells * args.steps * world / (hms * 1e-3) / 1e6
+        hach = cells * BYTES_PER_LUP_16 / (e0.elapsed_time(e1) / args.steps * 1e-3) / 1e9
+        half[st] = {"value": hv, "unit": "MLUPS", "ratio_vs_fp32": hv / (cells * args.steps * world / (ms_max * 1e-3) / 1e6),
+                    "ms_per_step": hms / args.steps, "achieved_gbs": hach,
+                    "frac_of_measured_hbm": hach / measured_peak()[0], "algorithmic_bytes_per_lup": BYTES_PER_LUP_16}
+        hs.close()
+
     # roofline of the step kernel (one launch per step, so launch duration = step time)
     peak, peak_kind = measured_peak()
     launch_s = ms / args.steps * 1e-3
@@ -265,11 +289,13 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_lup": BYTES_PER_LUP},
+            "half_store": half,
             "cpu_baseline": base,
             "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": io_bytes / args.steps,
                     "d2h_bytes_per_step": io_bytes / args.steps,
                     "job": f"lbm_init_fields(host) + lbm_step({args.steps}) + lbm_get_moments(host, all 5)"},
             "gpu_launches": args.steps,
+            "gpu_launches_half_store": 2 * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -50,6 +50,8 @@ extern "C" {
 #define LBM_EOS_LANGMUIR 1  /* sigma = sigma0 [1 + E0 ln(1 - psi)]    (Sec. 2.3, Langmuir EOS) */
 
 #define LBM_STORE_FP32 0    /* populations stored as float                                   */
+#define LBM_STORE_FP16 1    /* as FP16 deviations from references (see lbm_workspace_bytes) */
+#define LBM_STORE_BF16 2    /* as BF16 deviations from references                            */
 
 #define LBM_MEM_HOST 0      /* pointer arguments are host memory (pageable or pinned)        */
 #define LBM_MEM_DEVICE 1    /* pointer arguments are device memory on the handle's device    */
@@ -70,13 +72,13 @@ extern "C" {
  *   1/s1^f = M_phi/cs2 + 1/2,  1/s1^g = D/cs2 + 1/2 (Eq. for s1^g),  1/s2^h = mu/(rho cs2) + 1/2.
  * A value s_h[4] <= 0 means s4^h = s2^h (recommended: keeps plane Couette flow exact).
  * Requirements: nx >= 2, ny >= 2, phiA != phiB, W > 0, M_phi > 0, D > 0, rhoA = rhoB > 0,
- * muA, muB > 0, all rates in (0, 2) (s_h[4] may be <= 0), storage = LBM_STORE_FP32.
+ * muA, muB > 0, all rates in (0, 2) (s_h[4] may be <= 0), storage one of LBM_STORE_*.
  * (Density ratio != 1 is not supported by this build: lbm_create returns LBM_EINVAL.)        */
 typedef struct lbm_params {
     int32_t nx, ny;         /* grid size                                                     */
     int32_t bc_y;           /* LBM_BC_PERIODIC or LBM_BC_WALLS                               */
     int32_t eos;            /* LBM_EOS_LINEAR or LBM_EOS_LANGMUIR                            */
-    int32_t storage;        /* LBM_STORE_FP32                                                */
+    int32_t storage;        /* LBM_STORE_FP32, LBM_STORE_FP16 or LBM_STORE_BF16              */
     int32_t reserved;       /* must be 0                                                     */
     double u_top, u_bot;    /* x velocity of the top and bottom wall (LBM_BC_WALLS)          */
     double phiA, phiB;      /* order parameter of the pure phases (Sec. 2.1)                 */
@@ -93,14 +95,23 @@ typedef struct lbm_params {
 
 typedef struct lbm_handle lbm_handle;
 
-/* Bytes of device workspace lbm_create needs for these parameters: two population buffers, the
- * 2-plane velocity history, a status word and the reduction partials.  Returns LBM_EINVAL for
- * bad parameters.
- * Layout: the workspace starts with the two population buffers, each 26 * ny * pitch * 4 bytes
- * rounded up to a multiple of 256, with pitch = nx rounded up to a multiple of 32.  A buffer holds
- * 9 planes of (f_i, g_i) float pairs followed by 8 float planes h_1..h_8 (h_0 never influences the
- * step), each plane ny rows of pitch cells.  After lbm_init_fields and k steps the current state is
- * buffer k mod 2 (buffer 0 at offset 0). */
+/* Bytes of device workspace lbm_create needs for these parameters: two population buffers, two
+ * velocity-history buffers, a status word and the reduction partials.  Returns LBM_EINVAL for bad
+ * parameters.
+ * Layout: the workspace starts with the two population buffers, each B * ny * pitch bytes rounded
+ * up to a multiple of 256, with pitch = nx rounded up to a multiple of 32 and B = 104 (FP32
+ * storage) or 52 (16-bit storage).  A buffer holds 9 planes of (f_i, g_i) pairs followed by 8
+ * planes h_1..h_8 (h_0 never influences the step), each plane ny rows of pitch cells; after
+ * lbm_init_fields and k steps the current state is buffer k mod 2 (buffer 0 at offset 0).
+ * FP32 storage holds the values.  16-bit storage (FP16 / BF16, arithmetic still FP32) holds
+ * each value divided by its lattice weight w_i, as a scaled deviation from a reference:
+ * (f_i / w_i - phi_ref) S_f and (g_i / w_i) S_g with phi_ref = (phiA + phiB)/2, and
+ * (h_i / w_i - 3 rho c_i.u) S_h with u the velocity that the cell holding the slot wrote to the
+ * velocity history in the same step; S = (1, 256, 4096) for FP16 and 1 for BF16.  Dividing by
+ * w_i makes the bulk equilibria exactly representable; removing 3 rho c_i.u keeps the pressure
+ * part of h (about 1e-5) above the 16-bit rounding of the velocity part (about 1e-3).  The
+ * velocity history (two buffers of ny x pitch float pairs, alternating like the populations)
+ * follows the population buffers. */
 int lbm_workspace_bytes(const lbm_params* p, size_t* bytes);
 
 /* Create a handle on the current CUDA device.
@@ -149,7 +160,7 @@ int lbm_reduce(lbm_handle* h, int what, double* out);
  * already in device memory.  This call sums phi (LBM_SUM_PHI) or psi (LBM_SUM_PSI) of that buffer
  * in FP64 exactly like lbm_reduce, with its partial sums in a fixed device array compiled into the
  * library instead of a workspace.
- *   d_pops: device pointer to one population buffer of an nx x ny grid (read only).
+ *   d_pops: device pointer to one FP32-storage population buffer of an nx x ny grid (read only).
  *   out:    host memory, receives the sum.
  *   cuda_stream: stream on which the work is enqueued; the call waits for it (synchronous).
  * Limit: ny <= LBM_NOALLOC_MAX_ROWS (one partial sum per row); larger grids return LBM_EINVAL

@@ -1,7 +1,7 @@
 // Host implementation of the C ABI declared in include/lbm.h.
 //
 // The library owns no device memory: the caller passes one workspace, carved here into
-//   [pops A | pops B | u history | status word | reduction partials]
+//   [pops A | pops B | u history A | u history B | status word | reduction partials]
 // every part 256-byte aligned.  Between steps the population buffer that is not current is dead
 // (the next step overwrites all of it), so host transfers stage through it.
 #include <cmath>
@@ -14,7 +14,7 @@
 #include <string>
 
 #include "lbm.h"
-#include "lbm_kernels.cuh"
+#include "lbm_launch.h"
 
 namespace {
 
@@ -55,49 +55,32 @@ int get_encoder(EncodeTiledFn* fn) {
     return LBM_OK;
 }
 
-// 3-D tensor map {nx, ny, planes} of 4-byte floats or 8-byte (f, g) pairs; pitch and plane
-// stride counted in elements.
-int encode_map(CUtensorMap* tm, void* base, bool pairs, int nx, int ny, int planes, int pitch, size_t plane,
+// 3-D tensor map {nx, ny, planes} of elements of es bytes (8: float pairs, 4: floats or
+// 16-bit pairs, 2: 16-bit values); pitch and plane stride counted in elements.
+int encode_map(CUtensorMap* tm, void* base, int es, int nx, int ny, int planes, int pitch, size_t plane,
                unsigned bw, unsigned bh, unsigned bp) {
     EncodeTiledFn enc;
     int rc = get_encoder(&enc);
     if (rc) return rc;
-    const cuuint64_t es = pairs ? 8 : 4;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
     const cuuint64_t strides[2] = {(cuuint64_t)pitch * es, (cuuint64_t)plane * es};
     const cuuint32_t box[3] = {bw, bh, bp};
     const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(tm, pairs ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
+    const CUtensorMapDataType dt = es == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64
+                                   : (es == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16);
+    CUresult r = enc(tm, dt, 3, base, dims,
                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(LBM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return LBM_OK;
 }
 
-template <bool W_, bool L_, int M_>
-cudaError_t prepare_kernel(int* blocks_per_sm) {
-    auto k = lbm::step_kernel<W_, L_, M_>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lbm::kSmemBytes);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, lbm::NT, lbm::kSmemBytes);
-}
-
-// Opt every step-kernel instance into its dynamic shared memory; resident CTAs per SM.
-int prepare_kernels(int* blocks_per_sm) {
-    int b[8];
-    cudaError_t e = prepare_kernel<false, false, lbm::kStep>(&b[0]);
-    if (e == cudaSuccess) e = prepare_kernel<false, true, lbm::kStep>(&b[1]);
-    if (e == cudaSuccess) e = prepare_kernel<true, false, lbm::kStep>(&b[2]);
-    if (e == cudaSuccess) e = prepare_kernel<true, true, lbm::kStep>(&b[3]);
-    if (e == cudaSuccess) e = prepare_kernel<false, false, lbm::kMoments>(&b[4]);
-    if (e == cudaSuccess) e = prepare_kernel<false, true, lbm::kMoments>(&b[5]);
-    if (e == cudaSuccess) e = prepare_kernel<true, false, lbm::kMoments>(&b[6]);
-    if (e == cudaSuccess) e = prepare_kernel<true, true, lbm::kMoments>(&b[7]);
+// Opt the step-kernel instances of storage mode st into their shared memory; CTAs per SM.
+int prepare_kernels(int st, int* blocks_per_sm) {
+    cudaError_t e = st == LBM_STORE_FP32 ? lbm::prepare_step_fp32(blocks_per_sm)
+                    : (st == LBM_STORE_FP16 ? lbm::prepare_step_fp16(blocks_per_sm) : lbm::prepare_step_bf16(blocks_per_sm));
     if (e != cudaSuccess) return fail(LBM_ECUDA, "kernel setup: %s", cudaGetErrorString(e));
-    int m = b[0];
-    for (int k = 1; k < 8; ++k) m = b[k] < m ? b[k] : m;
-    if (m < 1) return fail(LBM_ECUDA, "the step kernel does not fit on an SM");
-    *blocks_per_sm = m;
+    if (*blocks_per_sm < 1) return fail(LBM_ECUDA, "the step kernel does not fit on an SM");
     return LBM_OK;
 }
 
@@ -108,7 +91,7 @@ struct Layout {
     int pitch;
     size_t plane;       // floats per plane
     size_t pops_bytes;  // one population buffer
-    size_t off_pops[2], off_hist, off_status, off_partials, total;
+    size_t off_pops[2], off_hist[2], off_status, off_partials, total;
 };
 
 bool rate_ok(double s) { return s > 0.0 && s < 2.0; }
@@ -119,7 +102,8 @@ int validate(const lbm_params* p) {
     if ((long long)p->nx * p->ny > (1LL << 30)) return fail(LBM_EINVAL, "grid too large");
     if (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_WALLS) return fail(LBM_EINVAL, "bad bc_y");
     if (p->eos != LBM_EOS_LINEAR && p->eos != LBM_EOS_LANGMUIR) return fail(LBM_EINVAL, "bad eos");
-    if (p->storage != LBM_STORE_FP32) return fail(LBM_EINVAL, "storage mode %d not supported", p->storage);
+    if (p->storage != LBM_STORE_FP32 && p->storage != LBM_STORE_FP16 && p->storage != LBM_STORE_BF16)
+        return fail(LBM_EINVAL, "storage mode %d not supported", p->storage);
     if (p->reserved != 0) return fail(LBM_EINVAL, "reserved must be 0");
     if (!(p->phiA != p->phiB) || !(p->W > 0) || !(p->M_phi > 0) || !(p->D > 0))
         return fail(LBM_EINVAL, "need phiA != phiB, W > 0, M_phi > 0, D > 0");
@@ -148,11 +132,12 @@ Layout layout_of(const lbm_params* p) {
     Layout L;
     L.pitch = (p->nx + 31) / 32 * 32;
     L.plane = (size_t)p->ny * L.pitch;
-    L.pops_bytes = align_up(L.plane * lbm::kPlanes * sizeof(float));
+    L.pops_bytes = align_up(L.plane * (size_t)lbm::pop_bytes_per_cell(p->storage));
     size_t off = 0;
     L.off_pops[0] = off; off += L.pops_bytes;
     L.off_pops[1] = off; off += L.pops_bytes;
-    L.off_hist = off; off += align_up(2 * L.plane * sizeof(float));
+    L.off_hist[0] = off; off += align_up(L.plane * sizeof(float2));
+    L.off_hist[1] = off; off += align_up(L.plane * sizeof(float2));
     L.off_status = off; off += kAlign;
     L.off_partials = off; off += align_up(lbm::kMaxPartials * sizeof(double) + sizeof(double));
     L.total = off;
@@ -207,6 +192,28 @@ lbm::Phys make_phys(const lbm_params* p, const Layout& L) {
     f.s4h_eff = (float)s4h;
     f.k4h = (float)(1.0 - 0.5 * s4h);
     f.tie_s4h = p->s_h[4] <= 0.0 ? 1 : 0;
+    // 16-bit storage: values divided by their weight, as deviations from references, times
+    // power-of-two scales that keep them normal in FP16 (BF16 has the FP32 exponent range)
+    const bool fp16 = p->storage == LBM_STORE_FP16;
+    const double S_f = 1.0, S_g = fp16 ? 256.0 : 1.0, S_h = fp16 ? 4096.0 : 1.0;
+    const double phi_ref = 0.5 * (p->phiA + p->phiB);
+    for (int i = 0; i < 9; ++i) {
+        const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+        f.dec_f[i] = (float)(w / S_f);
+        f.dec_g[i] = (float)(w / S_g);
+        f.enc_f[i] = (float)(S_f / w);
+        f.enc_g[i] = (float)(S_g / w);
+        f.ref_f[i] = (float)(w * phi_ref);
+        f.dec_h[i] = (float)(w / S_h);
+        f.enc_h[i] = (float)(S_h / w);
+    }
+    f.eref_f = (float)(-phi_ref * S_f);
+    f.kh_axis = (float)(3.0 / 9.0 * p->rhoA);
+    f.kh_diag = (float)(3.0 / 36.0 * p->rhoA);
+    f.kh_enc = (float)(3.0 * p->rhoA * S_h);
+    f.phi_ref = (float)phi_ref;
+    f.isc_f = (float)(1.0 / S_f);
+    f.isc_g = (float)(1.0 / S_g);
     f.u_top = (float)p->u_top;
     f.u_bot = (float)p->u_bot;
     f.n_eps2 = (float)(p->n_eps * p->n_eps);
@@ -221,13 +228,13 @@ struct lbm_handle {
     lbm::Phys phys;
     cudaStream_t stream;
     char* ws;
-    float* pops[2];
-    float* hist;
+    void* pops[2];
+    float2* hist[2];         // u history, alternating with the population buffers
     unsigned* status;
     double* partials;
     CUtensorMap tm_fg[2];    // TMA descriptors of the (f, g) pair planes of each buffer
     CUtensorMap tm_h[2];     // TMA descriptors of the h planes of each buffer
-    CUtensorMap tm_hist;     // TMA descriptor of the u history
+    CUtensorMap tm_hist[2];  // TMA descriptors of the u history buffers
     int tiles_x, tiles_y;    // step-kernel grid: one TX x TY tile per CTA
     int cur;          // buffer holding the current state
     int initialized;
@@ -242,42 +249,48 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
     std::memset(&a, 0, sizeof(a));
     a.tm_fg = h->tm_fg[h->cur];
     a.tm_h = h->tm_h[h->cur];
-    a.tm_hist = h->tm_hist;
+    a.tm_hist = h->tm_hist[h->cur];
     a.p = h->phys;
     a.p.first = h->first;
     a.src = h->pops[h->cur];
     a.dst = h->pops[h->cur ^ 1];
-    a.hist = h->hist;
+    a.hist_src = h->hist[h->cur];
+    a.hist_dst = h->hist[h->cur ^ 1];
     a.status = h->status;
+    {
+        // per-step salt of the stochastic rounding (a function of the step count, so a restored
+        // checkpoint continues bit for bit)
+        uint64_t z = (uint64_t)h->steps * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ull;
+        a.seed = (unsigned)(z ^ (z >> 29));
+    }
     if (out)
         for (int k = 0; k < 5; ++k) a.out[k] = out[k];
-    const dim3 grid(h->tiles_x, h->tiles_y), block(lbm::NT);
-    const size_t smem = lbm::kSmemBytes;
+    const dim3 grid(h->tiles_x, h->tiles_y);
     const bool walls = h->prm.bc_y == LBM_BC_WALLS, lang = h->prm.eos == LBM_EOS_LANGMUIR;
-    // Programmatic dependent launch: the step kernel waits (griddepcontrol.wait) for the previous
-    // grid before touching memory, so the next launch may be scheduled during this one's tail.
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = h->stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    using namespace lbm;
-#define LBM_LAUNCH(W_, L_)                                                                        \
-    do {                                                                                          \
-        if (mode == kStep) LBM_CUDA(cudaLaunchKernelEx(&cfg, step_kernel<W_, L_, kStep>, a));     \
-        else LBM_CUDA(cudaLaunchKernelEx(&cfg, step_kernel<W_, L_, kMoments>, a));                \
-    } while (0)
-    if (walls && lang) LBM_LAUNCH(true, true);
-    else if (walls) LBM_LAUNCH(true, false);
-    else if (lang) LBM_LAUNCH(false, true);
-    else LBM_LAUNCH(false, false);
-#undef LBM_LAUNCH
+    cudaError_t e;
+    if (h->prm.storage == LBM_STORE_FP16) e = lbm::launch_step_fp16(a, mode, walls, lang, grid, h->stream);
+    else if (h->prm.storage == LBM_STORE_BF16) e = lbm::launch_step_bf16(a, mode, walls, lang, grid, h->stream);
+    else e = lbm::launch_step_fp32(a, mode, walls, lang, grid, h->stream);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+// FP64 sum of phi (lane 0) or psi (lane 1) of a population buffer into partials[0..blocks),
+// then partials[blocks] ... written to *dres.
+int launch_reduce(int st, const void* pops, int lane, int nx, int ny, int pitch, size_t plane, const lbm::Phys& ph,
+                  int blocks, double* partials, double* dres, cudaStream_t stream) {
+    if (st == LBM_STORE_FP16)
+        lbm::reduce_partial_kernel<lbm::kFP16><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch,
+                                                                                           (long long)plane, ph, partials);
+    else if (st == LBM_STORE_BF16)
+        lbm::reduce_partial_kernel<lbm::kBF16><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch,
+                                                                                           (long long)plane, ph, partials);
+    else
+        lbm::reduce_partial_kernel<lbm::kFP32><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch,
+                                                                                           (long long)plane, ph, partials);
+    LBM_CUDA(cudaGetLastError());
+    lbm::reduce_final_kernel<<<1, lbm::kReduceThreads, 0, stream>>>(partials, blocks, dres);
     LBM_CUDA(cudaGetLastError());
     return LBM_OK;
 }
@@ -340,11 +353,11 @@ int lbm_reduce_noalloc(const void* d_pops, int nx, int ny, int what, void* cuda_
     if (rc) return rc;
     const int pitch = (nx + 31) / 32 * 32;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-    lbm::reduce_partial_kernel<<<ny, lbm::kReduceThreads, 0, stream>>>(
-        static_cast<const float*>(d_pops), what == LBM_SUM_PSI ? 1 : 0, nx, ny, pitch, (long long)ny * pitch, scratch);
-    LBM_CUDA(cudaGetLastError());
-    lbm::reduce_final_kernel<<<1, lbm::kReduceThreads, 0, stream>>>(scratch, ny, scratch + LBM_NOALLOC_MAX_ROWS);
-    LBM_CUDA(cudaGetLastError());
+    lbm::Phys ph;
+    std::memset(&ph, 0, sizeof(ph));
+    rc = launch_reduce(LBM_STORE_FP32, d_pops, what == LBM_SUM_PSI ? 1 : 0, nx, ny, pitch, (size_t)ny * pitch, ph, ny,
+                       scratch, scratch + LBM_NOALLOC_MAX_ROWS, stream);
+    if (rc) return rc;
     LBM_CUDA(cudaMemcpyAsync(out, scratch + LBM_NOALLOC_MAX_ROWS, sizeof(double), cudaMemcpyDeviceToHost, stream));
     LBM_CUDA(cudaStreamSynchronize(stream));
     return LBM_OK;
@@ -381,20 +394,26 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
     h->phys = make_phys(p, L);
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     h->ws = static_cast<char*>(d_workspace);
-    h->pops[0] = reinterpret_cast<float*>(h->ws + L.off_pops[0]);
-    h->pops[1] = reinterpret_cast<float*>(h->ws + L.off_pops[1]);
-    h->hist = reinterpret_cast<float*>(h->ws + L.off_hist);
+    h->pops[0] = h->ws + L.off_pops[0];
+    h->pops[1] = h->ws + L.off_pops[1];
+    h->hist[0] = reinterpret_cast<float2*>(h->ws + L.off_hist[0]);
+    h->hist[1] = reinterpret_cast<float2*>(h->ws + L.off_hist[1]);
     h->status = reinterpret_cast<unsigned*>(h->ws + L.off_status);
     h->partials = reinterpret_cast<double*>(h->ws + L.off_partials);
     int bps = 0;
-    rc = prepare_kernels(&bps);
+    rc = prepare_kernels(p->storage, &bps);
+    const bool half = p->storage != LBM_STORE_FP32;
+    const int es_pair = half ? 4 : 8, es_h = half ? 2 : 4;
+    const unsigned hbw = half ? lbm::Traits<lbm::kFP16>::H_BW : lbm::Traits<lbm::kFP32>::H_BW;
     for (int b = 0; b < 2 && !rc; ++b) {
-        rc = encode_map(&h->tm_fg[b], h->pops[b], true, p->nx, p->ny, lbm::kPairs, L.pitch, L.plane, lbm::BW, lbm::BH, 1);
-        if (!rc)
-            rc = encode_map(&h->tm_h[b], h->pops[b] + (size_t)lbm::kPlaneH * L.plane, false, p->nx, p->ny, 8, L.pitch,
-                            L.plane, lbm::BW, lbm::TY, 1);
+        rc = encode_map(&h->tm_fg[b], h->pops[b], es_pair, p->nx, p->ny, lbm::kPairs, L.pitch, L.plane, lbm::BW,
+                        lbm::BH, 1);
+        char* hbase = static_cast<char*>(h->pops[b]) + (size_t)lbm::kPairs * L.plane * es_pair;
+        if (!rc) rc = encode_map(&h->tm_h[b], hbase, es_h, p->nx, p->ny, lbm::kHPlanes, L.pitch, L.plane, hbw, lbm::TY, 1);
     }
-    if (!rc) rc = encode_map(&h->tm_hist, h->hist, false, p->nx, p->ny, 2, L.pitch, L.plane, lbm::TX, lbm::TY, 2);
+    for (int b = 0; b < 2 && !rc; ++b)
+        rc = half ? encode_map(&h->tm_hist[b], h->hist[b], 8, p->nx, p->ny, 1, L.pitch, L.plane, lbm::BW, lbm::BH, 1)
+                  : encode_map(&h->tm_hist[b], h->hist[b], 8, p->nx, p->ny, 1, L.pitch, L.plane, lbm::TX, lbm::TY, 1);
     if (rc) {
         delete h;
         return rc;
@@ -420,7 +439,8 @@ int lbm_init_fields(lbm_handle* h, const double* phi, const double* psi, const d
     const double* d[5] = {phi, psi, ux, uy, P};
     const int tgt = 0;
     if (mem == LBM_MEM_HOST) {
-        // stage through the buffer that becomes dead (5 doubles per cell fit in 26 floats)
+        // stage through the buffer that becomes dead (5 doubles per cell fit in a buffer's
+        // 104 or 52 bytes per cell)
         double* stage = reinterpret_cast<double*>(h->pops[tgt ^ 1]);
         for (int k = 0; k < 5; ++k) {
             LBM_CUDA(cudaMemcpyAsync(stage + k * n, d[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -434,12 +454,14 @@ int lbm_init_fields(lbm_handle* h, const double* phi, const double* psi, const d
     a.p = h->phys;
     a.phi = d[0]; a.psi = d[1]; a.ux = d[2]; a.uy = d[3]; a.P = d[4];
     a.dst = h->pops[tgt];
-    a.hist = h->hist;
+    a.hist = h->hist[tgt];
     a.status = h->status;
     a.langmuir = h->prm.eos == LBM_EOS_LANGMUIR;
     a.walls = h->prm.bc_y == LBM_BC_WALLS;
     const dim3 block(32, 8), grid((h->prm.nx + 31) / 32, (h->prm.ny + 7) / 8);
-    lbm::init_kernel<<<grid, block, 0, h->stream>>>(a);
+    if (h->prm.storage == LBM_STORE_FP16) lbm::init_kernel<lbm::kFP16><<<grid, block, 0, h->stream>>>(a);
+    else if (h->prm.storage == LBM_STORE_BF16) lbm::init_kernel<lbm::kBF16><<<grid, block, 0, h->stream>>>(a);
+    else lbm::init_kernel<lbm::kFP32><<<grid, block, 0, h->stream>>>(a);
     LBM_CUDA(cudaGetLastError());
     LBM_CUDA(cudaStreamSynchronize(h->stream));
     h->cur = tgt;
@@ -503,16 +525,13 @@ int lbm_reduce(lbm_handle* h, int what, double* out) {
     if (what != LBM_SUM_PHI && what != LBM_SUM_PSI) return fail(LBM_EINVAL, "bad reduction selector");
     if (!out) return fail(LBM_EINVAL, "out is NULL");
     const int blocks = h->prm.ny < lbm::kMaxPartials ? h->prm.ny : lbm::kMaxPartials;
-    lbm::reduce_partial_kernel<<<blocks, lbm::kReduceThreads, 0, h->stream>>>(
-        h->pops[h->cur], what == LBM_SUM_PSI ? 1 : 0, h->prm.nx, h->prm.ny, h->L.pitch, (long long)h->L.plane,
-        h->partials);
-    LBM_CUDA(cudaGetLastError());
     double* dres = h->partials + lbm::kMaxPartials;
-    lbm::reduce_final_kernel<<<1, lbm::kReduceThreads, 0, h->stream>>>(h->partials, blocks, dres);
-    LBM_CUDA(cudaGetLastError());
+    int rc = launch_reduce(h->prm.storage, h->pops[h->cur], what == LBM_SUM_PSI ? 1 : 0, h->prm.nx, h->prm.ny,
+                           h->L.pitch, h->L.plane, h->phys, blocks, h->partials, dres, h->stream);
+    if (rc) return rc;
     LBM_CUDA(cudaMemcpyAsync(out, dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     unsigned st = 0;
-    int rc = read_status(h, &st);
+    rc = read_status(h, &st);
     if (rc) return rc;
     return status_code(st);
 }
@@ -537,7 +556,8 @@ static const uint64_t kStateMagic = 0x4c424d3253544154ull;  // "LBM2STAT"
 int lbm_state_bytes(const lbm_handle* h, size_t* bytes) {
     g_err.clear();
     if (!h || !bytes) return fail(LBM_EINVAL, "NULL argument");
-    *bytes = sizeof(StateHeader) + h->L.plane * lbm::kPlanes * sizeof(float) + 2 * h->L.plane * sizeof(float);
+    *bytes = sizeof(StateHeader) + h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage) +
+             h->L.plane * sizeof(float2);
     return LBM_OK;
 }
 
@@ -551,9 +571,9 @@ int lbm_get_state(lbm_handle* h, void* host_blob, size_t bytes) {
     StateHeader hd{kStateMagic, h->prm.nx, h->prm.ny, h->L.pitch, h->first, h->steps};
     char* b = static_cast<char*>(host_blob);
     std::memcpy(b, &hd, sizeof(hd));
-    const size_t pb = h->L.plane * lbm::kPlanes * sizeof(float);
+    const size_t pb = h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage);
     LBM_CUDA(cudaMemcpyAsync(b + sizeof(hd), h->pops[h->cur], pb, cudaMemcpyDeviceToHost, h->stream));
-    LBM_CUDA(cudaMemcpyAsync(b + sizeof(hd) + pb, h->hist, 2 * h->L.plane * sizeof(float), cudaMemcpyDeviceToHost,
+    LBM_CUDA(cudaMemcpyAsync(b + sizeof(hd) + pb, h->hist[h->cur], h->L.plane * sizeof(float2), cudaMemcpyDeviceToHost,
                              h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
     return LBM_OK;
@@ -570,10 +590,10 @@ int lbm_set_state(lbm_handle* h, const void* host_blob, size_t bytes) {
     std::memcpy(&hd, b, sizeof(hd));
     if (hd.magic != kStateMagic || hd.nx != h->prm.nx || hd.ny != h->prm.ny || hd.pitch != h->L.pitch)
         return fail(LBM_EINVAL, "state blob does not match this handle");
-    const size_t pb = h->L.plane * lbm::kPlanes * sizeof(float);
+    const size_t pb = h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage);
     const int cur = (int)(hd.steps & 1);  // the current state after k steps is buffer k mod 2
     LBM_CUDA(cudaMemcpyAsync(h->pops[cur], b + sizeof(hd), pb, cudaMemcpyHostToDevice, h->stream));
-    LBM_CUDA(cudaMemcpyAsync(h->hist, b + sizeof(hd) + pb, 2 * h->L.plane * sizeof(float), cudaMemcpyHostToDevice,
+    LBM_CUDA(cudaMemcpyAsync(h->hist[cur], b + sizeof(hd) + pb, h->L.plane * sizeof(float2), cudaMemcpyHostToDevice,
                              h->stream));
     LBM_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));

@@ -1,22 +1,37 @@
 // Device code of the fused three-population lattice-Boltzmann step (arXiv 2408.15654).
 //
 // Data layout in HBM (one population buffer, ny rows x `pitch` cells per plane):
-//   9 pair planes  (f_i, g_i), i = 0..8, as float2   phase field (Sec. 3.1) and surfactant (Sec. 3.2)
-//   8 float planes h_1..h_8                           flow (Sec. 3.3)
-// f_i and g_i stream along the same link, so they travel and collide together as one float2:
-// one 64-bit load and store per pair, and Blackwell's packed FP32x2 arithmetic runs both
-// collisions at once.  h_0 is never stored: column 0 of M^-1 is e_0 and rows 1..8 of M do not
-// see h_0, so h_0 feeds only itself (Sec. 3.3, Sec. 4).
+//   9 pair planes  (f_i, g_i), i = 0..8      phase field (Sec. 3.1) and surfactant (Sec. 3.2)
+//   8 planes       h_1..h_8                  flow (Sec. 3.3)
+// in FP32 (float2 / float) or, for the 16-bit storage modes, as FP16 / BF16 deviations
+// (half2 / half).  f_i and g_i stream along the same link, so they travel and collide together:
+// one access per pair, and Blackwell's packed FP32x2 arithmetic runs both collisions at once.
+// h_0 is never stored: column 0 of M^-1 is e_0 and rows 1..8 of M do not see h_0, so h_0 feeds
+// only itself (Sec. 3.3, Sec. 4).  The u history is one float2 plane (u_x, u_y).
 // A buffer holds the post-collision populations of the previous step at the cell that produced
 // them; a step pulls q_i(x) = q*_i(x - c_i) ("pull" streaming), so it writes only its own cell
 // and two buffers alternate.  Across a wall the missing link is the cell's own opposite slot,
 // into which the previous step already folded the moving-wall term (half-way bounce-back, Sec. 4).
+//
+// 16-bit storage.  Every value is stored divided by its lattice weight, as a scaled deviation
+// from a reference:
+//   (f_i, g_i):  ((f_i / w_i - phi_ref) S_f, (g_i / w_i) S_g)   phi_ref = (phiA + phiB)/2
+//   h_i:         (h_i / w_i - 3 rho c_i.u(x_s)) S_h                x_s = the cell that stored the slot,
+// where u(x_s) is the velocity that cell wrote to the u history in the same step.  Dividing by
+// w_i makes the bulk equilibria (phi = phiA or phiB, psi = 0, u = 0) exactly representable, so
+// the bulk does not drift by repeated rounding; taking away the first-order velocity part keeps
+// the pressure (1e-5 against a velocity part of 1e-3) above the 16-bit rounding.  The step
+// stores with stochastic rounding (Blackwell's cvt.rs, random bits from a hash of cell, step and
+// link): in a steady flow a cell rounds nearly the same values every step, and round-to-nearest
+// would then add the same error every step.  All arithmetic stays in FP32.
 //
 // Velocity order (the columns of the printed moment matrix M, Sec. 4):
 //   0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
 #pragma once
 #include <cstdint>
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lbm {
@@ -29,9 +44,35 @@ __host__ __device__ constexpr float wgt(int i) { return i == 0 ? 4.f / 9.f : (i 
 static_assert(opp(1) == 3 && opp(3) == 1 && opp(2) == 4 && opp(4) == 2, "axis opposites");
 static_assert(opp(5) == 7 && opp(7) == 5 && opp(6) == 8 && opp(8) == 6, "diagonal opposites");
 
-constexpr int kPlanes = 26;     // float planes per buffer: 9 pair planes (18) + 8 h planes
-constexpr int kPairs = 9;       // (f_i, g_i) planes, float2
-constexpr int kPlaneH = 18;     // float-plane index of h_1
+constexpr int kPairs = 9;       // (f_i, g_i) planes
+constexpr int kHPlanes = 8;     // h_1..h_8 planes
+
+enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
+
+// Storage traits: element types, sizes, and the x origin / width of the h boxes (TMA x
+// coordinates must be multiples of 16 bytes: 4 cells of 4 bytes, 8 cells of 2 bytes).
+template <int ST> struct Traits;
+template <> struct Traits<kFP32> {
+    using P = float2;
+    using H = float;
+    static constexpr int H_X0 = 4, H_BW = 40;
+    static constexpr bool kHalo = false;  // the u history box needs no ring
+};
+template <> struct Traits<kFP16> {
+    using P = __half2;
+    using H = __half;
+    static constexpr int H_X0 = 8, H_BW = 48;
+    static constexpr bool kHalo = true;   // h pulls need the source cell's u
+};
+template <> struct Traits<kBF16> {
+    using P = __nv_bfloat162;
+    using H = __nv_bfloat16;
+    static constexpr int H_X0 = 8, H_BW = 48;
+    static constexpr bool kHalo = true;
+};
+
+// Bytes of one population buffer per cell: 9 pairs + 8 h values.
+__host__ __device__ constexpr int pop_bytes_per_cell(int st) { return st == kFP32 ? 9 * 8 + 8 * 4 : 9 * 4 + 8 * 2; }
 
 // Physical constants in FP32, precomputed on the host from lbm_params.
 struct Phys {
@@ -53,49 +94,68 @@ struct Phys {
     int tie_s4h;              // 1: s4^h = s2^h
     float u_top, u_bot;
     float n_eps2;             // n_eps^2
+    // 16-bit storage (unused for FP32): per link i, decode q = raw * dec + ref and encode
+    // raw = q * enc + eref; h additionally carries the velocity term 3 w_i rho c_i.u
+    float dec_f[9], dec_g[9], enc_f[9], enc_g[9];  // w_i / S and S / w_i
+    float ref_f[9];           // w_i phi_ref
+    float eref_f;             // -phi_ref S_f
+    float dec_h[9], enc_h[9]; // w_i / S_h and S_h / w_i
+    float kh_axis, kh_diag;   // 3 w_i rho for axis and diagonal links
+    float kh_enc;             // 3 rho S_h
+    float phi_ref, isc_f, isc_g;  // phi_ref and 1 / S of the (f, g) lanes
 };
 
 enum Mode { kStep = 0, kMoments = 1 };
 
 // Tile geometry.  A CTA of NT threads owns a TX x TY tile, one cell per thread.  TMA stages:
-//   pair plane i: box of BW x BH pairs,  row r, col c <-> (x0 - 4 + c, y0 - 1 - cy(i) + r)
-//   h plane i:    box of BW x TY floats, row r, col c <-> (x0 - 4 + c, y0 - cy(i) + r)
+//   pair plane i: box of BW x BH pairs,    row r, col c <-> (x0 - 4 + c, y0 - 1 - cy(i) + r)
+//   h plane i:    box of H_BW x TY values, row r, col c <-> (x0 - H_X0 + c, y0 - cy(i) + r)
+//   u history:    box of TX x TY (FP32) or BW x BH (16-bit, one-cell ring) float2
 // so extended-tile cell (ex, ey) (global (x0 - 1 + ex, y0 - 1 + ey)) pulls pair i from
-// [ey][ex + 3 - cx(i)], the own cell (tx, ty) pulls h_i from [ty][tx + 4 - cx(i)], and the own
-// cell's unshifted post-collision pair i sits at [ty + 1 + cy(i)][tx + 4].  Boxes start 4 cells
-// left of the tile so that every x coordinate is a multiple of 16 bytes.
+// [ey][ex + 3 - cx(i)], the own cell (tx, ty) pulls h_i from [ty][tx + H_X0 - cx(i)], and the
+// own cell's unshifted post-collision pair i sits at [ty + 1 + cy(i)][tx + 4].
 constexpr int TX = 32, TY = 8, NT = TX * TY;
 constexpr int BW = TX + 8, BH = TY + 2;
-constexpr int FG_BOX = BW * BH;            // pairs per pair-plane box (3200 B)
-constexpr int H_BOX = BW * TY;             // floats per h box (1280 B)
-constexpr int HIST_BOX = 2 * TX * TY;      // u_x, u_y of the tile
+constexpr int FG_BOX = BW * BH;            // pairs per pair-plane box
 constexpr int EX = TX + 2, EY = TY + 2, NE = EX * EY;
 constexpr int NRING = 2 * EX + 2 * TY;
-constexpr int SM_FG = 0;                                       // byte offsets in shared memory
-constexpr int SM_H = SM_FG + kPairs * FG_BOX * 8;
-constexpr int SM_HIST = SM_H + 8 * H_BOX * 4;
-constexpr int SM_PP = SM_HIST + HIST_BOX * 4;
-constexpr int SM_BAR = SM_PP + NE * 8;
-constexpr size_t kSmemBytes = SM_BAR + 16 + 128;               // + mbarrier + alignment slack
-constexpr unsigned kTileBytes = (unsigned)(kPairs * FG_BOX * 8 + 8 * H_BOX * 4 + HIST_BOX * 4);
-constexpr unsigned kSuspendNs = 200000;                        // sleep hint of one wait attempt
-constexpr unsigned kWaitLimit = 5000;                          // attempts: the wait ends within ~1 s
+constexpr unsigned kSuspendNs = 200000;    // sleep hint of one wait attempt
+constexpr unsigned kWaitLimit = 5000;      // attempts: the wait ends within ~1 s
 constexpr unsigned kStatusUnstable = 1u, kStatusTimeout = 2u;
-
-static_assert((FG_BOX * 8) % 128 == 0 && (H_BOX * 4) % 128 == 0 && SM_H % 128 == 0 && SM_HIST % 128 == 0,
-              "TMA destinations are 128-byte aligned");
 static_assert(NRING <= NT, "one thread per ring cell");
 
+__host__ __device__ constexpr int round128(int b) { return (b + 127) / 128 * 128; }
+
+// Shared-memory layout (bytes) of one tile for storage mode ST.
+template <int ST> struct Smem {
+    using T = Traits<ST>;
+    static constexpr int FG_SLOT = round128(FG_BOX * (int)sizeof(typename T::P));
+    static constexpr int H_BOX = T::H_BW * TY;
+    static constexpr int H_SLOT = round128(H_BOX * (int)sizeof(typename T::H));
+    static constexpr int HIST_W = T::kHalo ? BW : TX, HIST_H = T::kHalo ? BH : TY;
+    static constexpr int HIST_BYTES = HIST_W * HIST_H * 8;
+    static constexpr int FG = 0;
+    static constexpr int H = FG + kPairs * FG_SLOT;
+    static constexpr int HIST = H + kHPlanes * H_SLOT;
+    static constexpr int PP = HIST + round128(HIST_BYTES);
+    static constexpr int BAR = PP + NE * 8;
+    static constexpr int BYTES = BAR + 16 + 128;  // + mbarrier + alignment slack
+    static constexpr unsigned TX_BYTES =
+        (unsigned)(kPairs * FG_BOX * sizeof(typename T::P) + kHPlanes * H_BOX * sizeof(typename T::H) + HIST_BYTES);
+};
+
 struct StepArgs {
-    CUtensorMap tm_fg;            // {nx, ny, 9} 8-byte pairs, box {BW, BH, 1}
-    CUtensorMap tm_h;             // {nx, ny, 8} floats, box {BW, TY, 1}
-    CUtensorMap tm_hist;          // {nx, ny, 2} floats, box {TX, TY, 2}
+    CUtensorMap tm_fg;            // {nx, ny, 9} pairs, box {BW, BH, 1}
+    CUtensorMap tm_h;             // {nx, ny, 8} h values, box {H_BW, TY, 1}
+    CUtensorMap tm_hist;          // {nx, ny, 1} float2, box {TX, TY, 1} or {BW, BH, 1}
     Phys p;
-    const float* __restrict__ src;
-    float* __restrict__ dst;
-    float* __restrict__ hist;     // 2 planes: u_x, u_y of the previous step (in place)
+    const void* __restrict__ src;
+    void* __restrict__ dst;
+    const float2* __restrict__ hist_src;  // (u_x, u_y) of the previous step
+    float2* __restrict__ hist_dst;        // (u_x, u_y) of this step (the other history buffer)
     unsigned* __restrict__ status;
     double* __restrict__ out[5];  // kMoments: phi, psi, ux, uy, P (dense ny x nx), may be null
+    unsigned seed;                // per-step salt of the stochastic rounding
 };
 
 __device__ __forceinline__ int wrapg(int a, int n) {
@@ -109,6 +169,62 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// ---- storage conversions ----
+template <int ST> __device__ __forceinline__ float2 raw2(typename Traits<ST>::P v);
+template <> __device__ __forceinline__ float2 raw2<kFP32>(float2 v) { return v; }
+template <> __device__ __forceinline__ float2 raw2<kFP16>(__half2 v) { return __half22float2(v); }
+template <> __device__ __forceinline__ float2 raw2<kBF16>(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+template <int ST> __device__ __forceinline__ typename Traits<ST>::P pack2(float2 v);
+template <> __device__ __forceinline__ float2 pack2<kFP32>(float2 v) { return v; }
+template <> __device__ __forceinline__ __half2 pack2<kFP16>(float2 v) { return __float22half2_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat162 pack2<kBF16>(float2 v) { return __float22bfloat162_rn(v); }
+template <int ST> __device__ __forceinline__ float raw1(typename Traits<ST>::H v);
+template <> __device__ __forceinline__ float raw1<kFP32>(float v) { return v; }
+template <> __device__ __forceinline__ float raw1<kFP16>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float raw1<kBF16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <int ST> __device__ __forceinline__ typename Traits<ST>::H pack1(float v);
+template <> __device__ __forceinline__ float pack1<kFP32>(float v) { return v; }
+template <> __device__ __forceinline__ __half pack1<kFP16>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 pack1<kBF16>(float v) { return __float2bfloat16_rn(v); }
+
+// (f_i, g_i) from storage and back
+template <int ST, int I> __device__ __forceinline__ float2 dec_pair(typename Traits<ST>::P v, const Phys& p) {
+    if constexpr (ST == kFP32) return v;
+    else return fma2(raw2<ST>(v), make_float2(p.dec_f[I], p.dec_g[I]), make_float2(p.ref_f[I], 0.f));
+}
+template <int ST, int I> __device__ __forceinline__ typename Traits<ST>::P enc_pair(float2 q, const Phys& p) {
+    if constexpr (ST == kFP32) return q;
+    else return pack2<ST>(fma2(q, make_float2(p.enc_f[I], p.enc_g[I]), make_float2(p.eref_f, 0.f)));
+}
+
+// Two FP32 values to a 16-bit pair with stochastic rounding (lo in the low half).
+template <int ST> __device__ __forceinline__ uint32_t cvt_rs2(float lo, float hi, uint32_t rbits) {
+    uint32_t out;
+    if constexpr (ST == kFP16) asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(out) : "f"(hi), "f"(lo), "r"(rbits));
+    else asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(out) : "f"(hi), "f"(lo), "r"(rbits));
+    return out;
+}
+// Random bits for link k of a cell: a multiply-xorshift hash of the cell's per-step key.
+__device__ __forceinline__ uint32_t rbits_of(uint32_t key, uint32_t k) {
+    uint32_t h = key + k * 0x9E3779B9u;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    return h;
+}
+// (f_i, g_i) to stochastically rounded 16-bit storage
+template <int ST, int I> __device__ __forceinline__ typename Traits<ST>::P enc_pair_rs(float2 q, const Phys& p,
+                                                                                      uint32_t key) {
+    const float2 v = fma2(q, make_float2(p.enc_f[I], p.enc_g[I]), make_float2(p.eref_f, 0.f));
+    const uint32_t bits = cvt_rs2<ST>(v.x, v.y, rbits_of(key, I));
+    return *reinterpret_cast<const typename Traits<ST>::P*>(&bits);
+}
+// 3 w_i rho c_i.u: the first-order velocity part of h_eq removed before 16-bit storage
+template <int I> __device__ __forceinline__ float h_vel(float2 u, const Phys& p) {
+    const float k = I <= 4 ? p.kh_axis : p.kh_diag;
+    return k * ((float)cx(I) * u.x + (float)cy(I) * u.y);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
@@ -185,23 +301,30 @@ __device__ __forceinline__ void collide_pair(float2 q[9], float2 s, float ux, fl
 // Tiles whose boxes reach outside the grid: replace every staged value whose source lies outside
 // by the one the pull really reads there -- the periodic image, or across a wall the pulling
 // cell's own opposite slot (bounce-back).  Only the out-of-grid strips of each box are visited
-// (one warp per plane); entries no valid pull reads are left as loaded.
-template <bool WALLS>
-__device__ void patch_edges(const StepArgs& a, float2* FG, float* Hs, int x0, int y0) {
+// (one warp per box); entries no valid pull reads are left as loaded.
+template <int ST, bool WALLS>
+__device__ void patch_edges(const StepArgs& a, unsigned char* sm, int x0, int y0) {
+    using T = Traits<ST>;
+    using S = Smem<ST>;
+    using P = typename T::P;
+    using Hv = typename T::H;
     const Phys& p = a.p;
-    const float2* __restrict__ srcFG = reinterpret_cast<const float2*>(a.src);
-    const float* __restrict__ srcH = a.src + (size_t)kPlaneH * p.plane;
+    const P* __restrict__ srcFG = static_cast<const P*>(a.src);
+    const Hv* __restrict__ srcH = reinterpret_cast<const Hv*>(srcFG + (size_t)kPairs * p.plane);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cL = min(BW, max(0, 4 - x0));             // box columns [0, cL) lie left of x = 0
-    const int cR = max(cL, min(BW, p.nx - x0 + 4));     // box columns [cR, BW) lie right of nx - 1
-    for (int pl = warp; pl < kPairs + 8; pl += NT / 32) {
-        const bool isfg = pl < kPairs;
-        const int i = isfg ? pl : pl - kPairs + 1;       // direction
-        const int rows = isfg ? BH : TY;
-        const int gy0 = (isfg ? y0 - 1 : y0) - cy(i);    // global row of box row 0
-        const int rB = min(rows, max(0, -gy0));          // box rows [0, rB) lie below y = 0
-        const int rT = max(rB, min(rows, p.ny - gy0));   // box rows [rT, rows) lie above ny - 1
-        const int ncol = cL + (BW - cR), w = cR - cL;
+    constexpr int NBOX = kPairs + kHPlanes + (T::kHalo ? 1 : 0);
+    for (int pl = warp; pl < NBOX; pl += NT / 32) {
+        const int kind = pl < kPairs ? 0 : (pl < kPairs + kHPlanes ? 1 : 2);  // pair, h, history
+        const int i = kind == 0 ? pl : (kind == 1 ? pl - kPairs + 1 : 0);      // direction
+        const int bw = kind == 1 ? T::H_BW : BW;
+        const int xoff = kind == 1 ? T::H_X0 : 4;
+        const int rows = kind == 1 ? TY : BH;
+        const int gy0 = (kind == 1 ? y0 : y0 - 1) - cy(i);   // global row of box row 0
+        const int cL = min(bw, max(0, xoff - x0));           // box columns [0, cL) lie left of x = 0
+        const int cR = max(cL, min(bw, p.nx - x0 + xoff));   // box columns [cR, bw) lie right of nx - 1
+        const int rB = min(rows, max(0, -gy0));              // box rows [0, rB) lie below y = 0
+        const int rT = max(rB, min(rows, p.ny - gy0));       // box rows [rT, rows) lie above ny - 1
+        const int ncol = cL + (bw - cR), w = cR - cL;
         const int n1 = rows * ncol, n2 = (rB + rows - rT) * w;
         for (int k = lane; k < n1 + n2; k += 32) {
             int r, c;
@@ -214,18 +337,24 @@ __device__ void patch_edges(const StepArgs& a, float2* FG, float* Hs, int x0, in
                 c = cL + (kk - rr * w);
                 r = rr < rB ? rr : rT + (rr - rB);
             }
-            const int gx = x0 - 4 + c, gy = gy0 + r;
+            const int gx = x0 - xoff + c, gy = gy0 + r;
             const bool yin = gy >= 0 && gy < p.ny;
-            // the cell that pulls this entry must be one the tile uses
-            const int ex = c - 3 + cx(i);
-            if (isfg ? (ex < 0 || ex >= EX) : (ex - 1 < 0 || ex - 1 >= TX)) continue;
-            const int px = gx + cx(i), py = gy + cy(i);
+            // the cell that reads this entry must be one the tile uses
+            if (kind == 0) {
+                const int ex = c - 3 + cx(i);
+                if (ex < 0 || ex >= EX) continue;
+            } else if (kind == 1) {
+                const int tx = c - xoff + cx(i);
+                if (tx < 0 || tx >= TX) continue;
+            }
             int si = i, sx, sy;
             if (WALLS) {
-                if (py < 0 || py >= p.ny) continue;  // puller is a ring cell beyond a wall (mirrored)
+                const int py = gy + cy(i);
+                if (py < 0 || py >= p.ny) continue;  // reader is a ring cell beyond a wall (mirrored)
                 if (!yin) {
+                    if (kind == 2) continue;          // across a wall the h pull uses the own u
                     si = opp(i);
-                    sx = wrapg(px, p.nx);
+                    sx = wrapg(gx + cx(i), p.nx);
                     sy = py;
                 } else {
                     sx = wrapg(gx, p.nx);
@@ -236,9 +365,30 @@ __device__ void patch_edges(const StepArgs& a, float2* FG, float* Hs, int x0, in
                 sy = wrapg(gy, p.ny);
             }
             const size_t cell = (size_t)sy * p.pitch + sx;
-            if (isfg) FG[pl * FG_BOX + r * BW + c] = srcFG[(size_t)si * p.plane + cell];
-            else Hs[(pl - kPairs) * H_BOX + r * BW + c] = srcH[(size_t)(si - 1) * p.plane + cell];
+            if (kind == 0)
+                reinterpret_cast<P*>(sm + S::FG + pl * S::FG_SLOT)[r * bw + c] = srcFG[(size_t)si * p.plane + cell];
+            else if (kind == 1)
+                reinterpret_cast<Hv*>(sm + S::H + (pl - kPairs) * S::H_SLOT)[r * bw + c] =
+                    srcH[(size_t)(si - 1) * p.plane + cell];
+            else
+                reinterpret_cast<float2*>(sm + S::HIST)[r * bw + c] = a.hist_src[cell];
         }
+    }
+}
+
+template <int ST, int I>
+__device__ __forceinline__ float load_h(const unsigned char* sm, const float2* Hist, const Phys& p, int tx, int ty,
+                                        bool bb, float2 uown) {
+    using T = Traits<ST>;
+    using S = Smem<ST>;
+    const typename T::H v = reinterpret_cast<const typename T::H*>(sm + S::H + (I - 1) * S::H_SLOT)[ty * T::H_BW + tx + T::H_X0 - cx(I)];
+    if constexpr (ST == kFP32) {
+        return v;
+    } else {
+        // the slot was stored with the first-order velocity part of the cell that stored it:
+        // the source cell x - c_i, or across a wall the own cell (whose opposite slot it is)
+        const float2 us = bb ? make_float2(-uown.x, -uown.y) : Hist[(ty + 1 - cy(I)) * BW + tx + 4 - cx(I)];
+        return fmaf(raw1<ST>(v), p.dec_h[I], h_vel<I>(us, p));
     }
 }
 
@@ -248,15 +398,17 @@ __device__ void patch_edges(const StepArgs& a, float2* FG, float* Hs, int x0, in
 // of a one-cell ring give (phi, psi) for the 9-point stencils; the same boxes hold the own cell's
 // unshifted post-collision values, whose sums are phi and psi of the previous level
 // (m*_0 = phi exactly, Sec. 3.1), so only u of the previous level is stored.
-template <bool WALLS, bool LANGMUIR, int MODE>
+template <int ST, bool WALLS, bool LANGMUIR, int MODE>
 __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ StepArgs a) {
+    using T = Traits<ST>;
+    using S = Smem<ST>;
+    using P = typename T::P;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float2* FG = reinterpret_cast<float2*>(sm + SM_FG);
-    float* Hs = reinterpret_cast<float*>(sm + SM_H);
-    const float* Hist = reinterpret_cast<const float*>(sm + SM_HIST);
-    float2* PP = reinterpret_cast<float2*>(sm + SM_PP);
-    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + SM_BAR);
+    const P* FG = reinterpret_cast<const P*>(sm + S::FG);
+    const float2* Hist = reinterpret_cast<const float2*>(sm + S::HIST);
+    float2* PP = reinterpret_cast<float2*>(sm + S::PP);
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + S::BAR);
     const Phys& p = a.p;
     const int t = threadIdx.x;
     // The first and the last tile row (whose boxes need edge patching, and so run longest) are
@@ -274,17 +426,20 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     cudaTriggerProgrammaticLaunchCompletion();
     cudaGridDependencySynchronize();
     if (t == 0) {
-        mbar_expect_tx(mbar, kTileBytes);
+        mbar_expect_tx(mbar, S::TX_BYTES);
 #pragma unroll
-        for (int i = 0; i < kPairs; ++i) tma_load_3d(FG + i * FG_BOX, &a.tm_fg, x0 - 4, y0 - 1 - cy(i), i, mbar);
+        for (int i = 0; i < kPairs; ++i)
+            tma_load_3d(sm + S::FG + i * S::FG_SLOT, &a.tm_fg, x0 - 4, y0 - 1 - cy(i), i, mbar);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) tma_load_3d(Hs + (i - 1) * H_BOX, &a.tm_h, x0 - 4, y0 - cy(i), i - 1, mbar);
-        tma_load_3d(sm + SM_HIST, &a.tm_hist, x0, y0, 0, mbar);
+        for (int i = 1; i < 9; ++i)
+            tma_load_3d(sm + S::H + (i - 1) * S::H_SLOT, &a.tm_h, x0 - T::H_X0, y0 - cy(i), i - 1, mbar);
+        if constexpr (T::kHalo) tma_load_3d(sm + S::HIST, &a.tm_hist, x0 - 4, y0 - 1, 0, mbar);
+        else tma_load_3d(sm + S::HIST, &a.tm_hist, x0, y0, 0, mbar);
     }
     __syncthreads();
     bool abort = !mbar_wait_bounded(mbar, 0);
-    if (x0 == 0 || x0 + TX + 4 > p.nx || y0 == 0 || y0 + TY + 2 > p.ny) {
-        if (!abort) patch_edges<WALLS>(a, FG, Hs, x0, y0);
+    if (x0 == 0 || x0 + TX + 8 > p.nx || y0 == 0 || y0 + TY + 2 > p.ny) {
+        if (!abort) patch_edges<ST, WALLS>(a, sm, x0, y0);
         abort = __syncthreads_or(abort);
     }
 
@@ -299,12 +454,19 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     {
         int row = ty + 1;
         if (WALLS && y >= p.ny) row = p.ny - y0;
+        const P* base = FG + row * BW + tx + 4;
+        q[0] = dec_pair<ST, 0>(base[0 * S::FG_SLOT / (int)sizeof(P) - cx(0)], p);
+        q[1] = dec_pair<ST, 1>(base[1 * S::FG_SLOT / (int)sizeof(P) - cx(1)], p);
+        q[2] = dec_pair<ST, 2>(base[2 * S::FG_SLOT / (int)sizeof(P) - cx(2)], p);
+        q[3] = dec_pair<ST, 3>(base[3 * S::FG_SLOT / (int)sizeof(P) - cx(3)], p);
+        q[4] = dec_pair<ST, 4>(base[4 * S::FG_SLOT / (int)sizeof(P) - cx(4)], p);
+        q[5] = dec_pair<ST, 5>(base[5 * S::FG_SLOT / (int)sizeof(P) - cx(5)], p);
+        q[6] = dec_pair<ST, 6>(base[6 * S::FG_SLOT / (int)sizeof(P) - cx(6)], p);
+        q[7] = dec_pair<ST, 7>(base[7 * S::FG_SLOT / (int)sizeof(P) - cx(7)], p);
+        q[8] = dec_pair<ST, 8>(base[8 * S::FG_SLOT / (int)sizeof(P) - cx(8)], p);
         float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            q[i] = FG[i * FG_BOX + row * BW + tx + 4 - cx(i)];
-            s = add2(s, q[i]);
-        }
+        for (int i = 0; i < 9; ++i) s = add2(s, q[i]);
         PP[eo] = s;
     }
     if (t < NRING) {
@@ -319,9 +481,17 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
             if (gy < 0) row = 1 - y0;
             else if (gy >= p.ny) row = p.ny - y0;
         }
+        // phi = sum_i w_i (raw_i / S + ref) = (sum_i w_i raw_i) / S + phi_ref for 16-bit storage
+        const P* base = FG + row * BW + ex + 3;
         float2 s = make_float2(0.f, 0.f);
+        if constexpr (ST == kFP32) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s = add2(s, FG[i * FG_BOX + row * BW + ex + 3 - cx(i)]);
+            for (int i = 0; i < 9; ++i) s = add2(s, base[i * S::FG_SLOT / (int)sizeof(P) - cx(i)]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) s = fma2(bc(wgt(i)), raw2<ST>(base[i * S::FG_SLOT / (int)sizeof(P) - cx(i)]), s);
+            s = fma2(s, make_float2(p.isc_f, p.isc_g), make_float2(p.phi_ref, 0.f));
+        }
         PP[ey * EX + ex] = s;
     }
     if (__syncthreads_or(abort)) {
@@ -380,10 +550,23 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     const float Fx = cap * gpx + p.mar_k * (g2 * gsgx - sdg * gpx) + p.rho * p.gx;
     const float Fy = cap * gpy + p.mar_k * (g2 * gsgy - sdg * gpy) + p.rho * p.gy;
 
-    // flow populations pulled from the staged boxes
+    // own u of the previous level (also the encoding velocity of the own slots across a wall)
+    const float2 uown = T::kHalo ? Hist[(ty + 1) * BW + tx + 4] : Hist[ty * TX + tx];
+
+    // flow populations pulled from the staged boxes (16-bit: plus the source cell's 3 w rho c.u)
     float h[9];
-#pragma unroll
-    for (int i = 1; i < 9; ++i) h[i] = Hs[(i - 1) * H_BOX + ty * BW + tx + 4 - cx(i)];
+    {
+        const bool bb_up = WALLS && y == 0;           // links 2, 5, 6 come from below the bottom wall
+        const bool bb_dn = WALLS && y == p.ny - 1;    // links 4, 7, 8 come from above the top wall
+        h[1] = load_h<ST, 1>(sm, Hist, p, tx, ty, false, uown);
+        h[2] = load_h<ST, 2>(sm, Hist, p, tx, ty, bb_up, uown);
+        h[3] = load_h<ST, 3>(sm, Hist, p, tx, ty, false, uown);
+        h[4] = load_h<ST, 4>(sm, Hist, p, tx, ty, bb_dn, uown);
+        h[5] = load_h<ST, 5>(sm, Hist, p, tx, ty, bb_up, uown);
+        h[6] = load_h<ST, 6>(sm, Hist, p, tx, ty, bb_up, uown);
+        h[7] = load_h<ST, 7>(sm, Hist, p, tx, ty, bb_dn, uown);
+        h[8] = load_h<ST, 8>(sm, Hist, p, tx, ty, bb_dn, uown);
+    }
 
     // velocity: rho u = sum c_i h_i + F/2 (Sec. 3.3)
     const float h13 = h[1] - h[3], h24 = h[2] - h[4], h57 = h[5] - h[7], h68 = h[6] - h[8];
@@ -396,12 +579,19 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     float2 pprev = pp;
     float uxp = ux, uyp = uy;
     if (!p.first) {
+        const P* base = FG + (ty + 1) * BW + tx + 4;
         float2 s = make_float2(0.f, 0.f);
+        if constexpr (ST == kFP32) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s = add2(s, FG[i * FG_BOX + (ty + 1 + cy(i)) * BW + tx + 4]);
+            for (int i = 0; i < 9; ++i) s = add2(s, base[i * S::FG_SLOT / (int)sizeof(P) + cy(i) * BW]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) s = fma2(bc(wgt(i)), raw2<ST>(base[i * S::FG_SLOT / (int)sizeof(P) + cy(i) * BW]), s);
+            s = fma2(s, make_float2(p.isc_f, p.isc_g), make_float2(p.phi_ref, 0.f));
+        }
         pprev = s;
-        uxp = Hist[ty * TX + tx];
-        uyp = Hist[TX * TY + ty * TX + tx];
+        uxp = uown.x;
+        uyp = uown.y;
     }
 
     // time derivatives, backward difference over one step: d_t(phi u), d_t(psi u) as pairs
@@ -415,7 +605,7 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     // pressure (Eq. for P, Sec. 3.3) with K = w0/(c^2 - cs2) = 2/3:
     //   P = 3/5 [sum_{i>0} h_i - (2/3) rho |u|^2 + (1/3) d_t(rho |u|^2)]
     const float hsum = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
-    const float P = 0.6f * (hsum - (2.f / 3.f) * rho * (ux * ux + uy * uy) + (1.f / 3.f) * (dt_xx + dt_yy));
+    const float P_ = 0.6f * (hsum - (2.f / 3.f) * rho * (ux * ux + uy * uy) + (1.f / 3.f) * (dt_xx + dt_yy));
 
     {
         // |u| >= 0.3, or a non-finite value (NaN fails every comparison; a NaN anywhere in the
@@ -432,7 +622,7 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
         if (a.out[1]) a.out[1][o] = psi;
         if (a.out[2]) a.out[2][o] = ux;
         if (a.out[3]) a.out[3][o] = uy;
-        if (a.out[4]) a.out[4][o] = P;
+        if (a.out[4]) a.out[4][o] = P_;
     } else {
         // ---- f (Sec. 3.1) and g (Sec. 3.2) together; sources cs2 V = d_t(s u) + cs2 (A or B) n ----
         {
@@ -441,9 +631,22 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
             collide_pair(q, pp, ux, uy, vx, vy, make_float2(p.nS1[0], p.nS1[1]), make_float2(p.nS2[0], p.nS2[1]),
                          make_float2(p.nS3[0], p.nS3[1]), make_float2(p.nS4[0], p.nS4[1]),
                          make_float2(p.K1[0], p.K1[1]), make_float2(p.K3[0], p.K3[1]));
-            float2* __restrict__ dfg = reinterpret_cast<float2*>(a.dst) + cell;
+            P* __restrict__ dfg = static_cast<P*>(a.dst) + cell;
+            if constexpr (ST == kFP32) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) dfg[(size_t)i * p.plane] = q[i];
+                for (int i = 0; i < 9; ++i) dfg[(size_t)i * p.plane] = q[i];
+            } else {
+                const uint32_t key = (uint32_t)cell * 0x85EBCA6Bu ^ a.seed;
+                dfg[0 * p.plane] = enc_pair_rs<ST, 0>(q[0], p, key);
+                dfg[1 * p.plane] = enc_pair_rs<ST, 1>(q[1], p, key);
+                dfg[2 * p.plane] = enc_pair_rs<ST, 2>(q[2], p, key);
+                dfg[3 * p.plane] = enc_pair_rs<ST, 3>(q[3], p, key);
+                dfg[4 * p.plane] = enc_pair_rs<ST, 4>(q[4], p, key);
+                dfg[5 * p.plane] = enc_pair_rs<ST, 5>(q[5], p, key);
+                dfg[6 * p.plane] = enc_pair_rs<ST, 6>(q[6], p, key);
+                dfg[7 * p.plane] = enc_pair_rs<ST, 7>(q[7], p, key);
+                dfg[8 * p.plane] = enc_pair_rs<ST, 8>(q[8], p, key);
+            }
         }
         // ---- flow h (Sec. 3.3) ----
         float s2, k2, s4, k4;
@@ -468,12 +671,12 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
         // increments dm_k = -s_k (m_k - m_eq_k) + (1 - s_k/2) m_src_k, then h* = h + M^-1 dm
         const float d1 = k1 * Fx - s1 * (jx - Jx);
         const float d2 = k1 * Fy - s1 * (jy - Jy);
-        const float d3 = k2 * dt_xx - s2 * (m3 - (P + Jx * ux));
-        const float d4 = k2 * dt_yy - s2 * (m4 - (P + Jy * uy));
+        const float d3 = k2 * dt_xx - s2 * (m3 - (P_ + Jx * ux));
+        const float d4 = k2 * dt_yy - s2 * (m4 - (P_ + Jy * uy));
         const float d5 = k2 * dt_xy - s2 * (m5 - Jx * uy);
         const float d6 = (1.f / 3.f) * (k3 * Fx - s3 * (3.f * m6 - Jx));
         const float d7 = (1.f / 3.f) * (k3 * Fy - s3 * (3.f * m7 - Jy));
-        const float d8 = (1.f / 3.f) * (k4 * (dt_xx + dt_yy) - s4 * (3.f * m8 - (P + Jx * ux + Jy * uy)));
+        const float d8 = (1.f / 3.f) * (k4 * (dt_xx + dt_yy) - s4 * (3.f * m8 - (P_ + Jx * ux + Jy * uy)));
         const float A = d1 - d6, B = d3 - d8, C = d2 - d7, D = d4 - d8;
         const float E = d8 + d5, F = d8 - d5, G = d6 + d7, H = d7 - d6;
         h[1] += 0.5f * (A + B);
@@ -496,11 +699,33 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
                 h[6] -= 6.f * wgt(6) * rho * (-1.f) * p.u_top;
             }
         }
-        float* __restrict__ dh = a.dst + (size_t)kPlaneH * p.plane + cell;
+        using Hv = typename T::H;
+        Hv* __restrict__ dh = reinterpret_cast<Hv*>(static_cast<P*>(a.dst) + (size_t)kPairs * p.plane) + cell;
+        if constexpr (ST == kFP32) {
 #pragma unroll
-        for (int i = 1; i < 9; ++i) dh[(size_t)(i - 1) * p.plane] = h[i];
-        a.hist[cell] = ux;
-        a.hist[p.plane + cell] = uy;
+            for (int i = 1; i < 9; ++i) dh[(size_t)(i - 1) * p.plane] = h[i];
+        } else {
+            // every slot is stored relative to this cell's new u (what the next step reads back):
+            // raw = (h_i / w_i - 3 rho c_i.u) S_h, two links per stochastic conversion
+            const float vx = p.kh_enc * ux, vy = p.kh_enc * uy;
+            const uint32_t key = (uint32_t)cell * 0xC2B2AE35u ^ a.seed;
+            const uint32_t b12 = cvt_rs2<ST>(fmaf(h[1], p.enc_h[1], -vx), fmaf(h[2], p.enc_h[2], -vy), rbits_of(key, 9));
+            const uint32_t b34 = cvt_rs2<ST>(fmaf(h[3], p.enc_h[3], vx), fmaf(h[4], p.enc_h[4], vy), rbits_of(key, 10));
+            const uint32_t b56 =
+                cvt_rs2<ST>(fmaf(h[5], p.enc_h[5], -(vx + vy)), fmaf(h[6], p.enc_h[6], vx - vy), rbits_of(key, 11));
+            const uint32_t b78 =
+                cvt_rs2<ST>(fmaf(h[7], p.enc_h[7], vx + vy), fmaf(h[8], p.enc_h[8], vy - vx), rbits_of(key, 12));
+            unsigned short* dh16 = reinterpret_cast<unsigned short*>(dh);
+            dh16[0 * p.plane] = (unsigned short)(b12 & 0xFFFFu);
+            dh16[1 * p.plane] = (unsigned short)(b12 >> 16);
+            dh16[2 * p.plane] = (unsigned short)(b34 & 0xFFFFu);
+            dh16[3 * p.plane] = (unsigned short)(b34 >> 16);
+            dh16[4 * p.plane] = (unsigned short)(b56 & 0xFFFFu);
+            dh16[5 * p.plane] = (unsigned short)(b56 >> 16);
+            dh16[6 * p.plane] = (unsigned short)(b78 & 0xFFFFu);
+            dh16[7 * p.plane] = (unsigned short)(b78 >> 16);
+        }
+        a.hist_dst[cell] = make_float2(ux, uy);
     }
 }
 
@@ -512,52 +737,70 @@ struct InitArgs {
     const double* __restrict__ ux;
     const double* __restrict__ uy;
     const double* __restrict__ P;
-    float* __restrict__ dst;
-    float* __restrict__ hist;
+    void* __restrict__ dst;
+    float2* __restrict__ hist;    // history buffer of the initial level
     unsigned* __restrict__ status;
     int langmuir;
     int walls;
 };
 
+template <int ST>
 __global__ void init_kernel(const __grid_constant__ InitArgs a) {
+    using T = Traits<ST>;
+    using P = typename T::P;
+    using Hv = typename T::H;
     const Phys& p = a.p;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return;
     const size_t o = (size_t)y * p.nx + x;
-    const double phi = a.phi[o], psi = a.psi[o], ux = a.ux[o], uy = a.uy[o], P = a.P[o];
-    bool bad = !(isfinite(phi) && isfinite(psi) && isfinite(ux) && isfinite(uy) && isfinite(P));
+    const double phi = a.phi[o], psi = a.psi[o], ux = a.ux[o], uy = a.uy[o], P_ = a.P[o];
+    bool bad = !(isfinite(phi) && isfinite(psi) && isfinite(ux) && isfinite(uy) && isfinite(P_));
     if (a.langmuir) bad = bad || !(psi < 1.0);
     if (bad) atomicOr(a.status, kStatusUnstable);
     const double rho = p.rho;
     const double uu = ux * ux + uy * uy;
-    float2* fg = reinterpret_cast<float2*>(a.dst);
-    float* hp = a.dst + (size_t)kPlaneH * p.plane;
+    P* fg = static_cast<P*>(a.dst);
+    Hv* hp = reinterpret_cast<Hv*>(fg + (size_t)kPairs * p.plane);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const double cu = cx(i) * ux + cy(i) * uy;
         const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
         const double feq = w * phi * (1.0 + 3.0 * cu);
         const double geq = w * psi * (1.0 + 3.0 * cu);
-        const double heq = w * (3.0 * P + 3.0 * rho * cu + 4.5 * rho * (cu * cu - uu / 3.0));
+        const double heq = w * (3.0 * P_ + 3.0 * rho * cu + 4.5 * rho * (cu * cu - uu / 3.0));
         // the first pull at x for direction i reads slot i of x - c_i, or, across a wall, the
         // opposite slot of x itself
-        int tx_ = x - cx(i), ty_ = y - cy(i), slot = i;
-        if (a.walls && (ty_ < 0 || ty_ >= p.ny)) {
-            tx_ = x;
-            ty_ = y;
+        int sx = x - cx(i), sy = y - cy(i), slot = i;
+        if (a.walls && (sy < 0 || sy >= p.ny)) {
+            sx = x;
+            sy = y;
             slot = opp(i);
         } else {
-            tx_ = (tx_ + p.nx) % p.nx;
-            ty_ = (ty_ + p.ny) % p.ny;
+            sx = (sx + p.nx) % p.nx;
+            sy = (sy + p.ny) % p.ny;
         }
-        const size_t cell = (size_t)ty_ * p.pitch + tx_;
-        fg[(size_t)slot * p.plane + cell] = make_float2((float)feq, (float)geq);
-        if (slot != 0) hp[(size_t)(slot - 1) * p.plane + cell] = (float)heq;
+        const size_t cell = (size_t)sy * p.pitch + sx;
+        if constexpr (ST == kFP32) {
+            fg[(size_t)slot * p.plane + cell] = make_float2((float)feq, (float)geq);
+            if (slot != 0) hp[(size_t)(slot - 1) * p.plane + cell] = (float)heq;
+        } else {
+            // the slot holds link `slot`'s value heq/feq/geq of link i (equal links unless across a
+            // wall, where slot = opp(i) with the same weight)
+            fg[(size_t)slot * p.plane + cell] = pack2<ST>(make_float2(
+                (float)((feq / w - p.phi_ref) / p.isc_f), (float)(geq / w / p.isc_g)));
+            if (slot != 0) {
+                // stored relative to the storing cell's velocity, as the step will read it back:
+                // the source cell for a plain link, this cell for a slot across a wall
+                const size_t so = (size_t)sy * p.nx + sx;
+                const double sux = (float)a.ux[so], suy = (float)a.uy[so];
+                const double vel = 3.0 * rho * (cx(slot) * sux + cy(slot) * suy);
+                hp[(size_t)(slot - 1) * p.plane + cell] = pack1<ST>((float)((heq / w - vel) * p.enc_h[slot] * w));
+            }
+        }
     }
     const size_t cell = (size_t)y * p.pitch + x;
-    a.hist[cell] = (float)ux;
-    a.hist[p.plane + cell] = (float)uy;
+    a.hist[cell] = make_float2((float)ux, (float)uy);
 }
 
 // ---- FP64 sums of phi or psi: every population slot is pulled exactly once per step, so the
@@ -580,24 +823,33 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
     return v;
 }
 
-// lane 0 sums f (phi), lane 1 sums g (psi)
-__global__ void __launch_bounds__(kReduceThreads) reduce_partial_kernel(const float* __restrict__ pairs, int lane,
+// lane 0 sums f (phi), lane 1 sums g (psi); 16-bit storage is decoded to its value first
+template <int ST>
+__global__ void __launch_bounds__(kReduceThreads) reduce_partial_kernel(const void* __restrict__ pops, int lane,
                                                                         int nx, int ny, int pitch, long long plane,
-                                                                        double* __restrict__ partials) {
+                                                                        Phys p, double* __restrict__ partials) {
+    using P = typename Traits<ST>::P;
     __shared__ double smem[32];
+    const P* pairs = static_cast<const P*>(pops);
     double acc = 0.0;
     // block b owns rows b, b + gridDim.x, ...; threads stride over (pair plane, x)
     for (int y = blockIdx.x; y < ny; y += gridDim.x) {
         for (int k = threadIdx.x; k < kPairs * nx; k += blockDim.x) {
             const int i = k / nx, x = k - i * nx;
-            acc += (double)pairs[2 * ((size_t)i * plane + (size_t)y * pitch + x) + lane];
+            const float2 v = raw2<ST>(pairs[(size_t)i * plane + (size_t)y * pitch + x]);
+            if constexpr (ST == kFP32) {
+                acc += (double)(lane ? v.y : v.x);
+            } else {
+                const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+                acc += lane ? w * (double)v.y * p.isc_g : w * ((double)v.x * p.isc_f + p.phi_ref);
+            }
         }
     }
     acc = block_sum(acc, smem);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-__global__ void __launch_bounds__(kReduceThreads) reduce_final_kernel(const double* __restrict__ partials, int n,
+static __global__ void __launch_bounds__(kReduceThreads) reduce_final_kernel(const double* __restrict__ partials, int n,
                                                                       double* __restrict__ out) {
     __shared__ double smem[32];
     double acc = 0.0;

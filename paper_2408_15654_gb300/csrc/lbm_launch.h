@@ -1,0 +1,72 @@
+// Launch helpers of the step kernel, one translation unit per storage mode
+// (step_fp32.cu, step_fp16.cu, step_bf16.cu) so that the instances compile in parallel.
+#pragma once
+#include <cstring>
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+// Every step launch uses programmatic dependent launch: the kernel waits (griddepcontrol.wait)
+// for the previous grid before touching memory, so the next launch may be scheduled during the
+// tail of this one.
+template <int ST>
+cudaError_t launch_step_impl(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = Smem<ST>::BYTES;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+#define LBM_LAUNCH_CASE(W_, L_)                                                              \
+    do {                                                                                     \
+        if (mode == kStep) return cudaLaunchKernelEx(&cfg, step_kernel<ST, W_, L_, kStep>, a);      \
+        return cudaLaunchKernelEx(&cfg, step_kernel<ST, W_, L_, kMoments>, a);               \
+    } while (0)
+    if (walls && langmuir) LBM_LAUNCH_CASE(true, true);
+    if (walls) LBM_LAUNCH_CASE(true, false);
+    if (langmuir) LBM_LAUNCH_CASE(false, true);
+    LBM_LAUNCH_CASE(false, false);
+#undef LBM_LAUNCH_CASE
+}
+
+template <int ST, bool W_, bool L_, int M_>
+cudaError_t prepare_one(int* bps) {
+    auto k = step_kernel<ST, W_, L_, M_>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, NT, Smem<ST>::BYTES);
+}
+
+// Opt all eight instances of storage mode ST into their dynamic shared memory; resident CTAs
+// per SM (the minimum over the instances).
+template <int ST>
+cudaError_t prepare_step_impl(int* blocks_per_sm) {
+    int b[8] = {0};
+    cudaError_t e = prepare_one<ST, false, false, kStep>(&b[0]);
+    if (e == cudaSuccess) e = prepare_one<ST, false, true, kStep>(&b[1]);
+    if (e == cudaSuccess) e = prepare_one<ST, true, false, kStep>(&b[2]);
+    if (e == cudaSuccess) e = prepare_one<ST, true, true, kStep>(&b[3]);
+    if (e == cudaSuccess) e = prepare_one<ST, false, false, kMoments>(&b[4]);
+    if (e == cudaSuccess) e = prepare_one<ST, false, true, kMoments>(&b[5]);
+    if (e == cudaSuccess) e = prepare_one<ST, true, false, kMoments>(&b[6]);
+    if (e == cudaSuccess) e = prepare_one<ST, true, true, kMoments>(&b[7]);
+    int m = b[0];
+    for (int k = 1; k < 8; ++k) m = b[k] < m ? b[k] : m;
+    *blocks_per_sm = m;
+    return e;
+}
+
+cudaError_t launch_step_fp32(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t s);
+cudaError_t launch_step_fp16(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t s);
+cudaError_t launch_step_bf16(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t s);
+cudaError_t prepare_step_fp32(int* blocks_per_sm);
+cudaError_t prepare_step_fp16(int* blocks_per_sm);
+cudaError_t prepare_step_bf16(int* blocks_per_sm);
+
+}  // namespace lbm

@@ -16,7 +16,8 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = range(7)
 LBM_BC_PERIODIC, LBM_BC_WALLS = 0, 1
 LBM_EOS_LINEAR, LBM_EOS_LANGMUIR = 0, 1
-LBM_STORE_FP32 = 0
+LBM_STORE_FP32, LBM_STORE_FP16, LBM_STORE_BF16 = 0, 1, 2
+STORAGE = {"fp32": LBM_STORE_FP32, "fp16": LBM_STORE_FP16, "bf16": LBM_STORE_BF16}
 LBM_MEM_HOST, LBM_MEM_DEVICE = 0, 1
 LBM_PHI, LBM_PSI, LBM_UX, LBM_UY, LBM_P = 1, 2, 4, 8, 16
 LBM_SUM_PHI, LBM_SUM_PSI = 0, 1
@@ -99,7 +100,8 @@ def make_params(p: dict) -> lbm_params:
     q.nx, q.ny = int(p["nx"]), int(p["ny"])
     q.bc_y = LBM_BC_WALLS if p.get("walls", False) else LBM_BC_PERIODIC
     q.eos = LBM_EOS_LANGMUIR if p.get("eos", "linear") == "langmuir" else LBM_EOS_LINEAR
-    q.storage = int(p.get("storage", LBM_STORE_FP32))
+    st = p.get("storage", LBM_STORE_FP32)
+    q.storage = STORAGE[st] if isinstance(st, str) else int(st)
     q.reserved = 0
     for k in ("u_top", "u_bot", "phiA", "phiB", "rhoA", "rhoB", "muA", "muB", "W", "M_phi", "D",
               "sigma0", "E0", "gx", "gy", "n_eps"):

@@ -50,9 +50,14 @@ def test_workspace_bytes_without_gpu():
     p, _ = W.shear_drop(512, 256)
     n = lbm.lbm_workspace_bytes(lbm.make_params(p))
     pitch = 512
-    # two buffers of 26 float planes, the u history, status and partials
-    assert n >= 2 * 26 * 256 * pitch * 4 + 2 * 256 * pitch * 4
-    assert n < 2 * 26 * 256 * pitch * 4 + 2 * 256 * pitch * 4 + 64 * 1024
+    # two buffers of 26 float planes, two (u_x, u_y) history buffers, status and partials
+    assert n >= 2 * 26 * 256 * pitch * 4 + 2 * 256 * pitch * 8
+    assert n < 2 * 26 * 256 * pitch * 4 + 2 * 256 * pitch * 8 + 64 * 1024
+    # 16-bit storage halves the population buffers
+    p["storage"] = "fp16"
+    n16 = lbm.lbm_workspace_bytes(lbm.make_params(p))
+    assert n16 >= 2 * 13 * 256 * pitch * 4 + 2 * 256 * pitch * 8
+    assert n16 < 2 * 13 * 256 * pitch * 4 + 2 * 256 * pitch * 8 + 64 * 1024
 
 
 @pytest.mark.parametrize("bad", [dict(nx=1), dict(ny=0), dict(rhoA=2.0), dict(W=0.0), dict(M_phi=-1.0),
