@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 NX, NY = 2048, 1024
 BYTES_PER_LUP = 26 * 4 * 2 + 2 * 4 * 2  # 26 live float populations and 2 history floats, read + written
 BYTES_PER_LUP_16 = 26 * 2 * 2 + 2 * 4 * 2  # the same populations stored in 16 bits
+BYTES_PER_LUP_FG = 18 * 2 * 2 + 8 * 4 * 2 + 2 * 4 * 2  # f, g in 16 bits, h in FP32
+HALF_MODES = {"fp16": BYTES_PER_LUP_16, "bf16": BYTES_PER_LUP_16, "fp16_fg": BYTES_PER_LUP_FG,
+              "bf16_fg": BYTES_PER_LUP_FG}
 METRIC = "MLUPS (3 lattices) and % HBM roofline, FP32 vs half-store; serving p50/p99"
 WORKLOAD = "sheared drop 2048x1024 (R=160, Re=1, Ca=0.2, Langmuir E0=0.2, psi0=0.3), FP32 storage"
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_2048x1024_fp32.json")
@@ -236,7 +239,7 @@ def run_ours(args):
 
     # the same workload with 16-bit population storage (FP32 arithmetic)
     half = {}
-    for st in ("fp16", "bf16"):
+    for st, bpl in HALF_MODES.items():
         hs = lbm.Lattice(dict(p, storage=st), stream=stream)
         hs.init(**f)
         hs.step(args.warmup)
@@ -251,10 +254,10 @@ def run_ours(args):
         if hs.status != lbm.LBM_OK:
             raise RuntimeError(f"unstable state in the {st} benchmark: {lbm.lbm_last_error()}")
         hv = cells * args.steps * world / (hms * 1e-3) / 1e6
-        hach = cells * BYTES_PER_LUP_16 / (e0.elapsed_time(e1) / args.steps * 1e-3) / 1e9
+        hach = cells * bpl / (e0.elapsed_time(e1) / args.steps * 1e-3) / 1e9
         half[st] = {"value": hv, "unit": "MLUPS", "ratio_vs_fp32": hv / (cells * args.steps * world / (ms_max * 1e-3) / 1e6),
                     "ms_per_step": hms / args.steps, "achieved_gbs": hach,
-                    "frac_of_measured_hbm": hach / measured_peak()[0], "algorithmic_bytes_per_lup": BYTES_PER_LUP_16}
+                    "frac_of_measured_hbm": hach / measured_peak()[0], "algorithmic_bytes_per_lup": bpl}
         hs.close()
 
     # roofline of the step kernel (one launch per step, so launch duration = step time)
@@ -295,7 +298,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": io_bytes / args.steps,
                     "job": f"lbm_init_fields(host) + lbm_step({args.steps}) + lbm_get_moments(host, all 5)"},
             "gpu_launches": args.steps,
-            "gpu_launches_half_store": 2 * args.steps,
+            "gpu_launches_half_store": len(HALF_MODES) * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

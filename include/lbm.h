@@ -52,6 +52,8 @@ extern "C" {
 #define LBM_STORE_FP32 0    /* populations stored as float                                   */
 #define LBM_STORE_FP16 1    /* as FP16 deviations from references (see lbm_workspace_bytes) */
 #define LBM_STORE_BF16 2    /* as BF16 deviations from references                            */
+#define LBM_STORE_FP16_FG 3 /* f and g as FP16 deviations, h as float                        */
+#define LBM_STORE_BF16_FG 4 /* f and g as BF16 deviations, h as float                        */
 
 #define LBM_MEM_HOST 0      /* pointer arguments are host memory (pageable or pinned)        */
 #define LBM_MEM_DEVICE 1    /* pointer arguments are device memory on the handle's device    */
@@ -78,7 +80,7 @@ typedef struct lbm_params {
     int32_t nx, ny;         /* grid size                                                     */
     int32_t bc_y;           /* LBM_BC_PERIODIC or LBM_BC_WALLS                               */
     int32_t eos;            /* LBM_EOS_LINEAR or LBM_EOS_LANGMUIR                            */
-    int32_t storage;        /* LBM_STORE_FP32, LBM_STORE_FP16 or LBM_STORE_BF16              */
+    int32_t storage;        /* one of LBM_STORE_* (arithmetic is FP32 in every mode)         */
     int32_t reserved;       /* must be 0                                                     */
     double u_top, u_bot;    /* x velocity of the top and bottom wall (LBM_BC_WALLS)          */
     double phiA, phiB;      /* order parameter of the pure phases (Sec. 2.1)                 */
@@ -100,16 +102,20 @@ typedef struct lbm_handle lbm_handle;
  * parameters.
  * Layout: the workspace starts with the two population buffers, each B * ny * pitch bytes rounded
  * up to a multiple of 256, with pitch = nx rounded up to a multiple of 32 and B = 104 (FP32
- * storage) or 52 (16-bit storage).  A buffer holds 9 planes of (f_i, g_i) pairs followed by 8
- * planes h_1..h_8 (h_0 never influences the step), each plane ny rows of pitch cells; after
- * lbm_init_fields and k steps the current state is buffer k mod 2 (buffer 0 at offset 0).
+ * storage), 52 (FP16, BF16) or 68 (FP16_FG, BF16_FG).  A buffer holds 9 planes of (f_i, g_i)
+ * pairs followed by 8 planes h_1..h_8 (h_0 never influences the step), each plane ny rows of
+ * pitch cells; after lbm_init_fields and k steps the current state is buffer k mod 2 (buffer 0
+ * at offset 0).
  * FP32 storage holds the values.  16-bit storage (FP16 / BF16, arithmetic still FP32) holds
- * each value divided by its lattice weight w_i, as a scaled deviation from a reference:
+ * each value divided by its lattice weight w_i, as a scaled deviation from a reference (the
+ * _FG modes store only f and g this way and h as FP32 values):
  * (f_i / w_i - phi_ref) S_f and (g_i / w_i) S_g with phi_ref = (phiA + phiB)/2, and
  * (h_i / w_i - 3 rho c_i.u) S_h with u the velocity that the cell holding the slot wrote to the
  * velocity history in the same step; S = (1, 256, 4096) for FP16 and 1 for BF16.  Dividing by
  * w_i makes the bulk equilibria exactly representable; removing 3 rho c_i.u keeps the pressure
- * part of h (about 1e-5) above the 16-bit rounding of the velocity part (about 1e-3).  The
+ * part of h (about 1e-5) above the 16-bit rounding of the velocity part (about 1e-3).  Steps
+ * store 16-bit values with stochastic rounding, its random bits a hash of the cell index and
+ * the step count (so a run is deterministic and a restored state continues bit for bit).  The
  * velocity history (two buffers of ny x pitch float pairs, alternating like the populations)
  * follows the population buffers. */
 int lbm_workspace_bytes(const lbm_params* p, size_t* bytes);

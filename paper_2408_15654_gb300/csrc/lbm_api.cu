@@ -16,6 +16,10 @@
 #include "lbm.h"
 #include "lbm_launch.h"
 
+static_assert(LBM_STORE_FP32 == lbm::kFP32 && LBM_STORE_FP16 == lbm::kFP16 && LBM_STORE_BF16 == lbm::kBF16 &&
+                  LBM_STORE_FP16_FG == lbm::kFP16FG && LBM_STORE_BF16_FG == lbm::kBF16FG,
+              "storage codes of the ABI and the kernels agree");
+
 namespace {
 
 thread_local std::string g_err;
@@ -77,8 +81,14 @@ int encode_map(CUtensorMap* tm, void* base, int es, int nx, int ny, int planes, 
 
 // Opt the step-kernel instances of storage mode st into their shared memory; CTAs per SM.
 int prepare_kernels(int st, int* blocks_per_sm) {
-    cudaError_t e = st == LBM_STORE_FP32 ? lbm::prepare_step_fp32(blocks_per_sm)
-                    : (st == LBM_STORE_FP16 ? lbm::prepare_step_fp16(blocks_per_sm) : lbm::prepare_step_bf16(blocks_per_sm));
+    cudaError_t e;
+    switch (st) {
+        case LBM_STORE_FP16: e = lbm::prepare_step_fp16(blocks_per_sm); break;
+        case LBM_STORE_BF16: e = lbm::prepare_step_bf16(blocks_per_sm); break;
+        case LBM_STORE_FP16_FG: e = lbm::prepare_step_fp16fg(blocks_per_sm); break;
+        case LBM_STORE_BF16_FG: e = lbm::prepare_step_bf16fg(blocks_per_sm); break;
+        default: e = lbm::prepare_step_fp32(blocks_per_sm); break;
+    }
     if (e != cudaSuccess) return fail(LBM_ECUDA, "kernel setup: %s", cudaGetErrorString(e));
     if (*blocks_per_sm < 1) return fail(LBM_ECUDA, "the step kernel does not fit on an SM");
     return LBM_OK;
@@ -102,7 +112,7 @@ int validate(const lbm_params* p) {
     if ((long long)p->nx * p->ny > (1LL << 30)) return fail(LBM_EINVAL, "grid too large");
     if (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_WALLS) return fail(LBM_EINVAL, "bad bc_y");
     if (p->eos != LBM_EOS_LINEAR && p->eos != LBM_EOS_LANGMUIR) return fail(LBM_EINVAL, "bad eos");
-    if (p->storage != LBM_STORE_FP32 && p->storage != LBM_STORE_FP16 && p->storage != LBM_STORE_BF16)
+    if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16_FG)
         return fail(LBM_EINVAL, "storage mode %d not supported", p->storage);
     if (p->reserved != 0) return fail(LBM_EINVAL, "reserved must be 0");
     if (!(p->phiA != p->phiB) || !(p->W > 0) || !(p->M_phi > 0) || !(p->D > 0))
@@ -192,28 +202,12 @@ lbm::Phys make_phys(const lbm_params* p, const Layout& L) {
     f.s4h_eff = (float)s4h;
     f.k4h = (float)(1.0 - 0.5 * s4h);
     f.tie_s4h = p->s_h[4] <= 0.0 ? 1 : 0;
-    // 16-bit storage: values divided by their weight, as deviations from references, times
-    // power-of-two scales that keep them normal in FP16 (BF16 has the FP32 exponent range)
-    const bool fp16 = p->storage == LBM_STORE_FP16;
-    const double S_f = 1.0, S_g = fp16 ? 256.0 : 1.0, S_h = fp16 ? 4096.0 : 1.0;
-    const double phi_ref = 0.5 * (p->phiA + p->phiB);
-    for (int i = 0; i < 9; ++i) {
-        const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
-        f.dec_f[i] = (float)(w / S_f);
-        f.dec_g[i] = (float)(w / S_g);
-        f.enc_f[i] = (float)(S_f / w);
-        f.enc_g[i] = (float)(S_g / w);
-        f.ref_f[i] = (float)(w * phi_ref);
-        f.dec_h[i] = (float)(w / S_h);
-        f.enc_h[i] = (float)(S_h / w);
-    }
-    f.eref_f = (float)(-phi_ref * S_f);
+    // 16-bit storage: references of the stored deviations (the scales are compile-time
+    // constants of each mode)
+    f.phi_ref = (float)(0.5 * (p->phiA + p->phiB));
     f.kh_axis = (float)(3.0 / 9.0 * p->rhoA);
     f.kh_diag = (float)(3.0 / 36.0 * p->rhoA);
-    f.kh_enc = (float)(3.0 * p->rhoA * S_h);
-    f.phi_ref = (float)phi_ref;
-    f.isc_f = (float)(1.0 / S_f);
-    f.isc_g = (float)(1.0 / S_g);
+    f.kh3 = (float)(3.0 * p->rhoA);
     f.u_top = (float)p->u_top;
     f.u_bot = (float)p->u_bot;
     f.n_eps2 = (float)(p->n_eps * p->n_eps);
@@ -269,9 +263,13 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
     const dim3 grid(h->tiles_x, h->tiles_y);
     const bool walls = h->prm.bc_y == LBM_BC_WALLS, lang = h->prm.eos == LBM_EOS_LANGMUIR;
     cudaError_t e;
-    if (h->prm.storage == LBM_STORE_FP16) e = lbm::launch_step_fp16(a, mode, walls, lang, grid, h->stream);
-    else if (h->prm.storage == LBM_STORE_BF16) e = lbm::launch_step_bf16(a, mode, walls, lang, grid, h->stream);
-    else e = lbm::launch_step_fp32(a, mode, walls, lang, grid, h->stream);
+    switch (h->prm.storage) {
+        case LBM_STORE_FP16: e = lbm::launch_step_fp16(a, mode, walls, lang, grid, h->stream); break;
+        case LBM_STORE_BF16: e = lbm::launch_step_bf16(a, mode, walls, lang, grid, h->stream); break;
+        case LBM_STORE_FP16_FG: e = lbm::launch_step_fp16fg(a, mode, walls, lang, grid, h->stream); break;
+        case LBM_STORE_BF16_FG: e = lbm::launch_step_bf16fg(a, mode, walls, lang, grid, h->stream); break;
+        default: e = lbm::launch_step_fp32(a, mode, walls, lang, grid, h->stream); break;
+    }
     if (e != cudaSuccess) return fail(LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
@@ -280,15 +278,17 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
 // then partials[blocks] ... written to *dres.
 int launch_reduce(int st, const void* pops, int lane, int nx, int ny, int pitch, size_t plane, const lbm::Phys& ph,
                   int blocks, double* partials, double* dres, cudaStream_t stream) {
-    if (st == LBM_STORE_FP16)
-        lbm::reduce_partial_kernel<lbm::kFP16><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch,
-                                                                                           (long long)plane, ph, partials);
-    else if (st == LBM_STORE_BF16)
-        lbm::reduce_partial_kernel<lbm::kBF16><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch,
-                                                                                           (long long)plane, ph, partials);
+    // the pair planes of the FG modes are stored like those of the all-16-bit modes
+    const long long pl = (long long)plane;
+    if (st == LBM_STORE_FP16 || st == LBM_STORE_FP16_FG)
+        lbm::reduce_partial_kernel<lbm::kFP16><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch, pl,
+                                                                                           ph, partials);
+    else if (st == LBM_STORE_BF16 || st == LBM_STORE_BF16_FG)
+        lbm::reduce_partial_kernel<lbm::kBF16><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch, pl,
+                                                                                           ph, partials);
     else
-        lbm::reduce_partial_kernel<lbm::kFP32><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch,
-                                                                                           (long long)plane, ph, partials);
+        lbm::reduce_partial_kernel<lbm::kFP32><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch, pl,
+                                                                                           ph, partials);
     LBM_CUDA(cudaGetLastError());
     lbm::reduce_final_kernel<<<1, lbm::kReduceThreads, 0, stream>>>(partials, blocks, dres);
     LBM_CUDA(cudaGetLastError());
@@ -402,9 +402,9 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
     h->partials = reinterpret_cast<double*>(h->ws + L.off_partials);
     int bps = 0;
     rc = prepare_kernels(p->storage, &bps);
-    const bool half = p->storage != LBM_STORE_FP32;
-    const int es_pair = half ? 4 : 8, es_h = half ? 2 : 4;
-    const unsigned hbw = half ? lbm::Traits<lbm::kFP16>::H_BW : lbm::Traits<lbm::kFP32>::H_BW;
+    const bool pair16 = lbm::pair_is_16bit(p->storage), h16 = lbm::h_is_16bit(p->storage);
+    const int es_pair = pair16 ? 4 : 8, es_h = h16 ? 2 : 4;
+    const unsigned hbw = h16 ? lbm::Traits<lbm::kFP16>::H_BW : lbm::Traits<lbm::kFP32>::H_BW;
     for (int b = 0; b < 2 && !rc; ++b) {
         rc = encode_map(&h->tm_fg[b], h->pops[b], es_pair, p->nx, p->ny, lbm::kPairs, L.pitch, L.plane, lbm::BW,
                         lbm::BH, 1);
@@ -412,7 +412,7 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
         if (!rc) rc = encode_map(&h->tm_h[b], hbase, es_h, p->nx, p->ny, lbm::kHPlanes, L.pitch, L.plane, hbw, lbm::TY, 1);
     }
     for (int b = 0; b < 2 && !rc; ++b)
-        rc = half ? encode_map(&h->tm_hist[b], h->hist[b], 8, p->nx, p->ny, 1, L.pitch, L.plane, lbm::BW, lbm::BH, 1)
+        rc = h16 ? encode_map(&h->tm_hist[b], h->hist[b], 8, p->nx, p->ny, 1, L.pitch, L.plane, lbm::BW, lbm::BH, 1)
                   : encode_map(&h->tm_hist[b], h->hist[b], 8, p->nx, p->ny, 1, L.pitch, L.plane, lbm::TX, lbm::TY, 1);
     if (rc) {
         delete h;
@@ -440,7 +440,7 @@ int lbm_init_fields(lbm_handle* h, const double* phi, const double* psi, const d
     const int tgt = 0;
     if (mem == LBM_MEM_HOST) {
         // stage through the buffer that becomes dead (5 doubles per cell fit in a buffer's
-        // 104 or 52 bytes per cell)
+        // 104, 68 or 52 bytes per cell)
         double* stage = reinterpret_cast<double*>(h->pops[tgt ^ 1]);
         for (int k = 0; k < 5; ++k) {
             LBM_CUDA(cudaMemcpyAsync(stage + k * n, d[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -459,9 +459,13 @@ int lbm_init_fields(lbm_handle* h, const double* phi, const double* psi, const d
     a.langmuir = h->prm.eos == LBM_EOS_LANGMUIR;
     a.walls = h->prm.bc_y == LBM_BC_WALLS;
     const dim3 block(32, 8), grid((h->prm.nx + 31) / 32, (h->prm.ny + 7) / 8);
-    if (h->prm.storage == LBM_STORE_FP16) lbm::init_kernel<lbm::kFP16><<<grid, block, 0, h->stream>>>(a);
-    else if (h->prm.storage == LBM_STORE_BF16) lbm::init_kernel<lbm::kBF16><<<grid, block, 0, h->stream>>>(a);
-    else lbm::init_kernel<lbm::kFP32><<<grid, block, 0, h->stream>>>(a);
+    switch (h->prm.storage) {
+        case LBM_STORE_FP16: lbm::init_kernel<lbm::kFP16><<<grid, block, 0, h->stream>>>(a); break;
+        case LBM_STORE_BF16: lbm::init_kernel<lbm::kBF16><<<grid, block, 0, h->stream>>>(a); break;
+        case LBM_STORE_FP16_FG: lbm::init_kernel<lbm::kFP16FG><<<grid, block, 0, h->stream>>>(a); break;
+        case LBM_STORE_BF16_FG: lbm::init_kernel<lbm::kBF16FG><<<grid, block, 0, h->stream>>>(a); break;
+        default: lbm::init_kernel<lbm::kFP32><<<grid, block, 0, h->stream>>>(a); break;
+    }
     LBM_CUDA(cudaGetLastError());
     LBM_CUDA(cudaStreamSynchronize(h->stream));
     h->cur = tgt;

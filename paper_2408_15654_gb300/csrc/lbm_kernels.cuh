@@ -3,27 +3,29 @@
 // Data layout in HBM (one population buffer, ny rows x `pitch` cells per plane):
 //   9 pair planes  (f_i, g_i), i = 0..8      phase field (Sec. 3.1) and surfactant (Sec. 3.2)
 //   8 planes       h_1..h_8                  flow (Sec. 3.3)
-// in FP32 (float2 / float) or, for the 16-bit storage modes, as FP16 / BF16 deviations
-// (half2 / half).  f_i and g_i stream along the same link, so they travel and collide together:
-// one access per pair, and Blackwell's packed FP32x2 arithmetic runs both collisions at once.
-// h_0 is never stored: column 0 of M^-1 is e_0 and rows 1..8 of M do not see h_0, so h_0 feeds
-// only itself (Sec. 3.3, Sec. 4).  The u history is one float2 plane (u_x, u_y).
+// f_i and g_i stream along the same link, so they travel and collide together: one access per
+// pair, and Blackwell's packed FP32x2 arithmetic runs both collisions at once.  h_0 is never
+// stored: column 0 of M^-1 is e_0 and rows 1..8 of M do not see h_0, so h_0 feeds only itself
+// (Sec. 3.3, Sec. 4).  The u history is one float2 plane (u_x, u_y) per buffer.
 // A buffer holds the post-collision populations of the previous step at the cell that produced
 // them; a step pulls q_i(x) = q*_i(x - c_i) ("pull" streaming), so it writes only its own cell
 // and two buffers alternate.  Across a wall the missing link is the cell's own opposite slot,
 // into which the previous step already folded the moving-wall term (half-way bounce-back, Sec. 4).
 //
-// 16-bit storage.  Every value is stored divided by its lattice weight, as a scaled deviation
-// from a reference:
+// Storage modes: FP32; FP16 or BF16 for all 26 populations; FP16 or BF16 for the 18 of f and g
+// with h kept in FP32.  16-bit values are stored divided by their lattice weight, as scaled
+// deviations from a reference:
 //   (f_i, g_i):  ((f_i / w_i - phi_ref) S_f, (g_i / w_i) S_g)   phi_ref = (phiA + phiB)/2
 //   h_i:         (h_i / w_i - 3 rho c_i.u(x_s)) S_h                x_s = the cell that stored the slot,
 // where u(x_s) is the velocity that cell wrote to the u history in the same step.  Dividing by
 // w_i makes the bulk equilibria (phi = phiA or phiB, psi = 0, u = 0) exactly representable, so
 // the bulk does not drift by repeated rounding; taking away the first-order velocity part keeps
 // the pressure (1e-5 against a velocity part of 1e-3) above the 16-bit rounding.  The step
-// stores with stochastic rounding (Blackwell's cvt.rs, random bits from a hash of cell, step and
-// link): in a steady flow a cell rounds nearly the same values every step, and round-to-nearest
-// would then add the same error every step.  All arithmetic stays in FP32.
+// stores with stochastic rounding (Blackwell's cvt.rs, random bits from a hash of cell and step):
+// in a steady flow a cell rounds nearly the same values every step, and round-to-nearest would
+// then add the same error every step.  All arithmetic stays in FP32; f and g are collided as the
+// deviations f_i - w_i phi_ref that the storage holds (the reference enters only the even
+// moments, through phi - phi_ref).
 //
 // Velocity order (the columns of the printed moment matrix M, Sec. 4):
 //   0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
@@ -47,32 +49,53 @@ static_assert(opp(5) == 7 && opp(7) == 5 && opp(6) == 8 && opp(8) == 6, "diagona
 constexpr int kPairs = 9;       // (f_i, g_i) planes
 constexpr int kHPlanes = 8;     // h_1..h_8 planes
 
-enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
+enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2, kFP16FG = 3, kBF16FG = 4 };
 
-// Storage traits: element types, sizes, and the x origin / width of the h boxes (TMA x
-// coordinates must be multiples of 16 bytes: 4 cells of 4 bytes, 8 cells of 2 bytes).
+// Storage traits: element types, compile-time scales, and the x origin / width of the h boxes
+// (TMA x coordinates must be multiples of 16 bytes: 4 cells of 4 bytes, 8 cells of 2 bytes).
 template <int ST> struct Traits;
 template <> struct Traits<kFP32> {
     using P = float2;
     using H = float;
+    static constexpr bool kPair16 = false, kH16 = false;
     static constexpr int H_X0 = 4, H_BW = 40;
-    static constexpr bool kHalo = false;  // the u history box needs no ring
+    static constexpr float SF = 1.f, SG = 1.f, SH = 1.f;
 };
 template <> struct Traits<kFP16> {
     using P = __half2;
     using H = __half;
+    static constexpr bool kPair16 = true, kH16 = true;
     static constexpr int H_X0 = 8, H_BW = 48;
-    static constexpr bool kHalo = true;   // h pulls need the source cell's u
+    static constexpr float SF = 1.f, SG = 256.f, SH = 4096.f;  // keep the deviations normal in FP16
 };
 template <> struct Traits<kBF16> {
     using P = __nv_bfloat162;
     using H = __nv_bfloat16;
+    static constexpr bool kPair16 = true, kH16 = true;
     static constexpr int H_X0 = 8, H_BW = 48;
-    static constexpr bool kHalo = true;
+    static constexpr float SF = 1.f, SG = 1.f, SH = 1.f;        // BF16 has the FP32 exponent range
+};
+template <> struct Traits<kFP16FG> {
+    using P = __half2;
+    using H = float;
+    static constexpr bool kPair16 = true, kH16 = false;
+    static constexpr int H_X0 = 4, H_BW = 40;
+    static constexpr float SF = 1.f, SG = 256.f, SH = 1.f;
+};
+template <> struct Traits<kBF16FG> {
+    using P = __nv_bfloat162;
+    using H = float;
+    static constexpr bool kPair16 = true, kH16 = false;
+    static constexpr int H_X0 = 4, H_BW = 40;
+    static constexpr float SF = 1.f, SG = 1.f, SH = 1.f;
 };
 
-// Bytes of one population buffer per cell: 9 pairs + 8 h values.
-__host__ __device__ constexpr int pop_bytes_per_cell(int st) { return st == kFP32 ? 9 * 8 + 8 * 4 : 9 * 4 + 8 * 2; }
+// Bytes of one population buffer per cell: 9 (f, g) pairs + 8 h values.
+__host__ __device__ constexpr int pop_bytes_per_cell(int st) {
+    return st == kFP32 ? 9 * 8 + 8 * 4 : (st == kFP16 || st == kBF16 ? 9 * 4 + 8 * 2 : 9 * 4 + 8 * 4);
+}
+__host__ __device__ constexpr bool pair_is_16bit(int st) { return st != kFP32; }
+__host__ __device__ constexpr bool h_is_16bit(int st) { return st == kFP16 || st == kBF16; }
 
 // Physical constants in FP32, precomputed on the host from lbm_params.
 struct Phys {
@@ -94,15 +117,10 @@ struct Phys {
     int tie_s4h;              // 1: s4^h = s2^h
     float u_top, u_bot;
     float n_eps2;             // n_eps^2
-    // 16-bit storage (unused for FP32): per link i, decode q = raw * dec + ref and encode
-    // raw = q * enc + eref; h additionally carries the velocity term 3 w_i rho c_i.u
-    float dec_f[9], dec_g[9], enc_f[9], enc_g[9];  // w_i / S and S / w_i
-    float ref_f[9];           // w_i phi_ref
-    float eref_f;             // -phi_ref S_f
-    float dec_h[9], enc_h[9]; // w_i / S_h and S_h / w_i
-    float kh_axis, kh_diag;   // 3 w_i rho for axis and diagonal links
-    float kh_enc;             // 3 rho S_h
-    float phi_ref, isc_f, isc_g;  // phi_ref and 1 / S of the (f, g) lanes
+    // 16-bit storage (unused for FP32)
+    float phi_ref;            // (phiA + phiB) / 2
+    float kh_axis, kh_diag;   // 3 w_i rho for axis and diagonal links (h decode)
+    float kh3;                // 3 rho (h encode, before the scale)
 };
 
 enum Mode { kStep = 0, kMoments = 1 };
@@ -110,7 +128,7 @@ enum Mode { kStep = 0, kMoments = 1 };
 // Tile geometry.  A CTA of NT threads owns a TX x TY tile, one cell per thread.  TMA stages:
 //   pair plane i: box of BW x BH pairs,    row r, col c <-> (x0 - 4 + c, y0 - 1 - cy(i) + r)
 //   h plane i:    box of H_BW x TY values, row r, col c <-> (x0 - H_X0 + c, y0 - cy(i) + r)
-//   u history:    box of TX x TY (FP32) or BW x BH (16-bit, one-cell ring) float2
+//   u history:    box of TX x TY, or BW x BH (one-cell ring) when h is 16-bit, float2
 // so extended-tile cell (ex, ey) (global (x0 - 1 + ex, y0 - 1 + ey)) pulls pair i from
 // [ey][ex + 3 - cx(i)], the own cell (tx, ty) pulls h_i from [ty][tx + H_X0 - cx(i)], and the
 // own cell's unshifted post-collision pair i sits at [ty + 1 + cy(i)][tx + 4].
@@ -129,17 +147,18 @@ __host__ __device__ constexpr int round128(int b) { return (b + 127) / 128 * 128
 // Shared-memory layout (bytes) of one tile for storage mode ST.
 template <int ST> struct Smem {
     using T = Traits<ST>;
+    static constexpr bool kHalo = T::kH16;  // the 16-bit h decode needs the source cell's u
     static constexpr int FG_SLOT = round128(FG_BOX * (int)sizeof(typename T::P));
     static constexpr int H_BOX = T::H_BW * TY;
     static constexpr int H_SLOT = round128(H_BOX * (int)sizeof(typename T::H));
-    static constexpr int HIST_W = T::kHalo ? BW : TX, HIST_H = T::kHalo ? BH : TY;
+    static constexpr int HIST_W = kHalo ? BW : TX, HIST_H = kHalo ? BH : TY;
     static constexpr int HIST_BYTES = HIST_W * HIST_H * 8;
     static constexpr int FG = 0;
     static constexpr int H = FG + kPairs * FG_SLOT;
     static constexpr int HIST = H + kHPlanes * H_SLOT;
     static constexpr int PP = HIST + round128(HIST_BYTES);
     static constexpr int BAR = PP + NE * 8;
-    static constexpr int BYTES = BAR + 16 + 128;  // + mbarrier + alignment slack
+    static constexpr int BYTES = BAR + 16;
     static constexpr unsigned TX_BYTES =
         (unsigned)(kPairs * FG_BOX * sizeof(typename T::P) + kHPlanes * H_BOX * sizeof(typename T::H) + HIST_BYTES);
 };
@@ -171,59 +190,61 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // ---- storage conversions ----
-template <int ST> __device__ __forceinline__ float2 raw2(typename Traits<ST>::P v);
-template <> __device__ __forceinline__ float2 raw2<kFP32>(float2 v) { return v; }
-template <> __device__ __forceinline__ float2 raw2<kFP16>(__half2 v) { return __half22float2(v); }
-template <> __device__ __forceinline__ float2 raw2<kBF16>(__nv_bfloat162 v) { return __bfloat1622float2(v); }
-template <int ST> __device__ __forceinline__ typename Traits<ST>::P pack2(float2 v);
-template <> __device__ __forceinline__ float2 pack2<kFP32>(float2 v) { return v; }
-template <> __device__ __forceinline__ __half2 pack2<kFP16>(float2 v) { return __float22half2_rn(v); }
-template <> __device__ __forceinline__ __nv_bfloat162 pack2<kBF16>(float2 v) { return __float22bfloat162_rn(v); }
-template <int ST> __device__ __forceinline__ float raw1(typename Traits<ST>::H v);
-template <> __device__ __forceinline__ float raw1<kFP32>(float v) { return v; }
-template <> __device__ __forceinline__ float raw1<kFP16>(__half v) { return __half2float(v); }
-template <> __device__ __forceinline__ float raw1<kBF16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <int ST> __device__ __forceinline__ typename Traits<ST>::H pack1(float v);
-template <> __device__ __forceinline__ float pack1<kFP32>(float v) { return v; }
-template <> __device__ __forceinline__ __half pack1<kFP16>(float v) { return __float2half_rn(v); }
-template <> __device__ __forceinline__ __nv_bfloat16 pack1<kBF16>(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ float2 raw2(float2 v) { return v; }
+__device__ __forceinline__ float2 raw2(__half2 v) { return __half22float2(v); }
+__device__ __forceinline__ float2 raw2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+__device__ __forceinline__ float raw1(float v) { return v; }
+__device__ __forceinline__ float raw1(__half v) { return __half2float(v); }
+__device__ __forceinline__ float raw1(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T pack2(float2 v);
+template <> __device__ __forceinline__ float2 pack2<float2>(float2 v) { return v; }
+template <> __device__ __forceinline__ __half2 pack2<__half2>(float2 v) { return __float22half2_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat162 pack2<__nv_bfloat162>(float2 v) { return __float22bfloat162_rn(v); }
+template <typename T> __device__ __forceinline__ T pack1(float v);
+template <> __device__ __forceinline__ float pack1<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half pack1<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 pack1<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-// (f_i, g_i) from storage and back
-template <int ST, int I> __device__ __forceinline__ float2 dec_pair(typename Traits<ST>::P v, const Phys& p) {
-    if constexpr (ST == kFP32) return v;
-    else return fma2(raw2<ST>(v), make_float2(p.dec_f[I], p.dec_g[I]), make_float2(p.ref_f[I], 0.f));
-}
-template <int ST, int I> __device__ __forceinline__ typename Traits<ST>::P enc_pair(float2 q, const Phys& p) {
-    if constexpr (ST == kFP32) return q;
-    else return pack2<ST>(fma2(q, make_float2(p.enc_f[I], p.enc_g[I]), make_float2(p.eref_f, 0.f)));
-}
-
-// Two FP32 values to a 16-bit pair with stochastic rounding (lo in the low half).
-template <int ST> __device__ __forceinline__ uint32_t cvt_rs2(float lo, float hi, uint32_t rbits) {
-    uint32_t out;
-    if constexpr (ST == kFP16) asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(out) : "f"(hi), "f"(lo), "r"(rbits));
-    else asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(out) : "f"(hi), "f"(lo), "r"(rbits));
-    return out;
-}
-// Random bits for link k of a cell: a multiply-xorshift hash of the cell's per-step key.
-__device__ __forceinline__ uint32_t rbits_of(uint32_t key, uint32_t k) {
-    uint32_t h = key + k * 0x9E3779B9u;
-    h ^= h >> 15;
-    h *= 0x2C1B3C6Du;
-    h ^= h >> 12;
-    return h;
-}
-// (f_i, g_i) to stochastically rounded 16-bit storage
-template <int ST, int I> __device__ __forceinline__ typename Traits<ST>::P enc_pair_rs(float2 q, const Phys& p,
-                                                                                      uint32_t key) {
-    const float2 v = fma2(q, make_float2(p.enc_f[I], p.enc_g[I]), make_float2(p.eref_f, 0.f));
-    const uint32_t bits = cvt_rs2<ST>(v.x, v.y, rbits_of(key, I));
-    return *reinterpret_cast<const typename Traits<ST>::P*>(&bits);
+// (f_i, g_i) from storage: the values (FP32), or the deviations (f_i - w_i phi_ref, g_i) (16-bit)
+template <int ST, int I> __device__ __forceinline__ float2 dec_pair(typename Traits<ST>::P v) {
+    using T = Traits<ST>;
+    if constexpr (!T::kPair16) return v;
+    else return mul2(raw2(v), make_float2(wgt(I) / T::SF, wgt(I) / T::SG));
 }
 // 3 w_i rho c_i.u: the first-order velocity part of h_eq removed before 16-bit storage
 template <int I> __device__ __forceinline__ float h_vel(float2 u, const Phys& p) {
     const float k = I <= 4 ? p.kh_axis : p.kh_diag;
     return k * ((float)cx(I) * u.x + (float)cy(I) * u.y);
+}
+
+// Two FP32 values to a 16-bit pair with stochastic rounding (lo in the low half).
+template <typename T> __device__ __forceinline__ uint32_t cvt_rs2(float lo, float hi, uint32_t rbits) {
+    uint32_t out;
+    if constexpr (__is_same(T, __half2))
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(out) : "f"(hi), "f"(lo), "r"(rbits));
+    else
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(out) : "f"(hi), "f"(lo), "r"(rbits));
+    return out;
+}
+// Per-cell random word for the stochastic rounding of one step (multiply-xorshift hash).
+__device__ __forceinline__ uint32_t cell_key(uint32_t cell, uint32_t seed) {
+    uint32_t h = cell * 0x9E3779B1u ^ seed;
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    return h;
+}
+// Random bits of conversion k of a cell: a rotation of the cell's word.  Every rounding stays
+// unbiased; conversions of one cell share bits, which correlates their errors but adds no bias.
+__device__ __forceinline__ uint32_t rbits_of(uint32_t key, int k) { return __funnelshift_l(key, key, 5 * k + 1); }
+// (f_i, g_i) deviations to stochastically rounded 16-bit storage
+template <int ST, int I> __device__ __forceinline__ typename Traits<ST>::P enc_pair_rs(float2 q, uint32_t key) {
+    using T = Traits<ST>;
+    const float2 v = mul2(q, make_float2(T::SF / wgt(I), T::SG / wgt(I)));
+    const uint32_t bits = cvt_rs2<typename T::P>(v.x, v.y, rbits_of(key, I));
+    return *reinterpret_cast<const typename T::P*>(&bits);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
@@ -267,15 +288,18 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
 // For a scalar s (phi or psi) the equilibrium w_i s (1 + c_i.u/cs2) has moments
 // (s, s ux, s uy, s/3, s/3, 0, s ux/3, s uy/3, s/9); the source w_i c_i.V has moments
 // (0, cs2 Vx, cs2 Vy, 0, 0, 0, Vx/9, Vy/9, 0) with cs2 V = (vx, vy).  dm_0 = 0.
+// q may hold deviations q_i - w_i r (r per lane): the odd moments are unchanged, the even ones
+// drop r times (1, 1/3, 1/3, 1/9), so they are compared with sr = s - r.
 // nS_k = -s_k and K_k = 1 - s_k/2 per lane (f, g).
-__device__ __forceinline__ void collide_pair(float2 q[9], float2 s, float ux, float uy, float2 vx, float2 vy,
-                                             float2 nS1, float2 nS2, float2 nS3, float2 nS4, float2 K1, float2 K3) {
+__device__ __forceinline__ void collide_pair(float2 q[9], float2 s, float2 sr, float ux, float uy, float2 vx,
+                                             float2 vy, float2 nS1, float2 nS2, float2 nS3, float2 nS4, float2 K1,
+                                             float2 K3) {
     const float2 third = bc(1.f / 3.f);
     const float2 a = add2(q[5], q[7]), b = add2(q[6], q[8]), c = sub2(q[5], q[7]), d = sub2(q[6], q[8]);
     const float2 m5 = sub2(a, b), m8 = add2(a, b), m6 = sub2(c, d), m7 = add2(c, d);
     const float2 m1 = add2(sub2(q[1], q[3]), m6), m2 = add2(sub2(q[2], q[4]), m7);
     const float2 m3 = add2(add2(q[1], q[3]), m8), m4 = add2(add2(q[2], q[4]), m8);
-    const float2 su = mul2(s, bc(ux)), sv = mul2(s, bc(uy)), s3 = mul2(s, third);
+    const float2 su = mul2(s, bc(ux)), sv = mul2(s, bc(uy)), s3 = mul2(sr, third);
     const float2 d1 = fma2(nS1, sub2(m1, su), mul2(K1, vx));
     const float2 d2 = fma2(nS1, sub2(m2, sv), mul2(K1, vy));
     const float2 d3 = mul2(nS2, sub2(m3, s3));
@@ -283,7 +307,7 @@ __device__ __forceinline__ void collide_pair(float2 q[9], float2 s, float ux, fl
     const float2 d5 = mul2(nS2, m5);
     const float2 d6 = fma2(nS3, fma2(su, bc(-1.f / 3.f), m6), mul2(K3, mul2(vx, third)));
     const float2 d7 = fma2(nS3, fma2(sv, bc(-1.f / 3.f), m7), mul2(K3, mul2(vy, third)));
-    const float2 d8 = mul2(nS4, fma2(s, bc(-1.f / 9.f), m8));
+    const float2 d8 = mul2(nS4, fma2(sr, bc(-1.f / 9.f), m8));
     const float2 A = sub2(d1, d6), B = sub2(d3, d8), C = sub2(d2, d7), D = sub2(d4, d8);
     const float2 E = add2(d8, d5), F = sub2(d8, d5), G = add2(d6, d7), H = sub2(d7, d6);
     const float2 half = bc(0.5f), quarter = bc(0.25f);
@@ -312,7 +336,7 @@ __device__ void patch_edges(const StepArgs& a, unsigned char* sm, int x0, int y0
     const P* __restrict__ srcFG = static_cast<const P*>(a.src);
     const Hv* __restrict__ srcH = reinterpret_cast<const Hv*>(srcFG + (size_t)kPairs * p.plane);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int NBOX = kPairs + kHPlanes + (T::kHalo ? 1 : 0);
+    constexpr int NBOX = kPairs + kHPlanes + (S::kHalo ? 1 : 0);
     for (int pl = warp; pl < NBOX; pl += NT / 32) {
         const int kind = pl < kPairs ? 0 : (pl < kPairs + kHPlanes ? 1 : 2);  // pair, h, history
         const int i = kind == 0 ? pl : (kind == 1 ? pl - kPairs + 1 : 0);      // direction
@@ -382,13 +406,13 @@ __device__ __forceinline__ float load_h(const unsigned char* sm, const float2* H
     using T = Traits<ST>;
     using S = Smem<ST>;
     const typename T::H v = reinterpret_cast<const typename T::H*>(sm + S::H + (I - 1) * S::H_SLOT)[ty * T::H_BW + tx + T::H_X0 - cx(I)];
-    if constexpr (ST == kFP32) {
+    if constexpr (!T::kH16) {
         return v;
     } else {
         // the slot was stored with the first-order velocity part of the cell that stored it:
         // the source cell x - c_i, or across a wall the own cell (whose opposite slot it is)
         const float2 us = bb ? make_float2(-uown.x, -uown.y) : Hist[(ty + 1 - cy(I)) * BW + tx + 4 - cx(I)];
-        return fmaf(raw1<ST>(v), p.dec_h[I], h_vel<I>(us, p));
+        return fmaf(raw1(v), wgt(I) / T::SH, h_vel<I>(us, p));
     }
 }
 
@@ -403,8 +427,7 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     using T = Traits<ST>;
     using S = Smem<ST>;
     using P = typename T::P;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    extern __shared__ __align__(1024) unsigned char sm[];
     const P* FG = reinterpret_cast<const P*>(sm + S::FG);
     const float2* Hist = reinterpret_cast<const float2*>(sm + S::HIST);
     float2* PP = reinterpret_cast<float2*>(sm + S::PP);
@@ -433,7 +456,7 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
 #pragma unroll
         for (int i = 1; i < 9; ++i)
             tma_load_3d(sm + S::H + (i - 1) * S::H_SLOT, &a.tm_h, x0 - T::H_X0, y0 - cy(i), i - 1, mbar);
-        if constexpr (T::kHalo) tma_load_3d(sm + S::HIST, &a.tm_hist, x0 - 4, y0 - 1, 0, mbar);
+        if constexpr (S::kHalo) tma_load_3d(sm + S::HIST, &a.tm_hist, x0 - 4, y0 - 1, 0, mbar);
         else tma_load_3d(sm + S::HIST, &a.tm_hist, x0, y0, 0, mbar);
     }
     __syncthreads();
@@ -446,25 +469,28 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     const int tx = t % TX, ty = t / TX;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = (x < p.nx) && (y < p.ny);
+    // (phi, psi) references of the stored deviations (zero for FP32 storage)
+    const float2 ref = T::kPair16 ? make_float2(p.phi_ref, 0.f) : make_float2(0.f, 0.f);
 
     // ---- (phi, psi) of the extended tile: the own cell (pulled pairs kept for the collision)
     //      and the ring; cells beyond a wall take the value of the adjacent fluid row ----
     const int eo = (ty + 1) * EX + (tx + 1);
+    constexpr int SLOT = S::FG_SLOT / (int)sizeof(P);
     float2 q[9];
     {
         int row = ty + 1;
         if (WALLS && y >= p.ny) row = p.ny - y0;
         const P* base = FG + row * BW + tx + 4;
-        q[0] = dec_pair<ST, 0>(base[0 * S::FG_SLOT / (int)sizeof(P) - cx(0)], p);
-        q[1] = dec_pair<ST, 1>(base[1 * S::FG_SLOT / (int)sizeof(P) - cx(1)], p);
-        q[2] = dec_pair<ST, 2>(base[2 * S::FG_SLOT / (int)sizeof(P) - cx(2)], p);
-        q[3] = dec_pair<ST, 3>(base[3 * S::FG_SLOT / (int)sizeof(P) - cx(3)], p);
-        q[4] = dec_pair<ST, 4>(base[4 * S::FG_SLOT / (int)sizeof(P) - cx(4)], p);
-        q[5] = dec_pair<ST, 5>(base[5 * S::FG_SLOT / (int)sizeof(P) - cx(5)], p);
-        q[6] = dec_pair<ST, 6>(base[6 * S::FG_SLOT / (int)sizeof(P) - cx(6)], p);
-        q[7] = dec_pair<ST, 7>(base[7 * S::FG_SLOT / (int)sizeof(P) - cx(7)], p);
-        q[8] = dec_pair<ST, 8>(base[8 * S::FG_SLOT / (int)sizeof(P) - cx(8)], p);
-        float2 s = make_float2(0.f, 0.f);
+        q[0] = dec_pair<ST, 0>(base[0 * SLOT - cx(0)]);
+        q[1] = dec_pair<ST, 1>(base[1 * SLOT - cx(1)]);
+        q[2] = dec_pair<ST, 2>(base[2 * SLOT - cx(2)]);
+        q[3] = dec_pair<ST, 3>(base[3 * SLOT - cx(3)]);
+        q[4] = dec_pair<ST, 4>(base[4 * SLOT - cx(4)]);
+        q[5] = dec_pair<ST, 5>(base[5 * SLOT - cx(5)]);
+        q[6] = dec_pair<ST, 6>(base[6 * SLOT - cx(6)]);
+        q[7] = dec_pair<ST, 7>(base[7 * SLOT - cx(7)]);
+        q[8] = dec_pair<ST, 8>(base[8 * SLOT - cx(8)]);
+        float2 s = ref;
 #pragma unroll
         for (int i = 0; i < 9; ++i) s = add2(s, q[i]);
         PP[eo] = s;
@@ -481,17 +507,17 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
             if (gy < 0) row = 1 - y0;
             else if (gy >= p.ny) row = p.ny - y0;
         }
-        // phi = sum_i w_i (raw_i / S + ref) = (sum_i w_i raw_i) / S + phi_ref for 16-bit storage
         const P* base = FG + row * BW + ex + 3;
-        float2 s = make_float2(0.f, 0.f);
-        if constexpr (ST == kFP32) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) s = add2(s, base[i * S::FG_SLOT / (int)sizeof(P) - cx(i)]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) s = fma2(bc(wgt(i)), raw2<ST>(base[i * S::FG_SLOT / (int)sizeof(P) - cx(i)]), s);
-            s = fma2(s, make_float2(p.isc_f, p.isc_g), make_float2(p.phi_ref, 0.f));
-        }
+        float2 s = ref;
+        s = add2(s, dec_pair<ST, 0>(base[0 * SLOT - cx(0)]));
+        s = add2(s, dec_pair<ST, 1>(base[1 * SLOT - cx(1)]));
+        s = add2(s, dec_pair<ST, 2>(base[2 * SLOT - cx(2)]));
+        s = add2(s, dec_pair<ST, 3>(base[3 * SLOT - cx(3)]));
+        s = add2(s, dec_pair<ST, 4>(base[4 * SLOT - cx(4)]));
+        s = add2(s, dec_pair<ST, 5>(base[5 * SLOT - cx(5)]));
+        s = add2(s, dec_pair<ST, 6>(base[6 * SLOT - cx(6)]));
+        s = add2(s, dec_pair<ST, 7>(base[7 * SLOT - cx(7)]));
+        s = add2(s, dec_pair<ST, 8>(base[8 * SLOT - cx(8)]));
         PP[ey * EX + ex] = s;
     }
     if (__syncthreads_or(abort)) {
@@ -551,7 +577,7 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     const float Fy = cap * gpy + p.mar_k * (g2 * gsgy - sdg * gpy) + p.rho * p.gy;
 
     // own u of the previous level (also the encoding velocity of the own slots across a wall)
-    const float2 uown = T::kHalo ? Hist[(ty + 1) * BW + tx + 4] : Hist[ty * TX + tx];
+    const float2 uown = S::kHalo ? Hist[(ty + 1) * BW + tx + 4] : Hist[ty * TX + tx];
 
     // flow populations pulled from the staged boxes (16-bit: plus the source cell's 3 w rho c.u)
     float h[9];
@@ -580,15 +606,16 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     float uxp = ux, uyp = uy;
     if (!p.first) {
         const P* base = FG + (ty + 1) * BW + tx + 4;
-        float2 s = make_float2(0.f, 0.f);
-        if constexpr (ST == kFP32) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) s = add2(s, base[i * S::FG_SLOT / (int)sizeof(P) + cy(i) * BW]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) s = fma2(bc(wgt(i)), raw2<ST>(base[i * S::FG_SLOT / (int)sizeof(P) + cy(i) * BW]), s);
-            s = fma2(s, make_float2(p.isc_f, p.isc_g), make_float2(p.phi_ref, 0.f));
-        }
+        float2 s = ref;
+        s = add2(s, dec_pair<ST, 0>(base[0 * SLOT + cy(0) * BW]));
+        s = add2(s, dec_pair<ST, 1>(base[1 * SLOT + cy(1) * BW]));
+        s = add2(s, dec_pair<ST, 2>(base[2 * SLOT + cy(2) * BW]));
+        s = add2(s, dec_pair<ST, 3>(base[3 * SLOT + cy(3) * BW]));
+        s = add2(s, dec_pair<ST, 4>(base[4 * SLOT + cy(4) * BW]));
+        s = add2(s, dec_pair<ST, 5>(base[5 * SLOT + cy(5) * BW]));
+        s = add2(s, dec_pair<ST, 6>(base[6 * SLOT + cy(6) * BW]));
+        s = add2(s, dec_pair<ST, 7>(base[7 * SLOT + cy(7) * BW]));
+        s = add2(s, dec_pair<ST, 8>(base[8 * SLOT + cy(8) * BW]));
         pprev = s;
         uxp = uown.x;
         uyp = uown.y;
@@ -624,28 +651,29 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
         if (a.out[3]) a.out[3][o] = uy;
         if (a.out[4]) a.out[4][o] = P_;
     } else {
+        uint32_t key = 0;
+        if constexpr (T::kPair16) key = cell_key((uint32_t)cell, a.seed);
         // ---- f (Sec. 3.1) and g (Sec. 3.2) together; sources cs2 V = d_t(s u) + cs2 (A or B) n ----
         {
             const float2 vx = fma2(make_float2(Aterm, Bterm), bc(nx_ * (1.f / 3.f)), dtX);
             const float2 vy = fma2(make_float2(Aterm, Bterm), bc(ny_ * (1.f / 3.f)), dtY);
-            collide_pair(q, pp, ux, uy, vx, vy, make_float2(p.nS1[0], p.nS1[1]), make_float2(p.nS2[0], p.nS2[1]),
-                         make_float2(p.nS3[0], p.nS3[1]), make_float2(p.nS4[0], p.nS4[1]),
-                         make_float2(p.K1[0], p.K1[1]), make_float2(p.K3[0], p.K3[1]));
+            collide_pair(q, pp, sub2(pp, ref), ux, uy, vx, vy, make_float2(p.nS1[0], p.nS1[1]),
+                         make_float2(p.nS2[0], p.nS2[1]), make_float2(p.nS3[0], p.nS3[1]),
+                         make_float2(p.nS4[0], p.nS4[1]), make_float2(p.K1[0], p.K1[1]), make_float2(p.K3[0], p.K3[1]));
             P* __restrict__ dfg = static_cast<P*>(a.dst) + cell;
-            if constexpr (ST == kFP32) {
+            if constexpr (!T::kPair16) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) dfg[(size_t)i * p.plane] = q[i];
             } else {
-                const uint32_t key = (uint32_t)cell * 0x85EBCA6Bu ^ a.seed;
-                dfg[0 * p.plane] = enc_pair_rs<ST, 0>(q[0], p, key);
-                dfg[1 * p.plane] = enc_pair_rs<ST, 1>(q[1], p, key);
-                dfg[2 * p.plane] = enc_pair_rs<ST, 2>(q[2], p, key);
-                dfg[3 * p.plane] = enc_pair_rs<ST, 3>(q[3], p, key);
-                dfg[4 * p.plane] = enc_pair_rs<ST, 4>(q[4], p, key);
-                dfg[5 * p.plane] = enc_pair_rs<ST, 5>(q[5], p, key);
-                dfg[6 * p.plane] = enc_pair_rs<ST, 6>(q[6], p, key);
-                dfg[7 * p.plane] = enc_pair_rs<ST, 7>(q[7], p, key);
-                dfg[8 * p.plane] = enc_pair_rs<ST, 8>(q[8], p, key);
+                dfg[0 * p.plane] = enc_pair_rs<ST, 0>(q[0], key);
+                dfg[1 * p.plane] = enc_pair_rs<ST, 1>(q[1], key);
+                dfg[2 * p.plane] = enc_pair_rs<ST, 2>(q[2], key);
+                dfg[3 * p.plane] = enc_pair_rs<ST, 3>(q[3], key);
+                dfg[4 * p.plane] = enc_pair_rs<ST, 4>(q[4], key);
+                dfg[5 * p.plane] = enc_pair_rs<ST, 5>(q[5], key);
+                dfg[6 * p.plane] = enc_pair_rs<ST, 6>(q[6], key);
+                dfg[7 * p.plane] = enc_pair_rs<ST, 7>(q[7], key);
+                dfg[8 * p.plane] = enc_pair_rs<ST, 8>(q[8], key);
             }
         }
         // ---- flow h (Sec. 3.3) ----
@@ -701,20 +729,20 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
         }
         using Hv = typename T::H;
         Hv* __restrict__ dh = reinterpret_cast<Hv*>(static_cast<P*>(a.dst) + (size_t)kPairs * p.plane) + cell;
-        if constexpr (ST == kFP32) {
+        if constexpr (!T::kH16) {
 #pragma unroll
             for (int i = 1; i < 9; ++i) dh[(size_t)(i - 1) * p.plane] = h[i];
         } else {
             // every slot is stored relative to this cell's new u (what the next step reads back):
             // raw = (h_i / w_i - 3 rho c_i.u) S_h, two links per stochastic conversion
-            const float vx = p.kh_enc * ux, vy = p.kh_enc * uy;
-            const uint32_t key = (uint32_t)cell * 0xC2B2AE35u ^ a.seed;
-            const uint32_t b12 = cvt_rs2<ST>(fmaf(h[1], p.enc_h[1], -vx), fmaf(h[2], p.enc_h[2], -vy), rbits_of(key, 9));
-            const uint32_t b34 = cvt_rs2<ST>(fmaf(h[3], p.enc_h[3], vx), fmaf(h[4], p.enc_h[4], vy), rbits_of(key, 10));
+            const float vx = p.kh3 * T::SH * ux, vy = p.kh3 * T::SH * uy;
+            constexpr float e1 = T::SH / wgt(1), e5 = T::SH / wgt(5);
+            const uint32_t b12 = cvt_rs2<typename T::P>(fmaf(h[1], e1, -vx), fmaf(h[2], e1, -vy), rbits_of(key, 9));
+            const uint32_t b34 = cvt_rs2<typename T::P>(fmaf(h[3], e1, vx), fmaf(h[4], e1, vy), rbits_of(key, 10));
             const uint32_t b56 =
-                cvt_rs2<ST>(fmaf(h[5], p.enc_h[5], -(vx + vy)), fmaf(h[6], p.enc_h[6], vx - vy), rbits_of(key, 11));
+                cvt_rs2<typename T::P>(fmaf(h[5], e5, -(vx + vy)), fmaf(h[6], e5, vx - vy), rbits_of(key, 11));
             const uint32_t b78 =
-                cvt_rs2<ST>(fmaf(h[7], p.enc_h[7], vx + vy), fmaf(h[8], p.enc_h[8], vy - vx), rbits_of(key, 12));
+                cvt_rs2<typename T::P>(fmaf(h[7], e5, vx + vy), fmaf(h[8], e5, vy - vx), rbits_of(key, 12));
             unsigned short* dh16 = reinterpret_cast<unsigned short*>(dh);
             dh16[0 * p.plane] = (unsigned short)(b12 & 0xFFFFu);
             dh16[1 * p.plane] = (unsigned short)(b12 >> 16);
@@ -770,7 +798,7 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
         const double geq = w * psi * (1.0 + 3.0 * cu);
         const double heq = w * (3.0 * P_ + 3.0 * rho * cu + 4.5 * rho * (cu * cu - uu / 3.0));
         // the first pull at x for direction i reads slot i of x - c_i, or, across a wall, the
-        // opposite slot of x itself
+        // opposite slot of x itself (same weight)
         int sx = x - cx(i), sy = y - cy(i), slot = i;
         if (a.walls && (sy < 0 || sy >= p.ny)) {
             sx = x;
@@ -781,22 +809,21 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
             sy = (sy + p.ny) % p.ny;
         }
         const size_t cell = (size_t)sy * p.pitch + sx;
-        if constexpr (ST == kFP32) {
+        if constexpr (!T::kPair16)
             fg[(size_t)slot * p.plane + cell] = make_float2((float)feq, (float)geq);
-            if (slot != 0) hp[(size_t)(slot - 1) * p.plane + cell] = (float)heq;
+        else
+            fg[(size_t)slot * p.plane + cell] = pack2<P>(
+                make_float2((float)((feq / w - p.phi_ref) * T::SF), (float)(geq / w * T::SG)));
+        if (slot == 0) continue;
+        if constexpr (!T::kH16) {
+            hp[(size_t)(slot - 1) * p.plane + cell] = (Hv)heq;
         } else {
-            // the slot holds link `slot`'s value heq/feq/geq of link i (equal links unless across a
-            // wall, where slot = opp(i) with the same weight)
-            fg[(size_t)slot * p.plane + cell] = pack2<ST>(make_float2(
-                (float)((feq / w - p.phi_ref) / p.isc_f), (float)(geq / w / p.isc_g)));
-            if (slot != 0) {
-                // stored relative to the storing cell's velocity, as the step will read it back:
-                // the source cell for a plain link, this cell for a slot across a wall
-                const size_t so = (size_t)sy * p.nx + sx;
-                const double sux = (float)a.ux[so], suy = (float)a.uy[so];
-                const double vel = 3.0 * rho * (cx(slot) * sux + cy(slot) * suy);
-                hp[(size_t)(slot - 1) * p.plane + cell] = pack1<ST>((float)((heq / w - vel) * p.enc_h[slot] * w));
-            }
+            // stored relative to the storing cell's velocity, as the step will read it back:
+            // the source cell for a plain link, this cell for a slot across a wall
+            const size_t so = (size_t)sy * p.nx + sx;
+            const double sux = (float)a.ux[so], suy = (float)a.uy[so];
+            const double vel = 3.0 * rho * (cx(slot) * sux + cy(slot) * suy);
+            hp[(size_t)(slot - 1) * p.plane + cell] = pack1<Hv>((float)((heq / w - vel) * T::SH));
         }
     }
     const size_t cell = (size_t)y * p.pitch + x;
@@ -828,7 +855,8 @@ template <int ST>
 __global__ void __launch_bounds__(kReduceThreads) reduce_partial_kernel(const void* __restrict__ pops, int lane,
                                                                         int nx, int ny, int pitch, long long plane,
                                                                         Phys p, double* __restrict__ partials) {
-    using P = typename Traits<ST>::P;
+    using T = Traits<ST>;
+    using P = typename T::P;
     __shared__ double smem[32];
     const P* pairs = static_cast<const P*>(pops);
     double acc = 0.0;
@@ -836,12 +864,12 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partial_kernel(const vo
     for (int y = blockIdx.x; y < ny; y += gridDim.x) {
         for (int k = threadIdx.x; k < kPairs * nx; k += blockDim.x) {
             const int i = k / nx, x = k - i * nx;
-            const float2 v = raw2<ST>(pairs[(size_t)i * plane + (size_t)y * pitch + x]);
-            if constexpr (ST == kFP32) {
+            const float2 v = raw2(pairs[(size_t)i * plane + (size_t)y * pitch + x]);
+            if constexpr (!T::kPair16) {
                 acc += (double)(lane ? v.y : v.x);
             } else {
                 const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
-                acc += lane ? w * (double)v.y * p.isc_g : w * ((double)v.x * p.isc_f + p.phi_ref);
+                acc += lane ? w * (double)v.y / T::SG : w * ((double)v.x / T::SF + p.phi_ref);
             }
         }
     }

@@ -1,5 +1,6 @@
 // Launch helpers of the step kernel, one translation unit per storage mode
-// (step_fp32.cu, step_fp16.cu, step_bf16.cu) so that the instances compile in parallel.
+// (step_fp32.cu, step_fp16.cu, step_bf16.cu, step_fp16fg.cu, step_bf16fg.cu) so that the
+// instances compile in parallel.
 #pragma once
 #include <cstring>
 
@@ -65,8 +66,12 @@ cudaError_t prepare_step_impl(int* blocks_per_sm) {
 cudaError_t launch_step_fp32(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t s);
 cudaError_t launch_step_fp16(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t s);
 cudaError_t launch_step_bf16(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t s);
+cudaError_t launch_step_fp16fg(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t s);
+cudaError_t launch_step_bf16fg(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t s);
 cudaError_t prepare_step_fp32(int* blocks_per_sm);
 cudaError_t prepare_step_fp16(int* blocks_per_sm);
 cudaError_t prepare_step_bf16(int* blocks_per_sm);
+cudaError_t prepare_step_fp16fg(int* blocks_per_sm);
+cudaError_t prepare_step_bf16fg(int* blocks_per_sm);
 
 }  // namespace lbm

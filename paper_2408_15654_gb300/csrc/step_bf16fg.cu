@@ -1,0 +1,12 @@
+// Step-kernel instances for BF16 storage of the (f, g) pairs, FP32 storage of h.
+#include "lbm_launch.h"
+
+namespace lbm {
+
+cudaError_t launch_step_bf16fg(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t s) {
+    return launch_step_impl<kBF16FG>(a, mode, walls, langmuir, grid, s);
+}
+
+cudaError_t prepare_step_bf16fg(int* blocks_per_sm) { return prepare_step_impl<kBF16FG>(blocks_per_sm); }
+
+}  // namespace lbm

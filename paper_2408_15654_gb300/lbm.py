@@ -16,8 +16,9 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = range(7)
 LBM_BC_PERIODIC, LBM_BC_WALLS = 0, 1
 LBM_EOS_LINEAR, LBM_EOS_LANGMUIR = 0, 1
-LBM_STORE_FP32, LBM_STORE_FP16, LBM_STORE_BF16 = 0, 1, 2
-STORAGE = {"fp32": LBM_STORE_FP32, "fp16": LBM_STORE_FP16, "bf16": LBM_STORE_BF16}
+LBM_STORE_FP32, LBM_STORE_FP16, LBM_STORE_BF16, LBM_STORE_FP16_FG, LBM_STORE_BF16_FG = 0, 1, 2, 3, 4
+STORAGE = {"fp32": LBM_STORE_FP32, "fp16": LBM_STORE_FP16, "bf16": LBM_STORE_BF16,
+           "fp16_fg": LBM_STORE_FP16_FG, "bf16_fg": LBM_STORE_BF16_FG}
 LBM_MEM_HOST, LBM_MEM_DEVICE = 0, 1
 LBM_PHI, LBM_PSI, LBM_UX, LBM_UY, LBM_P = 1, 2, 4, 8, 16
 LBM_SUM_PHI, LBM_SUM_PSI = 0, 1

@@ -58,6 +58,11 @@ def test_workspace_bytes_without_gpu():
     n16 = lbm.lbm_workspace_bytes(lbm.make_params(p))
     assert n16 >= 2 * 13 * 256 * pitch * 4 + 2 * 256 * pitch * 8
     assert n16 < 2 * 13 * 256 * pitch * 4 + 2 * 256 * pitch * 8 + 64 * 1024
+    # f and g in 16 bits, h in FP32: 68 bytes per cell and buffer
+    p["storage"] = "bf16_fg"
+    nfg = lbm.lbm_workspace_bytes(lbm.make_params(p))
+    assert nfg >= 2 * 68 * 256 * pitch + 2 * 256 * pitch * 8
+    assert nfg < 2 * 68 * 256 * pitch + 2 * 256 * pitch * 8 + 64 * 1024
 
 
 @pytest.mark.parametrize("bad", [dict(nx=1), dict(ny=0), dict(rhoA=2.0), dict(W=0.0), dict(M_phi=-1.0),

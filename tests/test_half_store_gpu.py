@@ -20,14 +20,19 @@ OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
 _records = {}
 
 # stated relative-L2 error bounds after 1000 steps (128^2 stationary drop, 512x256 shear drop),
-# per storage mode and field; measured on GB300: FP16 phi 8.1e-4, psi 1.2e-3, u 5.3e-5; BF16
-# phi 6.4e-3, psi 9.1e-3, u 3.2e-4 (worst of the two workloads)
+# per storage mode and field; measured on GB300 (worst of the two workloads): FP16 phi 9.7e-4,
+# psi 1.2e-3, u 5.8e-5; BF16 phi 8.0e-3, psi 8.4e-3, u 3.4e-4; the _fg modes (h in FP32) within
+# 5 % of these
 BOUND = {
     "fp16": {"phi": 3e-3, "psi": 5e-3, "u": 5e-4},
     "bf16": {"phi": 2e-2, "psi": 3e-2, "u": 2e-3},
 }
+# f and g in 16 bits with h in FP32: no worse than the all-16-bit mode of the same type
+BOUND["fp16_fg"] = BOUND["fp16"]
+BOUND["bf16_fg"] = BOUND["bf16"]
+HALF = ("fp16", "bf16", "fp16_fg", "bf16_fg")
 # 120 steps on a 45 x 19 grid with perturbed fields (every cell near the interface or a wall);
-# measured: FP16 phi 6.8e-3, psi 1.5e-2, u 4.4e-4; BF16 phi 7.6e-3, psi 1.8e-2, u 3.0e-3
+# measured: FP16 phi 6.7e-3, psi 1.5e-2, u 5.2e-4; BF16 phi 7.6e-3, psi 1.8e-2, u 3.6e-3
 BOUND_RAGGED = {"phi": 3e-2, "psi": 5e-2, "u": 1e-2}
 
 
@@ -77,7 +82,7 @@ def oracle_moments(key, params, flds, steps):
     return _oracle_cache[key]
 
 
-@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("storage", HALF)
 @pytest.mark.parametrize("case", ["stationary_drop_128", "shear_drop_512x256"])
 def test_half_store_error_after_1000_steps(storage, case):
     if case == "stationary_drop_128":
@@ -98,12 +103,13 @@ def test_half_store_error_after_1000_steps(storage, case):
     b = BOUND[storage]
     assert e["phi"] <= b["phi"] and e["psi"] <= b["psi"] and e["u"] <= b["u"], e
     # stochastic rounding keeps the storage error unbiased: the totals drift by random walk only
-    assert e["sum_phi_rel"] <= (5e-4 if storage == "fp16" else 5e-3)
-    assert e["sum_psi_rel"] <= (1e-3 if storage == "fp16" else 3e-3)
+    fp16 = storage.startswith("fp16")
+    assert e["sum_phi_rel"] <= (5e-4 if fp16 else 5e-3)
+    assert e["sum_psi_rel"] <= (1e-3 if fp16 else 3e-3)
     assert g.status == 0
 
 
-@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("storage", HALF)
 def test_half_store_ragged_grid_runs_and_conserves(storage):
     """Ragged grid with walls: the 16-bit path of the edge patch and the bounce-back decoding."""
     p, f = W.shear_drop(45, 19, R=6)
@@ -121,7 +127,7 @@ def test_half_store_ragged_grid_runs_and_conserves(storage):
     assert e["phi"] <= b["phi"] and e["psi"] <= b["psi"] and e["u"] <= b["u"], e
 
 
-@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("storage", HALF)
 def test_half_store_checkpoint_is_bitwise(storage):
     p, f = W.shear_drop(80, 48, R=9)
     p["storage"] = storage
@@ -137,7 +143,7 @@ def test_half_store_checkpoint_is_bitwise(storage):
     assert a.state() == b.state()
 
 
-@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("storage", HALF)
 def test_half_store_init_round_trip(storage):
     """Right after initialisation the decoded populations give back the fields to 16-bit precision."""
     p, f = W.shear_drop(40, 24, R=6)
@@ -146,7 +152,7 @@ def test_half_store_init_round_trip(storage):
     g = lbm.Lattice(dict(p, storage=storage))
     g.init(**f)
     m = g.moments()
-    eps = 2.0 ** (-11 if storage == "fp16" else -8)
+    eps = 2.0 ** (-11 if storage.startswith("fp16") else -8)
     np.testing.assert_allclose(m["phi"], f["phi"], atol=9 * eps)
     np.testing.assert_allclose(m["psi"], f["psi"], atol=9 * eps)
     np.testing.assert_allclose(m["ux"], f["ux"], atol=3e-2 * eps * 30)
