@@ -168,6 +168,50 @@ def cpu_baseline(budget_s: float = 12.0):
                       f"OpenMP over rows ({cores} threads)"}
 
 
+def batch_leg(torch, lbm, W, storage: str, steps: int, alone_steps: int = 0):
+    """The 64-lattice mix (sizes 128^2 .. 1024x512, seed 0) advanced by one launch per step:
+    autotuned schedule, then `steps` device-timed steps; optionally each lattice alone for
+    `alone_steps` steps (one lbm_step launch per lattice and step) for comparison."""
+    bstream = torch.cuda.Stream()
+    inst = W.batch_instances(64, seed=0)
+    lats = []
+    for p, f in inst:
+        g = lbm.Lattice(dict(p, storage=storage), stream=bstream)
+        g.init(**f)
+        lats.append(g)
+    cells = sum(g.nx * g.ny for g in lats)
+    b = lbm.Batch(lats, bstream)
+    sched, k = b.autotune(trial_steps=32)
+    torch.cuda.synchronize()
+    n0 = b.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(bstream)
+    b.step(steps)
+    e1.record(bstream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if any(g.status != lbm.LBM_OK for g in lats):
+        raise RuntimeError(f"unstable member in the {storage} batch: {lbm.lbm_last_error()}")
+    bpl = BYTES_PER_LUP if storage == "fp32" else HALF_MODES[storage]
+    out = {"value": cells * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "storage": storage, "steps": steps,
+           "ms_per_step": ms / steps, "schedule": sched, "graph_steps": k, "gpu_launches": b.launches - n0,
+           "achieved_gbs": cells * bpl * steps / (ms * 1e-3) / 1e9,
+           "frac_of_measured_hbm": cells * bpl * steps / (ms * 1e-3) / 1e9 / measured_peak()[0]}
+    if alone_steps:
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(bstream)
+        for g in lats:
+            g.step(alone_steps)
+        a1.record(bstream)
+        torch.cuda.synchronize()
+        out["one_at_a_time"] = {"value": cells * alone_steps / (a0.elapsed_time(a1) * 1e-3) / 1e6, "unit": "MLUPS",
+                                "steps": alone_steps, "gpu_launches": 64 * alone_steps}
+    b.close()
+    for g in lats:
+        g.close()
+    return out, cells
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle as it stands on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", 0))
@@ -260,6 +304,15 @@ def run_ours(args):
                     "frac_of_measured_hbm": hach / measured_peak()[0], "algorithmic_bytes_per_lup": bpl}
         hs.close()
 
+    # many lattices at once: the 64-lattice mix, FP32 and FP16 storage
+    batch = {}
+    if args.batch_steps > 0:
+        for st in ("fp32", "fp16"):
+            batch[st], bcells = batch_leg(torch, lbm, W, st, args.batch_steps,
+                                          alone_steps=100 if st == "fp32" else 0)
+        batch["workload"] = (f"64 seeded drops (seed 0), sizes uniform over 128^2, 256^2, 512x256, 1024x512 "
+                             f"({bcells} cells), walls at +/-U with U ~ U[0, 0.02], linear EOS")
+
     # roofline of the step kernel (one launch per step, so launch duration = step time)
     peak, peak_kind = measured_peak()
     launch_s = ms / args.steps * 1e-3
@@ -293,6 +346,7 @@ def run_ours(args):
                          "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_lup": BYTES_PER_LUP},
             "half_store": half,
+            "batch": batch,
             "cpu_baseline": base,
             "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": io_bytes / args.steps,
                     "d2h_bytes_per_step": io_bytes / args.steps,
@@ -315,6 +369,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=1000, help="steps of the 64-lattice batch legs (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

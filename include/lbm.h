@@ -202,6 +202,63 @@ int lbm_destroy(lbm_handle* h);
  * valid until the next call on the same thread. */
 const char* lbm_last_error(void);
 
+/* ---- many lattices in one launch per step --------------------------------------------------
+ * Not in the paper, which treats one lattice at a time: a batch advances many independent
+ * lattices (lbm_handle members, each with its own parameters, grid and workspace) by one launch
+ * of one kernel per step and per group of members that share storage mode, boundary kind and
+ * EOS.  Every member's result is bit for bit the one lbm_step gives it alone: a cell's update
+ * depends only on its lattice's buffers, constants and step count, never on the schedule.
+ * Ownership: the caller owns the batch workspace and the members; members stay valid and are
+ * not destroyed while they belong to a batch (lbm_batch_set_members replaces the list).  All
+ * members are created on the batch's stream.  Between batch calls a member may be used through
+ * the single-lattice calls (lbm_get_moments, lbm_reduce, lbm_status, lbm_get_state, and also
+ * lbm_step, lbm_init_fields, lbm_set_state): the batch reads each member's step count and
+ * current buffer at the start of every lbm_batch_step.                                        */
+typedef struct lbm_batch lbm_batch;
+
+#define LBM_SCHED_MEMBER_ORDER 0     /* tiles lattice by lattice, in member order              */
+#define LBM_SCHED_LARGEST_FIRST 1    /* lattice by lattice, the one with most tiles first      */
+#define LBM_SCHED_EDGES_FIRST 2      /* the edge tile rows of all lattices, then the interiors */
+#define LBM_SCHED_ROW_INTERLEAVED 3  /* tile row r of every lattice, then row r + 1            */
+/* Within a lattice the two edge tile rows always come before the interior rows. */
+
+/* Total tiles (ceil(nx/32) * ceil(ny/8) per lattice) of n members. */
+int lbm_batch_tiles(lbm_handle* const* members, int n, int64_t* tiles);
+
+/* Device workspace of a batch of up to max_members lattices with up to max_tiles tiles in total:
+ * one descriptor per member (TMA maps, constants, buffer pointers, step count) and the tile
+ * list, each 256-byte aligned. */
+int lbm_batch_workspace_bytes(int max_members, int64_t max_tiles, size_t* bytes);
+
+/* Create an empty batch enqueuing its work on cuda_stream.  CUDA graphs (lbm_batch_set_schedule)
+ * need a created stream: on the legacy default stream (NULL) graph_steps is forced to 0. */
+int lbm_batch_create(int max_members, int64_t max_tiles, void* d_workspace, size_t bytes, void* cuda_stream,
+                     lbm_batch** out);
+
+/* Replace the member list (n <= max_members distinct handles, at most max_tiles tiles, each
+ * lattice at most 65535 tiles along an axis; n = 0 empties the batch). */
+int lbm_batch_set_members(lbm_batch* b, lbm_handle* const* members, int n);
+
+/* Order of the tiles (LBM_SCHED_*) and the number of steps per captured CUDA graph (0: plain
+ * launches).  Default: LBM_SCHED_LARGEST_FIRST, no graph. */
+int lbm_batch_set_schedule(lbm_batch* b, int schedule, int graph_steps);
+
+/* Advance every member by n steps (asynchronous, like lbm_step).  Each member's device status
+ * word collects its own instability flags; read it with lbm_status(member). */
+int lbm_batch_step(lbm_batch* b, int64_t n);
+
+/* Time each schedule with 16-step graphs, and the fastest of them without a graph, over about
+ * trial_steps steps each, and keep the fastest.  The trials are real steps: every member
+ * advances by 4 * (16 + trial_steps rounded up to a multiple of 16) + 1 + trial_steps steps
+ * (without graphs, on the legacy default stream: 4 * (1 + trial_steps)).  Synchronous. */
+int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* schedule, int* graph_steps);
+
+/* Kernels this batch has launched so far (a graph replay counts its kernels). */
+int lbm_batch_launches(const lbm_batch* b, int64_t* launches);
+
+/* Free the batch (host memory only; the workspace and the members stay the caller's). */
+int lbm_batch_destroy(lbm_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,14 +13,13 @@
 #include <new>
 #include <string>
 
-#include "lbm.h"
-#include "lbm_launch.h"
+#include "lbm_internal.h"
 
 static_assert(LBM_STORE_FP32 == lbm::kFP32 && LBM_STORE_FP16 == lbm::kFP16 && LBM_STORE_BF16 == lbm::kBF16 &&
                   LBM_STORE_FP16_FG == lbm::kFP16FG && LBM_STORE_BF16_FG == lbm::kBF16FG,
               "storage codes of the ABI and the kernels agree");
 
-namespace {
+namespace lbm_host {
 
 thread_local std::string g_err;
 
@@ -34,11 +33,11 @@ int fail(int code, const char* fmt, ...) {
     return code;
 }
 
-#define LBM_CUDA(call)                                                                       \
-    do {                                                                                     \
-        cudaError_t e_ = (call);                                                             \
-        if (e_ != cudaSuccess) return fail(LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-    } while (0)
+}  // namespace lbm_host
+
+using namespace lbm_host;
+
+namespace {
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -93,16 +92,6 @@ int prepare_kernels(int st, int* blocks_per_sm) {
     if (*blocks_per_sm < 1) return fail(LBM_ECUDA, "the step kernel does not fit on an SM");
     return LBM_OK;
 }
-
-constexpr size_t kAlign = 256;
-size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-
-struct Layout {
-    int pitch;
-    size_t plane;       // floats per plane
-    size_t pops_bytes;  // one population buffer
-    size_t off_pops[2], off_hist[2], off_status, off_partials, total;
-};
 
 bool rate_ok(double s) { return s > 0.0 && s < 2.0; }
 
@@ -162,7 +151,6 @@ lbm::Phys make_phys(const lbm_params* p, const Layout& L) {
     f.ny = p->ny;
     f.pitch = L.pitch;
     f.plane = (long long)L.plane;
-    f.first = 1;
     f.phiA = (float)p->phiA;
     f.phiB = (float)p->phiB;
     f.inv_dphi = (float)(1.0 / dphi);
@@ -216,25 +204,6 @@ lbm::Phys make_phys(const lbm_params* p, const Layout& L) {
 
 }  // namespace
 
-struct lbm_handle {
-    lbm_params prm;
-    Layout L;
-    lbm::Phys phys;
-    cudaStream_t stream;
-    char* ws;
-    void* pops[2];
-    float2* hist[2];         // u history, alternating with the population buffers
-    unsigned* status;
-    double* partials;
-    CUtensorMap tm_fg[2];    // TMA descriptors of the (f, g) pair planes of each buffer
-    CUtensorMap tm_h[2];     // TMA descriptors of the h planes of each buffer
-    CUtensorMap tm_hist[2];  // TMA descriptors of the u history buffers
-    int tiles_x, tiles_y;    // step-kernel grid: one TX x TY tile per CTA
-    int cur;          // buffer holding the current state
-    int initialized;
-    int first;        // 1 until the first step after lbm_init_fields
-    int64_t steps;
-};
 
 namespace {
 
@@ -245,21 +214,17 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
     a.tm_h = h->tm_h[h->cur];
     a.tm_hist = h->tm_hist[h->cur];
     a.p = h->phys;
-    a.p.first = h->first;
-    a.src = h->pops[h->cur];
-    a.dst = h->pops[h->cur ^ 1];
-    a.hist_src = h->hist[h->cur];
-    a.hist_dst = h->hist[h->cur ^ 1];
-    a.status = h->status;
-    {
-        // per-step salt of the stochastic rounding (a function of the step count, so a restored
-        // checkpoint continues bit for bit)
-        uint64_t z = (uint64_t)h->steps * 0x9E3779B97F4A7C15ull;
-        z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ull;
-        a.seed = (unsigned)(z ^ (z >> 29));
-    }
+    a.io.first = h->first;
+    a.io.src = h->pops[h->cur];
+    a.io.dst = h->pops[h->cur ^ 1];
+    a.io.hist_src = h->hist[h->cur];
+    a.io.hist_dst = h->hist[h->cur ^ 1];
+    a.io.status = h->status;
+    // salt of the stochastic rounding: a function of the step count, so a restored checkpoint
+    // continues bit for bit
+    a.io.seed = lbm::step_seed(h->steps);
     if (out)
-        for (int k = 0; k < 5; ++k) a.out[k] = out[k];
+        for (int k = 0; k < 5; ++k) a.io.out[k] = out[k];
     const dim3 grid(h->tiles_x, h->tiles_y);
     const bool walls = h->prm.bc_y == LBM_BC_WALLS, lang = h->prm.eos == LBM_EOS_LANGMUIR;
     cudaError_t e;

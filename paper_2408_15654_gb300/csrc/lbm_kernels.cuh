@@ -99,7 +99,7 @@ __host__ __device__ constexpr bool h_is_16bit(int st) { return st == kFP16 || st
 
 // Physical constants in FP32, precomputed on the host from lbm_params.
 struct Phys {
-    int nx, ny, pitch, first;
+    int nx, ny, pitch, pad0;
     long long plane;          // cells per plane (ny * pitch)
     float phiA, phiB, inv_dphi;
     float cA;                 // 4 / (W dphi):  A = cA (phiA - phi)(phi - phiB), B = cA psi (phiA + phiB - 2 phi)
@@ -159,15 +159,14 @@ template <int ST> struct Smem {
     static constexpr int PP = HIST + round128(HIST_BYTES);
     static constexpr int BAR = PP + NE * 8;
     static constexpr int BYTES = BAR + 16;
+    static constexpr int PHYS = BYTES;                       // batched kernel: the instance's Phys
+    static constexpr int BYTES_BATCH = PHYS + (int)((sizeof(Phys) + 15) / 16 * 16);
     static constexpr unsigned TX_BYTES =
         (unsigned)(kPairs * FG_BOX * sizeof(typename T::P) + kHPlanes * H_BOX * sizeof(typename T::H) + HIST_BYTES);
 };
 
-struct StepArgs {
-    CUtensorMap tm_fg;            // {nx, ny, 9} pairs, box {BW, BH, 1}
-    CUtensorMap tm_h;             // {nx, ny, 8} h values, box {H_BW, TY, 1}
-    CUtensorMap tm_hist;          // {nx, ny, 1} float2, box {TX, TY, 1} or {BW, BH, 1}
-    Phys p;
+// Buffers of one step of one lattice.
+struct TileIO {
     const void* __restrict__ src;
     void* __restrict__ dst;
     const float2* __restrict__ hist_src;  // (u_x, u_y) of the previous step
@@ -175,7 +174,24 @@ struct StepArgs {
     unsigned* __restrict__ status;
     double* __restrict__ out[5];  // kMoments: phi, psi, ux, uy, P (dense ny x nx), may be null
     unsigned seed;                // per-step salt of the stochastic rounding
+    int first;                    // 1 on the first step after initialisation (zero d/dt terms)
 };
+
+struct StepArgs {
+    CUtensorMap tm_fg;            // {nx, ny, 9} pairs, box {BW, BH, 1}
+    CUtensorMap tm_h;             // {nx, ny, 8} h values, box {H_BW, TY, 1}
+    CUtensorMap tm_hist;          // {nx, ny, 1} float2, box {TX, TY, 1} or {BW, BH, 1}
+    Phys p;
+    TileIO io;
+};
+
+// Salt of the stochastic rounding of step number `steps` (steps taken since initialisation), a
+// splitmix64 finaliser: the same on host and device, so any launch path gives the same bits.
+__host__ __device__ inline unsigned step_seed(long long steps) {
+    unsigned long long z = (unsigned long long)steps * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ull;
+    return (unsigned)(z ^ (z >> 29));
+}
 
 __device__ __forceinline__ int wrapg(int a, int n) {
     const int r = a % n;
@@ -327,13 +343,12 @@ __device__ __forceinline__ void collide_pair(float2 q[9], float2 s, float2 sr, f
 // cell's own opposite slot (bounce-back).  Only the out-of-grid strips of each box are visited
 // (one warp per box); entries no valid pull reads are left as loaded.
 template <int ST, bool WALLS>
-__device__ void patch_edges(const StepArgs& a, unsigned char* sm, int x0, int y0) {
+__device__ void patch_edges(const Phys& p, const TileIO& io, unsigned char* sm, int x0, int y0) {
     using T = Traits<ST>;
     using S = Smem<ST>;
     using P = typename T::P;
     using Hv = typename T::H;
-    const Phys& p = a.p;
-    const P* __restrict__ srcFG = static_cast<const P*>(a.src);
+    const P* __restrict__ srcFG = static_cast<const P*>(io.src);
     const Hv* __restrict__ srcH = reinterpret_cast<const Hv*>(srcFG + (size_t)kPairs * p.plane);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NBOX = kPairs + kHPlanes + (S::kHalo ? 1 : 0);
@@ -395,7 +410,7 @@ __device__ void patch_edges(const StepArgs& a, unsigned char* sm, int x0, int y0
                 reinterpret_cast<Hv*>(sm + S::H + (pl - kPairs) * S::H_SLOT)[r * bw + c] =
                     srcH[(size_t)(si - 1) * p.plane + cell];
             else
-                reinterpret_cast<float2*>(sm + S::HIST)[r * bw + c] = a.hist_src[cell];
+                reinterpret_cast<float2*>(sm + S::HIST)[r * bw + c] = io.hist_src[cell];
         }
     }
 }
@@ -416,53 +431,42 @@ __device__ __forceinline__ float load_h(const unsigned char* sm, const float2* H
     }
 }
 
-// One fused step (kStep) or the macroscopic fields of the current level (kMoments) for one tile.
-// One elected thread stages the tile with TMA (9 pair boxes, 8 h boxes, the u history) on one
-// mbarrier; edge tiles then patch wrapped and bounced entries.  The pulled (f, g) of the tile and
-// of a one-cell ring give (phi, psi) for the 9-point stencils; the same boxes hold the own cell's
-// unshifted post-collision values, whose sums are phi and psi of the previous level
-// (m*_0 = phi exactly, Sec. 3.1), so only u of the previous level is stored.
+// Stage the boxes of tile (x0, y0) with TMA on one mbarrier (called by one thread).
+template <int ST>
+__device__ __forceinline__ void issue_tile_loads(unsigned char* sm, const CUtensorMap* tm_fg, const CUtensorMap* tm_h,
+                                                 const CUtensorMap* tm_hist, int x0, int y0, unsigned long long* mbar) {
+    using T = Traits<ST>;
+    using S = Smem<ST>;
+    mbar_expect_tx(mbar, S::TX_BYTES);
+#pragma unroll
+    for (int i = 0; i < kPairs; ++i) tma_load_3d(sm + S::FG + i * S::FG_SLOT, tm_fg, x0 - 4, y0 - 1 - cy(i), i, mbar);
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+        tma_load_3d(sm + S::H + (i - 1) * S::H_SLOT, tm_h, x0 - T::H_X0, y0 - cy(i), i - 1, mbar);
+    if constexpr (S::kHalo) tma_load_3d(sm + S::HIST, tm_hist, x0 - 4, y0 - 1, 0, mbar);
+    else tma_load_3d(sm + S::HIST, tm_hist, x0, y0, 0, mbar);
+}
+
+// One fused step (kStep) or the macroscopic fields of the current level (kMoments) for one tile,
+// after one thread has issued the tile's TMA loads on the mbarrier.  Edge tiles patch wrapped and
+// bounced entries.  The pulled (f, g) of the tile and of a one-cell ring give (phi, psi) for the
+// 9-point stencils; the same boxes hold the own cell's unshifted post-collision values, whose sums
+// are phi and psi of the previous level (m*_0 = phi exactly, Sec. 3.1), so only u of the
+// previous level is stored.
 template <int ST, bool WALLS, bool LANGMUIR, int MODE>
-__global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ StepArgs a) {
+__device__ __forceinline__ void step_tile(const Phys& p, const TileIO& io, unsigned char* sm, int x0, int y0) {
     using T = Traits<ST>;
     using S = Smem<ST>;
     using P = typename T::P;
-    extern __shared__ __align__(1024) unsigned char sm[];
     const P* FG = reinterpret_cast<const P*>(sm + S::FG);
     const float2* Hist = reinterpret_cast<const float2*>(sm + S::HIST);
     float2* PP = reinterpret_cast<float2*>(sm + S::PP);
     unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + S::BAR);
-    const Phys& p = a.p;
     const int t = threadIdx.x;
-    // The first and the last tile row (whose boxes need edge patching, and so run longest) are
-    // launched first, so that the last wave holds interior tiles only.
-    const int ntr = gridDim.y;
-    const int tr = blockIdx.y == 0 ? 0 : (blockIdx.y == 1 ? ntr - 1 : (int)blockIdx.y - 1);
-    const int x0 = blockIdx.x * TX, y0 = tr * TY;
-
-    if (t == 0) {
-        mbar_init(mbar, 1);
-        fence_mbar_init();
-    }
-    // Programmatic dependent launch: let the next step's CTAs be scheduled into the slots this
-    // grid frees, and wait here until the previous step's writes are complete and visible.
-    cudaTriggerProgrammaticLaunchCompletion();
-    cudaGridDependencySynchronize();
-    if (t == 0) {
-        mbar_expect_tx(mbar, S::TX_BYTES);
-#pragma unroll
-        for (int i = 0; i < kPairs; ++i)
-            tma_load_3d(sm + S::FG + i * S::FG_SLOT, &a.tm_fg, x0 - 4, y0 - 1 - cy(i), i, mbar);
-#pragma unroll
-        for (int i = 1; i < 9; ++i)
-            tma_load_3d(sm + S::H + (i - 1) * S::H_SLOT, &a.tm_h, x0 - T::H_X0, y0 - cy(i), i - 1, mbar);
-        if constexpr (S::kHalo) tma_load_3d(sm + S::HIST, &a.tm_hist, x0 - 4, y0 - 1, 0, mbar);
-        else tma_load_3d(sm + S::HIST, &a.tm_hist, x0, y0, 0, mbar);
-    }
     __syncthreads();
     bool abort = !mbar_wait_bounded(mbar, 0);
     if (x0 == 0 || x0 + TX + 8 > p.nx || y0 == 0 || y0 + TY + 2 > p.ny) {
-        if (!abort) patch_edges<ST, WALLS>(a, sm, x0, y0);
+        if (!abort) patch_edges<ST, WALLS>(p, io, sm, x0, y0);
         abort = __syncthreads_or(abort);
     }
 
@@ -523,7 +527,7 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     if (__syncthreads_or(abort)) {
         // a staging copy did not arrive in time: report it, wait (bounded) for it, store nothing
         if (t == 0) {
-            atomicOr(a.status, kStatusTimeout);
+            atomicOr(io.status, kStatusTimeout);
             mbar_wait_bounded(mbar, 0);
         }
         __syncthreads();
@@ -604,7 +608,7 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     // previous level: (phi, psi) from the own cell's post-collision pairs, u from history
     float2 pprev = pp;
     float uxp = ux, uyp = uy;
-    if (!p.first) {
+    if (!io.first) {
         const P* base = FG + (ty + 1) * BW + tx + 4;
         float2 s = ref;
         s = add2(s, dec_pair<ST, 0>(base[0 * SLOT + cy(0) * BW]));
@@ -639,20 +643,20 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
         // cell reaches u, phi or psi within a step), or psi >= 1 under the Langmuir EOS
         bool bad = !(fabsf(ux) < 0.3f) | !(fabsf(uy) < 0.3f) | !(fabsf(phi) < 1e30f) | !(fabsf(psi) < 1e30f);
         if (LANGMUIR) bad |= !(psi < 1.f);
-        if (bad) atomicOr(a.status, kStatusUnstable);
+        if (bad) atomicOr(io.status, kStatusUnstable);
     }
 
     const size_t cell = (size_t)y * p.pitch + x;
     if constexpr (MODE == kMoments) {
         const size_t o = (size_t)y * p.nx + x;
-        if (a.out[0]) a.out[0][o] = phi;
-        if (a.out[1]) a.out[1][o] = psi;
-        if (a.out[2]) a.out[2][o] = ux;
-        if (a.out[3]) a.out[3][o] = uy;
-        if (a.out[4]) a.out[4][o] = P_;
+        if (io.out[0]) io.out[0][o] = phi;
+        if (io.out[1]) io.out[1][o] = psi;
+        if (io.out[2]) io.out[2][o] = ux;
+        if (io.out[3]) io.out[3][o] = uy;
+        if (io.out[4]) io.out[4][o] = P_;
     } else {
         uint32_t key = 0;
-        if constexpr (T::kPair16) key = cell_key((uint32_t)cell, a.seed);
+        if constexpr (T::kPair16) key = cell_key((uint32_t)cell, io.seed);
         // ---- f (Sec. 3.1) and g (Sec. 3.2) together; sources cs2 V = d_t(s u) + cs2 (A or B) n ----
         {
             const float2 vx = fma2(make_float2(Aterm, Bterm), bc(nx_ * (1.f / 3.f)), dtX);
@@ -660,7 +664,7 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
             collide_pair(q, pp, sub2(pp, ref), ux, uy, vx, vy, make_float2(p.nS1[0], p.nS1[1]),
                          make_float2(p.nS2[0], p.nS2[1]), make_float2(p.nS3[0], p.nS3[1]),
                          make_float2(p.nS4[0], p.nS4[1]), make_float2(p.K1[0], p.K1[1]), make_float2(p.K3[0], p.K3[1]));
-            P* __restrict__ dfg = static_cast<P*>(a.dst) + cell;
+            P* __restrict__ dfg = static_cast<P*>(io.dst) + cell;
             if constexpr (!T::kPair16) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) dfg[(size_t)i * p.plane] = q[i];
@@ -728,7 +732,7 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
             }
         }
         using Hv = typename T::H;
-        Hv* __restrict__ dh = reinterpret_cast<Hv*>(static_cast<P*>(a.dst) + (size_t)kPairs * p.plane) + cell;
+        Hv* __restrict__ dh = reinterpret_cast<Hv*>(static_cast<P*>(io.dst) + (size_t)kPairs * p.plane) + cell;
         if constexpr (!T::kH16) {
 #pragma unroll
             for (int i = 1; i < 9; ++i) dh[(size_t)(i - 1) * p.plane] = h[i];
@@ -753,8 +757,95 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
             dh16[6 * p.plane] = (unsigned short)(b78 & 0xFFFFu);
             dh16[7 * p.plane] = (unsigned short)(b78 >> 16);
         }
-        a.hist_dst[cell] = make_float2(ux, uy);
+        io.hist_dst[cell] = make_float2(ux, uy);
     }
+}
+
+// One step (or the moments) of one lattice: one TX x TY tile per CTA.
+template <int ST, bool WALLS, bool LANGMUIR, int MODE>
+__global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ StepArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + Smem<ST>::BAR);
+    // The first and the last tile row (whose boxes need edge patching, and so run longest) are
+    // launched first, so that the last wave holds interior tiles only.
+    const int ntr = gridDim.y;
+    const int tr = blockIdx.y == 0 ? 0 : (blockIdx.y == 1 ? ntr - 1 : (int)blockIdx.y - 1);
+    const int x0 = blockIdx.x * TX, y0 = tr * TY;
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+    }
+    // Programmatic dependent launch: let the next step's CTAs be scheduled into the slots this
+    // grid frees, and wait here until the previous step's writes are complete and visible.
+    cudaTriggerProgrammaticLaunchCompletion();
+    cudaGridDependencySynchronize();
+    if (threadIdx.x == 0) issue_tile_loads<ST>(sm, &a.tm_fg, &a.tm_h, &a.tm_hist, x0, y0, mbar);
+    step_tile<ST, WALLS, LANGMUIR, MODE>(a.p, a.io, sm, x0, y0);
+}
+
+// ---- many lattices in one launch ----
+// Per-lattice descriptor, in device memory, written by the host between launches and advanced by
+// batch_advance_kernel.  Buffer `cur` holds the current state; `steps` steps were taken since
+// initialisation.
+struct alignas(64) InstDesc {
+    CUtensorMap tm_fg[2], tm_h[2], tm_hist[2];
+    Phys p;
+    void* pops[2];
+    float2* hist[2];
+    unsigned* status;
+    long long steps;
+    int cur;
+    int first;
+};
+
+// Launch s (0-based) of a sequence that started from the descriptors' state; each CTA owns the
+// tile tiles[blockIdx.x] = (lattice, tile column | tile row << 16).
+struct BatchArgs {
+    const InstDesc* __restrict__ descs;
+    const uint2* __restrict__ tiles;
+    int s;
+};
+
+template <int ST, bool WALLS, bool LANGMUIR>
+__global__ void __launch_bounds__(NT, 4) batch_step_kernel(const __grid_constant__ BatchArgs b) {
+    using S = Smem<ST>;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + S::BAR);
+    cudaTriggerProgrammaticLaunchCompletion();
+    cudaGridDependencySynchronize();  // descriptors and populations of the previous launch
+    const uint2 te = b.tiles[blockIdx.x];
+    const InstDesc& d = b.descs[te.x];
+    const int x0 = (int)(te.y & 0xFFFFu) * TX, y0 = (int)(te.y >> 16) * TY;
+    const int cur = (d.cur + b.s) & 1;
+    // the lattice's constants in shared memory (made visible by the first barrier of step_tile)
+    Phys* sp = reinterpret_cast<Phys*>(sm + S::PHYS);
+    static_assert(sizeof(Phys) % 4 == 0, "Phys is copied as words");
+    for (int k = threadIdx.x; k < (int)(sizeof(Phys) / 4); k += NT)
+        reinterpret_cast<uint32_t*>(sp)[k] = reinterpret_cast<const uint32_t*>(&d.p)[k];
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        issue_tile_loads<ST>(sm, &d.tm_fg[cur], &d.tm_h[cur], &d.tm_hist[cur], x0, y0, mbar);
+    }
+    TileIO io;
+    io.src = d.pops[cur];
+    io.dst = d.pops[cur ^ 1];
+    io.hist_src = d.hist[cur];
+    io.hist_dst = d.hist[cur ^ 1];
+    io.status = d.status;
+    io.out[0] = io.out[1] = io.out[2] = io.out[3] = io.out[4] = nullptr;
+    io.seed = step_seed(d.steps + b.s);
+    io.first = d.first && b.s == 0;
+    step_tile<ST, WALLS, LANGMUIR, kStep>(*sp, io, sm, x0, y0);
+}
+
+// After a sequence of n launches: advance every descriptor by n steps.
+static __global__ void batch_advance_kernel(InstDesc* __restrict__ descs, int count, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count || n <= 0) return;
+    descs[k].steps += n;
+    descs[k].cur = (descs[k].cur + n) & 1;
+    descs[k].first = 0;
 }
 
 // ---- initialisation: equilibria of the given fields, written where the first pull reads them ----

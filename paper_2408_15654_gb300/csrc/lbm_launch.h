@@ -63,6 +63,46 @@ cudaError_t prepare_step_impl(int* blocks_per_sm) {
     return e;
 }
 
+// One launch of the many-lattice kernel over `ntiles` tiles (all lattices of one storage mode,
+// boundary kind and EOS).
+template <int ST>
+cudaError_t launch_batch_impl(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(ntiles);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = Smem<ST>::BYTES_BATCH;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (walls && langmuir) return cudaLaunchKernelEx(&cfg, batch_step_kernel<ST, true, true>, b);
+    if (walls) return cudaLaunchKernelEx(&cfg, batch_step_kernel<ST, true, false>, b);
+    if (langmuir) return cudaLaunchKernelEx(&cfg, batch_step_kernel<ST, false, true>, b);
+    return cudaLaunchKernelEx(&cfg, batch_step_kernel<ST, false, false>, b);
+}
+
+template <int ST, bool W_, bool L_>
+cudaError_t prepare_batch_one() {
+    return cudaFuncSetAttribute(batch_step_kernel<ST, W_, L_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Smem<ST>::BYTES_BATCH);
+}
+
+template <int ST>
+cudaError_t prepare_batch_impl() {
+    cudaError_t e = prepare_batch_one<ST, false, false>();
+    if (e == cudaSuccess) e = prepare_batch_one<ST, false, true>();
+    if (e == cudaSuccess) e = prepare_batch_one<ST, true, false>();
+    if (e == cudaSuccess) e = prepare_batch_one<ST, true, true>();
+    return e;
+}
+
+// Entry points of the per-storage translation units; st is the storage mode.
+cudaError_t launch_batch(int st, const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s);
+cudaError_t prepare_batch(int st);
+
 cudaError_t launch_step_fp32(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t s);
 cudaError_t launch_step_fp16(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t s);
 cudaError_t launch_step_bf16(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, cudaStream_t s);
@@ -73,5 +113,15 @@ cudaError_t prepare_step_fp16(int* blocks_per_sm);
 cudaError_t prepare_step_bf16(int* blocks_per_sm);
 cudaError_t prepare_step_fp16fg(int* blocks_per_sm);
 cudaError_t prepare_step_bf16fg(int* blocks_per_sm);
+cudaError_t launch_batch_fp32(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s);
+cudaError_t launch_batch_fp16(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s);
+cudaError_t launch_batch_bf16(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s);
+cudaError_t launch_batch_fp16fg(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s);
+cudaError_t launch_batch_bf16fg(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s);
+cudaError_t prepare_batch_fp32();
+cudaError_t prepare_batch_fp16();
+cudaError_t prepare_batch_bf16();
+cudaError_t prepare_batch_fp16fg();
+cudaError_t prepare_batch_bf16fg();
 
 }  // namespace lbm

@@ -9,4 +9,10 @@ cudaError_t launch_step_bf16(const StepArgs& a, int mode, bool walls, bool langm
 
 cudaError_t prepare_step_bf16(int* blocks_per_sm) { return prepare_step_impl<kBF16>(blocks_per_sm); }
 
+cudaError_t launch_batch_bf16(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s) {
+    return launch_batch_impl<kBF16>(b, walls, langmuir, ntiles, s);
+}
+
+cudaError_t prepare_batch_bf16() { return prepare_batch_impl<kBF16>(); }
+
 }  // namespace lbm

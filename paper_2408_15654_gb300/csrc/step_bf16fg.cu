@@ -9,4 +9,10 @@ cudaError_t launch_step_bf16fg(const StepArgs& a, int mode, bool walls, bool lan
 
 cudaError_t prepare_step_bf16fg(int* blocks_per_sm) { return prepare_step_impl<kBF16FG>(blocks_per_sm); }
 
+cudaError_t launch_batch_bf16fg(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s) {
+    return launch_batch_impl<kBF16FG>(b, walls, langmuir, ntiles, s);
+}
+
+cudaError_t prepare_batch_bf16fg() { return prepare_batch_impl<kBF16FG>(); }
+
 }  // namespace lbm

@@ -9,4 +9,10 @@ cudaError_t launch_step_fp16fg(const StepArgs& a, int mode, bool walls, bool lan
 
 cudaError_t prepare_step_fp16fg(int* blocks_per_sm) { return prepare_step_impl<kFP16FG>(blocks_per_sm); }
 
+cudaError_t launch_batch_fp16fg(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s) {
+    return launch_batch_impl<kFP16FG>(b, walls, langmuir, ntiles, s);
+}
+
+cudaError_t prepare_batch_fp16fg() { return prepare_batch_impl<kFP16FG>(); }
+
 }  // namespace lbm

@@ -23,12 +23,16 @@ LBM_MEM_HOST, LBM_MEM_DEVICE = 0, 1
 LBM_PHI, LBM_PSI, LBM_UX, LBM_UY, LBM_P = 1, 2, 4, 8, 16
 LBM_SUM_PHI, LBM_SUM_PSI = 0, 1
 LBM_NOALLOC_MAX_ROWS = 8192
+LBM_SCHED_MEMBER_ORDER, LBM_SCHED_LARGEST_FIRST, LBM_SCHED_EDGES_FIRST, LBM_SCHED_ROW_INTERLEAVED = 0, 1, 2, 3
+SCHEDULES = ("member_order", "largest_first", "edges_first", "row_interleaved")
 FIELDS = ("phi", "psi", "ux", "uy", "P")
 
 # Symbols declared in include/lbm.h (checked by the tests against the header and the library).
 EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_init_fields", "lbm_step", "lbm_get_moments",
            "lbm_reduce", "lbm_reduce_noalloc", "lbm_status", "lbm_state_bytes", "lbm_get_state", "lbm_set_state",
-           "lbm_steps_taken", "lbm_destroy", "lbm_last_error")
+           "lbm_steps_taken", "lbm_destroy", "lbm_last_error", "lbm_batch_tiles", "lbm_batch_workspace_bytes",
+           "lbm_batch_create", "lbm_batch_set_members", "lbm_batch_set_schedule", "lbm_batch_step",
+           "lbm_batch_autotune", "lbm_batch_launches", "lbm_batch_destroy")
 
 
 class lbm_params(C.Structure):
@@ -76,6 +80,15 @@ def load(path: str | None = None):
         "lbm_steps_taken": [vp, C.POINTER(C.c_int64)],
         "lbm_destroy": [vp],
         "lbm_last_error": [],
+        "lbm_batch_tiles": [C.POINTER(vp), C.c_int, C.POINTER(C.c_int64)],
+        "lbm_batch_workspace_bytes": [C.c_int, C.c_int64, C.POINTER(sz)],
+        "lbm_batch_create": [C.c_int, C.c_int64, vp, sz, vp, C.POINTER(vp)],
+        "lbm_batch_set_members": [vp, C.POINTER(vp), C.c_int],
+        "lbm_batch_set_schedule": [vp, C.c_int, C.c_int],
+        "lbm_batch_step": [vp, C.c_int64],
+        "lbm_batch_autotune": [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+        "lbm_batch_launches": [vp, C.POINTER(C.c_int64)],
+        "lbm_batch_destroy": [vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -248,3 +261,105 @@ class Lattice:
     @property
     def steps(self) -> int:
         return lbm_steps_taken(self.handle)
+
+
+def _handles(members):
+    return (C.c_void_p * max(1, len(members)))(*[C.c_void_p(m) for m in members])
+
+
+def lbm_batch_tiles(members) -> int:
+    v = C.c_int64()
+    _check(load().lbm_batch_tiles(_handles(members), len(members), C.byref(v)))
+    return v.value
+
+
+def lbm_batch_workspace_bytes(max_members: int, max_tiles: int) -> int:
+    n = C.c_size_t()
+    _check(load().lbm_batch_workspace_bytes(int(max_members), int(max_tiles), C.byref(n)))
+    return n.value
+
+
+def lbm_batch_create(max_members: int, max_tiles: int, workspace_ptr: int, nbytes: int, stream_ptr: int) -> int:
+    b = C.c_void_p()
+    _check(load().lbm_batch_create(int(max_members), int(max_tiles), C.c_void_p(workspace_ptr), nbytes,
+                                   C.c_void_p(stream_ptr), C.byref(b)))
+    return b.value
+
+
+def lbm_batch_set_members(b: int, members):
+    _check(load().lbm_batch_set_members(C.c_void_p(b), _handles(members), len(members)))
+
+
+def lbm_batch_set_schedule(b: int, schedule: int, graph_steps: int):
+    _check(load().lbm_batch_set_schedule(C.c_void_p(b), int(schedule), int(graph_steps)))
+
+
+def lbm_batch_step(b: int, n: int):
+    _check(load().lbm_batch_step(C.c_void_p(b), int(n)))
+
+
+def lbm_batch_autotune(b: int, trial_steps: int):
+    s, k = C.c_int(), C.c_int()
+    _check(load().lbm_batch_autotune(C.c_void_p(b), int(trial_steps), C.byref(s), C.byref(k)))
+    return s.value, k.value
+
+
+def lbm_batch_launches(b: int) -> int:
+    v = C.c_int64()
+    _check(load().lbm_batch_launches(C.c_void_p(b), C.byref(v)))
+    return v.value
+
+
+def lbm_batch_destroy(b: int):
+    _check(load().lbm_batch_destroy(C.c_void_p(b)))
+
+
+class Batch:
+    """Many ``Lattice`` objects advanced together (one launch per step and member group).
+
+    All members must use the batch's stream.  ``capacity`` bounds the member count and
+    ``max_tiles`` the total tile count (default: exactly what ``lattices`` need)."""
+
+    def __init__(self, lattices, stream, capacity=None, max_tiles=None):
+        import torch
+
+        self.lattices = list(lattices)
+        handles = [m.handle for m in self.lattices]
+        capacity = capacity or max(1, len(handles))
+        max_tiles = max_tiles or max(1, lbm_batch_tiles(handles))
+        nbytes = lbm_batch_workspace_bytes(capacity, max_tiles)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream
+        self.handle = lbm_batch_create(capacity, max_tiles, self.workspace.data_ptr(), nbytes, stream.cuda_stream)
+        lbm_batch_set_members(self.handle, handles)
+
+    def set_members(self, lattices):
+        self.lattices = list(lattices)
+        lbm_batch_set_members(self.handle, [m.handle for m in self.lattices])
+
+    def set_schedule(self, schedule, graph_steps=0):
+        if isinstance(schedule, str):
+            schedule = SCHEDULES.index(schedule)
+        lbm_batch_set_schedule(self.handle, schedule, graph_steps)
+
+    def step(self, n: int = 1):
+        lbm_batch_step(self.handle, n)
+
+    def autotune(self, trial_steps: int = 32):
+        s, k = lbm_batch_autotune(self.handle, trial_steps)
+        return SCHEDULES[s], k
+
+    @property
+    def launches(self) -> int:
+        return lbm_batch_launches(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
