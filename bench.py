@@ -212,6 +212,41 @@ def batch_leg(torch, lbm, W, storage: str, steps: int, alone_steps: int = 0):
     return out, cells
 
 
+def serving_leg(torch, lbm, W, reqs, jobs, policy: str, max_jobs: int, force_fp32: bool = False):
+    """Replay the request stream against a lattice server: each job is submitted at its arrival
+    time; time to solution = final fields copied out - submission, on the server's clock."""
+    import numpy as np
+
+    stream = torch.cuda.Stream()
+    srv = lbm.Server(8 << 30 if max_jobs > 1 else 1 << 30, stream, policy=policy, max_jobs=max_jobs,
+                     max_cells=8 << 20, chunk_steps=200, graph_steps=16)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r, (p, f) in zip(reqs, jobs):
+        delay = t0 + r["t"] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        srv.submit(dict(p, storage="fp32") if force_fp32 else p, f, r["steps"])
+    res = []
+    while len(res) < len(reqs):
+        got = srv.poll(64, timeout=5.0)
+        if not got and time.perf_counter() - t0 > 3600:
+            raise RuntimeError("server made no progress")
+        res += got
+    st = srv.stats()
+    srv.close()
+    bad = [r for r in res if r["status"] != lbm.LBM_OK]
+    if bad:
+        raise RuntimeError(f"serving job failed: {bad[0]['message']}")
+    tts = np.array([r["t_done"] - r["t_submit"] for r in res])
+    makespan = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    lup = sum(r["nx"] * r["ny"] * r["steps"] for r in res)
+    return {"policy": policy, "max_jobs": max_jobs, "storage": "fp32" if force_fp32 else "fp32/fp16 as requested",
+            "p50_s": float(np.percentile(tts, 50)), "p99_s": float(np.percentile(tts, 99)),
+            "mean_s": float(tts.mean()), "makespan_s": makespan, "value": lup / makespan / 1e6, "unit": "MLUPS",
+            "lattice_updates": lup, "gpu_launches": st["kernel_launches"], "rounds": st["rounds"]}
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle as it stands on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", 0))
@@ -313,6 +348,20 @@ def run_ours(args):
         batch["workload"] = (f"64 seeded drops (seed 0), sizes uniform over 128^2, 256^2, 512x256, 1024x512 "
                              f"({bcells} cells), walls at +/-U with U ~ U[0, 0.02], linear EOS")
 
+    # serving: a seeded Poisson stream of sheared-drop jobs against the lattice server
+    serving = {}
+    if args.serving_requests > 0:
+        reqs = W.serving_requests(200, 20.0, seed=0)[:args.serving_requests]
+        jobs = [W.serving_job(r) for r in reqs]
+        serving = {"workload": (f"the first {len(reqs)} of 200 seeded requests (seed 0): Poisson arrivals at 20/s, "
+                                f"sheared drops nx = side ~ U{{256..2048 step 64}}, ny = side/2, R = 40 side/512, "
+                                f"steps ~ U[5000, 50000], storage FP32 or FP16 with p = 1/2; p99 over "
+                                f"{len(reqs)} jobs")}
+        for pol in args.serving_policies.split(","):
+            serving[pol] = serving_leg(torch, lbm, W, reqs, jobs, pol, max_jobs=64)
+        serving["one_at_a_time_fp32"] = serving_leg(torch, lbm, W, reqs, jobs, "fcfs", max_jobs=1, force_fp32=True)
+        del jobs
+
     # roofline of the step kernel (one launch per step, so launch duration = step time)
     peak, peak_kind = measured_peak()
     launch_s = ms / args.steps * 1e-3
@@ -347,6 +396,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_lup": BYTES_PER_LUP},
             "half_store": half,
             "batch": batch,
+            "serving": serving,
             "cpu_baseline": base,
             "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": io_bytes / args.steps,
                     "d2h_bytes_per_step": io_bytes / args.steps,
@@ -370,6 +420,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=1000, help="steps of the 64-lattice batch legs (0: skip)")
+    ap.add_argument("--serving-requests", type=int, default=24,
+                    help="requests of the seeded serving stream to replay (at most 200; 0: skip)")
+    ap.add_argument("--serving-policies", default="fcfs,shortest_first")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -259,6 +259,75 @@ int lbm_batch_launches(const lbm_batch* b, int64_t* launches);
 /* Free the batch (host memory only; the workspace and the members stay the caller's). */
 int lbm_batch_destroy(lbm_batch* b);
 
+/* ---- lattice server (continuous batching) --------------------------------------------------
+ * Not in the paper: a job is one lattice (parameters, initial fields, step count); jobs are
+ * submitted from any host thread and run by one worker thread that keeps all admitted jobs in one
+ * many-lattice batch.  Each round advances every active job by one chunk of steps (cut so that no
+ * job passes its step count); finished jobs leave with their final fields copied out and queued
+ * jobs join at the next round.  Results are bit for bit those of the job run alone.
+ * Admission: at most max_jobs active jobs with at most max_cells cells and max_tiles tiles in
+ * total (a job alone may exceed max_cells), whose workspaces fit the job arena (first fit).
+ * LBM_SERVE_FCFS admits in submission order (a job that does not fit blocks those behind it);
+ * LBM_SERVE_SHORTEST_FIRST admits the queued job with the least work (cells x steps) first.     */
+typedef struct lbm_server lbm_server;
+
+#define LBM_SERVE_FCFS 0
+#define LBM_SERVE_SHORTEST_FIRST 1
+
+typedef struct lbm_server_config {
+    int32_t policy;        /* LBM_SERVE_FCFS or LBM_SERVE_SHORTEST_FIRST                      */
+    int32_t max_jobs;      /* active jobs at most (>= 1)                                      */
+    int64_t max_cells;     /* active cells at most (>= 1)                                     */
+    int64_t max_tiles;     /* tiles of all active jobs at most (>= 1); sizes the batch        */
+    int64_t chunk_steps;   /* steps per round at most (>= 1)                                  */
+    int32_t graph_steps;   /* steps per captured CUDA graph of the batch (0: plain launches) */
+    int32_t schedule;      /* tile order of the batch, LBM_SCHED_*                            */
+} lbm_server_config;
+
+typedef struct lbm_job_result {
+    int64_t id;
+    int32_t status;        /* LBM_OK, or the code that ended the job                          */
+    int32_t storage, nx, ny;
+    int64_t steps;
+    double t_submit, t_admit, t_done;  /* seconds on the server's steady clock                */
+    char message[128];     /* error text when status != LBM_OK                                */
+} lbm_job_result;
+
+typedef struct lbm_server_stats {
+    int64_t submitted, completed, queued, active;
+    int64_t lattice_updates;  /* cells x steps advanced so far                                 */
+    int64_t rounds;
+    int64_t kernel_launches;  /* step, advance, init and moments kernels launched so far       */
+    double busy_seconds;      /* worker time spent in rounds (launch to synchronise)          */
+    double now;               /* the server's clock                                           */
+} lbm_server_stats;
+
+/* Device workspace of a server: the batch tables, then a job arena of job_arena_bytes. */
+int lbm_server_workspace_bytes(const lbm_server_config* cfg, size_t job_arena_bytes, size_t* bytes);
+
+/* Start a server (and its worker thread) on the current device.  The workspace (device memory,
+ * 256-byte aligned) and the stream (a created stream, not NULL) are the caller's and must
+ * outlive the server; everything the server launches goes to that stream. */
+int lbm_server_create(const lbm_server_config* cfg, void* d_workspace, size_t bytes, void* cuda_stream,
+                      lbm_server** out);
+
+/* Queue a job.  The five initial fields (host, row-major ny x nx doubles, as lbm_init_fields) and
+ * the non-NULL entries of out (host arrays receiving phi, psi, ux, uy, P at the end, as
+ * lbm_get_moments) stay valid and untouched until the job's result has been polled.  Fails with
+ * LBM_EINVAL for bad parameters or a job that can never fit; *id is the job's id (> 0). */
+int lbm_server_submit(lbm_server* s, const lbm_params* p, const double* phi, const double* psi, const double* ux,
+                      const double* uy, const double* P, int64_t steps, double* const out[5], int64_t* id);
+
+/* Move up to max finished jobs' results into out (*n of them), waiting up to timeout_s seconds
+ * for the first one (0: do not wait).  Results come in completion order. */
+int lbm_server_poll(lbm_server* s, lbm_job_result* out, int max, double timeout_s, int* n);
+
+int lbm_server_get_stats(lbm_server* s, lbm_server_stats* out);
+
+/* Stop the worker after its current round; jobs not finished end with LBM_ESTATE (their results
+ * are dropped with the server).  Frees host memory only. */
+int lbm_server_destroy(lbm_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,8 @@ LBM_SUM_PHI, LBM_SUM_PSI = 0, 1
 LBM_NOALLOC_MAX_ROWS = 8192
 LBM_SCHED_MEMBER_ORDER, LBM_SCHED_LARGEST_FIRST, LBM_SCHED_EDGES_FIRST, LBM_SCHED_ROW_INTERLEAVED = 0, 1, 2, 3
 SCHEDULES = ("member_order", "largest_first", "edges_first", "row_interleaved")
+LBM_SERVE_FCFS, LBM_SERVE_SHORTEST_FIRST = 0, 1
+POLICIES = {"fcfs": LBM_SERVE_FCFS, "shortest_first": LBM_SERVE_SHORTEST_FIRST}
 FIELDS = ("phi", "psi", "ux", "uy", "P")
 
 # Symbols declared in include/lbm.h (checked by the tests against the header and the library).
@@ -32,7 +34,9 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_init_fields", "lbm_step", "
            "lbm_reduce", "lbm_reduce_noalloc", "lbm_status", "lbm_state_bytes", "lbm_get_state", "lbm_set_state",
            "lbm_steps_taken", "lbm_destroy", "lbm_last_error", "lbm_batch_tiles", "lbm_batch_workspace_bytes",
            "lbm_batch_create", "lbm_batch_set_members", "lbm_batch_set_schedule", "lbm_batch_step",
-           "lbm_batch_autotune", "lbm_batch_launches", "lbm_batch_destroy")
+           "lbm_batch_autotune", "lbm_batch_launches", "lbm_batch_destroy", "lbm_server_workspace_bytes",
+           "lbm_server_create", "lbm_server_submit", "lbm_server_poll", "lbm_server_get_stats",
+           "lbm_server_destroy")
 
 
 class lbm_params(C.Structure):
@@ -46,6 +50,23 @@ class lbm_params(C.Structure):
         ("gy", C.c_double), ("n_eps", C.c_double),
         ("s_f", C.c_double * 5), ("s_g", C.c_double * 5), ("s_h", C.c_double * 5),
     ]
+
+
+class lbm_server_config(C.Structure):
+    _fields_ = [("policy", C.c_int32), ("max_jobs", C.c_int32), ("max_cells", C.c_int64), ("max_tiles", C.c_int64),
+                ("chunk_steps", C.c_int64), ("graph_steps", C.c_int32), ("schedule", C.c_int32)]
+
+
+class lbm_job_result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("storage", C.c_int32), ("nx", C.c_int32),
+                ("ny", C.c_int32), ("steps", C.c_int64), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("message", C.c_char * 128)]
+
+
+class lbm_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("queued", C.c_int64), ("active", C.c_int64),
+                ("lattice_updates", C.c_int64), ("rounds", C.c_int64), ("kernel_launches", C.c_int64),
+                ("busy_seconds", C.c_double), ("now", C.c_double)]
 
 
 class LBMError(RuntimeError):
@@ -89,6 +110,12 @@ def load(path: str | None = None):
         "lbm_batch_autotune": [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)],
         "lbm_batch_launches": [vp, C.POINTER(C.c_int64)],
         "lbm_batch_destroy": [vp],
+        "lbm_server_workspace_bytes": [C.POINTER(lbm_server_config), sz, C.POINTER(sz)],
+        "lbm_server_create": [C.POINTER(lbm_server_config), vp, sz, vp, C.POINTER(vp)],
+        "lbm_server_submit": [vp, P, vp, vp, vp, vp, vp, C.c_int64, C.POINTER(vp), C.POINTER(C.c_int64)],
+        "lbm_server_poll": [vp, C.POINTER(lbm_job_result), C.c_int, C.c_double, C.POINTER(C.c_int)],
+        "lbm_server_get_stats": [vp, C.POINTER(lbm_server_stats)],
+        "lbm_server_destroy": [vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -356,6 +383,97 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lbm_server_workspace_bytes(cfg: lbm_server_config, job_arena_bytes: int) -> int:
+    n = C.c_size_t()
+    _check(load().lbm_server_workspace_bytes(C.byref(cfg), int(job_arena_bytes), C.byref(n)))
+    return n.value
+
+
+def lbm_server_create(cfg: lbm_server_config, workspace_ptr: int, nbytes: int, stream_ptr: int) -> int:
+    h = C.c_void_p()
+    _check(load().lbm_server_create(C.byref(cfg), C.c_void_p(workspace_ptr), nbytes, C.c_void_p(stream_ptr),
+                                    C.byref(h)))
+    return h.value
+
+
+def lbm_server_submit(s: int, params: lbm_params, fields, steps: int, outs) -> int:
+    v = C.c_int64()
+    arr = (C.c_void_p * 5)(*[(C.c_void_p(o.ctypes.data) if o is not None else None) for o in outs])
+    _check(load().lbm_server_submit(C.c_void_p(s), C.byref(params), *[C.c_void_p(a.ctypes.data) for a in fields],
+                                    int(steps), arr, C.byref(v)))
+    return v.value
+
+
+def lbm_server_poll(s: int, max_results: int, timeout_s: float):
+    buf = (lbm_job_result * max(1, max_results))()
+    n = C.c_int()
+    _check(load().lbm_server_poll(C.c_void_p(s), buf, int(max_results), float(timeout_s), C.byref(n)))
+    return [buf[k] for k in range(n.value)]
+
+
+def lbm_server_get_stats(s: int) -> dict:
+    st = lbm_server_stats()
+    _check(load().lbm_server_get_stats(C.c_void_p(s), C.byref(st)))
+    return {f: getattr(st, f) for f, _ in lbm_server_stats._fields_}
+
+
+def lbm_server_destroy(s: int):
+    _check(load().lbm_server_destroy(C.c_void_p(s)))
+
+
+class Server:
+    """A lattice server on the current device: jobs run by a native worker thread in one
+    continuously re-formed batch.  ``arena_bytes`` of device memory hold the job workspaces."""
+
+    def __init__(self, arena_bytes: int, stream, policy="fcfs", max_jobs=64, max_cells=1 << 24,
+                 max_tiles=1 << 20, chunk_steps=100, graph_steps=16, schedule="largest_first"):
+        import torch
+
+        cfg = lbm_server_config()
+        cfg.policy = POLICIES[policy] if isinstance(policy, str) else int(policy)
+        cfg.max_jobs, cfg.max_cells, cfg.max_tiles = int(max_jobs), int(max_cells), int(max_tiles)
+        cfg.chunk_steps, cfg.graph_steps = int(chunk_steps), int(graph_steps)
+        cfg.schedule = SCHEDULES.index(schedule) if isinstance(schedule, str) else int(schedule)
+        nbytes = lbm_server_workspace_bytes(cfg, arena_bytes)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream
+        self.handle = lbm_server_create(cfg, self.workspace.data_ptr(), nbytes, stream.cuda_stream)
+        self._jobs = {}
+
+    def submit(self, params: dict, fields: dict, steps: int, outputs: bool = True) -> int:
+        ny, nx = int(params["ny"]), int(params["nx"])
+        ins = [np.ascontiguousarray(np.broadcast_to(np.asarray(fields[k], dtype=np.float64), (ny, nx)))
+               for k in FIELDS]
+        outs = [np.empty((ny, nx)) for _ in FIELDS] if outputs else [None] * 5
+        jid = lbm_server_submit(self.handle, make_params(params), ins, steps, outs)
+        self._jobs[jid] = (ins, outs)  # kept alive until the result is polled
+        return jid
+
+    def poll(self, max_results: int = 64, timeout: float = 0.0) -> list:
+        out = []
+        for r in lbm_server_poll(self.handle, max_results, timeout):
+            ins, outs = self._jobs.pop(r.id)
+            d = {f: getattr(r, f) for f, _ in lbm_job_result._fields_ if f != "message"}
+            d["message"] = r.message.decode(errors="replace")
+            d["moments"] = {FIELDS[k]: outs[k] for k in range(5) if outs[k] is not None}
+            out.append(d)
+        return out
+
+    def stats(self) -> dict:
+        return lbm_server_get_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -16,6 +16,8 @@ Workloads (stand-ins for the paper's Sec. 4 benchmarks; the paper's comparison d
   shear_drop         drop between walls moving at +/-U (Sec. 4.4): 512 x 256 with R = 40 and
                      2048 x 1024 with R = 160, Re = 1, Ca = 0.2, Langmuir EOS E0 = 0.2, psi0 = 0.3
   batch_instances    64 seeded drops of mixed sizes for the batched launch
+  serving_requests   a seeded Poisson stream of sheared-drop jobs of mixed sizes, step counts and
+                     storage modes, for the lattice server
 """
 from __future__ import annotations
 
@@ -173,3 +175,32 @@ def batch_instances(count=64, seed=0):
         ux = -U + 2.0 * U * (y + 0.5) / ny
         out.append((p, fields(phi, psi, ux=ux)))
     return out
+
+
+SERVING_SIDES = tuple(range(256, 2049, 64))
+
+
+def serving_requests(count=200, rate=20.0, seed=0):
+    """Seeded job stream for the lattice server: Poisson arrivals at `rate` per second; each job a
+    sheared drop (as shear_drop) of nx = side ~ U{256, 320, ..., 2048}, ny = side / 2 and
+    R = 40 side / 512; steps ~ U[5000, 50000]; storage FP32 or FP16 with probability 1/2 each.
+    Returns dicts with the arrival time `t` (seconds from the first), nx, ny, R, steps, storage;
+    serving_job builds a job's parameters and fields."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(count):
+        if k:
+            t += rng.exponential(1.0 / rate)
+        side = int(SERVING_SIDES[rng.integers(0, len(SERVING_SIDES))])
+        steps = int(rng.integers(5000, 50001))
+        storage = "fp16" if rng.random() < 0.5 else "fp32"
+        out.append({"t": t, "nx": side, "ny": side // 2, "R": 40.0 * side / 512.0, "steps": steps,
+                    "storage": storage})
+    return out
+
+
+def serving_job(req: dict):
+    """Parameters (with the request's storage mode) and initial fields of one server job."""
+    p, f = shear_drop(nx=req["nx"], ny=req["ny"], R=req["R"])
+    return dict(p, storage=req["storage"]), f

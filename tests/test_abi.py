@@ -22,7 +22,7 @@ def declared_functions():
 def test_library_exports_every_declared_symbol():
     lib = lbm.load()
     names = declared_functions()
-    assert len(names) >= 12
+    assert len(names) >= 27
     assert sorted(lbm.EXPORTS) == names
     for n in names:
         assert hasattr(lib, n), n
@@ -31,19 +31,21 @@ def test_library_exports_every_declared_symbol():
     assert set(names) <= exported
 
 
-def test_params_struct_layout_matches_header(tmp_path):
+@pytest.mark.parametrize("name", ["lbm_params", "lbm_server_config", "lbm_job_result", "lbm_server_stats"])
+def test_struct_layout_matches_header(tmp_path, name):
     """Compile a probe against the header with gcc and compare sizeof/offsetof with ctypes."""
-    fields = [f[0] for f in lbm.lbm_params._fields_]
+    cls = getattr(lbm, name)
+    fields = [f[0] for f in cls._fields_]
     src = tmp_path / "probe.c"
-    body = "\n".join(f'printf("{f} %zu\\n", offsetof(lbm_params, {f}));' for f in fields)
+    body = "\n".join(f'printf("{f} %zu\\n", offsetof({name}, {f}));' for f in fields)
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm.h"\nint main(void){'
-                   f'printf("size %zu\\n", sizeof(lbm_params));{body}return 0;}}\n')
+                   f'printf("size %zu\\n", sizeof({name}));{body}return 0;}}\n')
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), "-o", str(exe), str(src)], check=True)
     got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n") if line)
-    assert int(got["size"]) == C.sizeof(lbm.lbm_params)
+    assert int(got["size"]) == C.sizeof(cls)
     for f in fields:
-        assert int(got[f]) == getattr(lbm.lbm_params, f).offset, f
+        assert int(got[f]) == getattr(cls, f).offset, f
 
 
 def test_workspace_bytes_without_gpu():
