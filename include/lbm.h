@@ -198,6 +198,20 @@ int lbm_steps_taken(const lbm_handle* h, int64_t* steps);
 /* Free the handle (not the workspace).  Waits for the handle's stream.  NULL is allowed. */
 int lbm_destroy(lbm_handle* h);
 
+/* Step kernel of a handle.  Both variants compute the same step bit for bit; they differ in how
+ * the work is laid out on the GPU:
+ *   LBM_KERNEL_TILE       one CTA per 32 x 8 tile, launched as a grid of all tiles;
+ *   LBM_KERNEL_PIPELINED  persistent CTAs (as many as fit on all SMs, at most one per tile),
+ *                         each staging its next tile with TMA while it computes the current one;
+ *   LBM_KERNEL_AUTO       (lbm_set_kernel only) the library's choice, currently TILE for every
+ *                         storage mode (the faster or equal one on GB300 at 2048 x 1024).
+ * A new handle uses the library's choice.  LBM_EINVAL if the pipelined kernel does not fit. */
+#define LBM_KERNEL_AUTO 0
+#define LBM_KERNEL_TILE 1
+#define LBM_KERNEL_PIPELINED 2
+int lbm_set_kernel(lbm_handle* h, int variant);
+int lbm_get_kernel(const lbm_handle* h, int* variant);
+
 /* Message describing the last failing call on this host thread ("" if none).  The pointer is
  * valid until the next call on the same thread. */
 const char* lbm_last_error(void);

@@ -40,11 +40,15 @@ struct lbm_handle {
     void* pops[2];
     float2* hist[2];         // u history, alternating with the population buffers
     unsigned* status;
+    unsigned* tile_ctr;      // two tile counters of the pipelined kernel (status region + 8 bytes)
+    int64_t last_pipe_step;  // step index of the last pipelined launch (-2: none since a reset)
     double* partials;
     CUtensorMap tm_fg[2];    // TMA descriptors of the (f, g) pair planes of each buffer
     CUtensorMap tm_h[2];     // TMA descriptors of the h planes of each buffer
     CUtensorMap tm_hist[2];  // TMA descriptors of the u history buffers
     int tiles_x, tiles_y;    // step-kernel grid: one TX x TY tile per CTA
+    int kernel;              // LBM_KERNEL_TILE or LBM_KERNEL_PIPELINED
+    int pipe_ctas;           // CTAs of the pipelined kernel (0: it does not fit)
     int cur;          // buffer holding the current state
     int initialized;
     int first;        // 1 until the first step after lbm_init_fields

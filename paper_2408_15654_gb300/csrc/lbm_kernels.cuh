@@ -161,6 +161,13 @@ template <int ST> struct Smem {
     static constexpr int BYTES = BAR + 16;
     static constexpr int PHYS = BYTES;                       // batched kernel: the instance's Phys
     static constexpr int BYTES_BATCH = PHYS + (int)((sizeof(Phys) + 15) / 16 * 16);
+    // pipelined kernel: two stages of the TMA boxes ([0, PP) each), one (phi, psi) tile, two
+    // mbarriers
+    static constexpr int STAGE = PP;
+    static constexpr int PIPE_PP = 2 * STAGE;
+    static constexpr int PIPE_BAR = PIPE_PP + NE * 8;
+    static constexpr int PIPE_SLOT = PIPE_BAR + 16;  // tile index of each stage
+    static constexpr int BYTES_PIPE = PIPE_SLOT + 16;
     static constexpr unsigned TX_BYTES =
         (unsigned)(kPairs * FG_BOX * sizeof(typename T::P) + kHPlanes * H_BOX * sizeof(typename T::H) + HIST_BYTES);
 };
@@ -183,6 +190,8 @@ struct StepArgs {
     CUtensorMap tm_hist;          // {nx, ny, 1} float2, box {TX, TY, 1} or {BW, BH, 1}
     Phys p;
     TileIO io;
+    unsigned* tile_ctr;           // pipelined kernel: tile counter of this launch (zero at start)
+    unsigned* tile_ctr_next;      // and of the next launch, zeroed by this one
 };
 
 // Salt of the stochastic rounding of step number `steps` (steps taken since initialisation), a
@@ -448,23 +457,24 @@ __device__ __forceinline__ void issue_tile_loads(unsigned char* sm, const CUtens
 }
 
 // One fused step (kStep) or the macroscopic fields of the current level (kMoments) for one tile,
-// after one thread has issued the tile's TMA loads on the mbarrier.  Edge tiles patch wrapped and
-// bounced entries.  The pulled (f, g) of the tile and of a one-cell ring give (phi, psi) for the
+// after one thread has issued the tile's TMA loads into `stage` on `mbar`, whose phase of this
+// tile has parity `parity`; PP holds the tile's (phi, psi).  Returns true (uniformly) if a copy
+// did not arrive within its bounded wait (nothing stored).  Edge tiles patch wrapped and bounced
+// entries.  The pulled (f, g) of the tile and of a one-cell ring give (phi, psi) for the
 // 9-point stencils; the same boxes hold the own cell's unshifted post-collision values, whose sums
 // are phi and psi of the previous level (m*_0 = phi exactly, Sec. 3.1), so only u of the
 // previous level is stored.
 template <int ST, bool WALLS, bool LANGMUIR, int MODE>
-__device__ __forceinline__ void step_tile(const Phys& p, const TileIO& io, unsigned char* sm, int x0, int y0) {
+__device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsigned char* sm, float2* PP,
+                                          unsigned long long* mbar, uint32_t parity, int x0, int y0) {
     using T = Traits<ST>;
     using S = Smem<ST>;
     using P = typename T::P;
     const P* FG = reinterpret_cast<const P*>(sm + S::FG);
     const float2* Hist = reinterpret_cast<const float2*>(sm + S::HIST);
-    float2* PP = reinterpret_cast<float2*>(sm + S::PP);
-    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + S::BAR);
     const int t = threadIdx.x;
     __syncthreads();
-    bool abort = !mbar_wait_bounded(mbar, 0);
+    bool abort = !mbar_wait_bounded(mbar, parity);
     if (x0 == 0 || x0 + TX + 8 > p.nx || y0 == 0 || y0 + TY + 2 > p.ny) {
         if (!abort) patch_edges<ST, WALLS>(p, io, sm, x0, y0);
         abort = __syncthreads_or(abort);
@@ -528,12 +538,12 @@ __device__ __forceinline__ void step_tile(const Phys& p, const TileIO& io, unsig
         // a staging copy did not arrive in time: report it, wait (bounded) for it, store nothing
         if (t == 0) {
             atomicOr(io.status, kStatusTimeout);
-            mbar_wait_bounded(mbar, 0);
+            mbar_wait_bounded(mbar, parity);
         }
         __syncthreads();
-        return;
+        return true;
     }
-    if (!active) return;
+    if (!active) return false;
 
     const float2 pp = PP[eo];          // (phi, psi)
     const float phi = pp.x, psi = pp.y;
@@ -759,6 +769,7 @@ __device__ __forceinline__ void step_tile(const Phys& p, const TileIO& io, unsig
         }
         io.hist_dst[cell] = make_float2(ux, uy);
     }
+    return false;
 }
 
 // One step (or the moments) of one lattice: one TX x TY tile per CTA.
@@ -780,7 +791,80 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     cudaTriggerProgrammaticLaunchCompletion();
     cudaGridDependencySynchronize();
     if (threadIdx.x == 0) issue_tile_loads<ST>(sm, &a.tm_fg, &a.tm_h, &a.tm_hist, x0, y0, mbar);
-    step_tile<ST, WALLS, LANGMUIR, MODE>(a.p, a.io, sm, x0, y0);
+    step_tile<ST, WALLS, LANGMUIR, MODE>(a.p, a.io, sm, reinterpret_cast<float2*>(sm + Smem<ST>::PP), mbar, 0, x0, y0);
+}
+
+// Tile k of a grid of ntx x nty tiles: rows in the order first, last, then the interior (the two
+// edge rows, which patch their boxes, run first).
+__device__ __forceinline__ void tile_origin(int k, int ntx, int nty, int& x0, int& y0) {
+    const int r = k / ntx, c = k - r * ntx;
+    const int tr = r == 0 ? 0 : (r == 1 ? nty - 1 : r - 1);
+    x0 = c * TX;
+    y0 = tr * TY;
+}
+
+// One step of one lattice by a persistent grid: each CTA claims tiles from an atomic counter
+// and stages its next tile's boxes with TMA into the other of two buffers while it computes the
+// current one, so the copy latency hides behind the arithmetic.  Claiming tiles one at a time
+// balances the longer edge tiles across the CTAs.  Thread 0 claims a tile one iteration before
+// it needs it, so the atomic's latency also hides behind a tile's work.
+template <int ST, bool WALLS, bool LANGMUIR>
+__global__ void __launch_bounds__(NT, 4) step_kernel_pipe(const __grid_constant__ StepArgs a, int ntx, int nty) {
+    using S = Smem<ST>;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float2* PP = reinterpret_cast<float2*>(sm + S::PIPE_PP);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(sm + S::PIPE_BAR);
+    volatile unsigned* slot = reinterpret_cast<volatile unsigned*>(sm + S::PIPE_SLOT);
+    const unsigned ntiles = (unsigned)(ntx * nty);
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    cudaTriggerProgrammaticLaunchCompletion();
+    cudaGridDependencySynchronize();  // also: the previous launch no longer uses its counter
+    unsigned ahead = 0;               // thread 0: the tile claimed for the stage after next
+    if (threadIdx.x == 0) {
+        if (blockIdx.x == 0) *a.tile_ctr_next = 0u;
+        const unsigned k0 = atomicAdd(a.tile_ctr, 1u);
+        slot[0] = k0;
+        if (k0 < ntiles) {
+            int x0, y0;
+            tile_origin((int)k0, ntx, nty, x0, y0);
+            issue_tile_loads<ST>(sm, &a.tm_fg, &a.tm_h, &a.tm_hist, x0, y0, &bars[0]);
+            ahead = atomicAdd(a.tile_ctr, 1u);
+        } else {
+            ahead = ntiles;
+        }
+    }
+    __syncthreads();
+    for (int it = 0;; ++it) {
+        const int cur = it & 1, nxt = cur ^ 1;
+        const unsigned k = slot[cur];
+        if (k >= ntiles) break;  // uniform: every thread reads the same slot
+        if (threadIdx.x == 0) {
+            // the other stage and its slot were released by the barrier that ended the previous tile
+            slot[nxt] = ahead;
+            if (ahead < ntiles) {
+                int xn, yn;
+                tile_origin((int)ahead, ntx, nty, xn, yn);
+                issue_tile_loads<ST>(sm + nxt * S::STAGE, &a.tm_fg, &a.tm_h, &a.tm_hist, xn, yn, &bars[nxt]);
+                ahead = atomicAdd(a.tile_ctr, 1u);
+            }
+        }
+        int x0, y0;
+        tile_origin((int)k, ntx, nty, x0, y0);
+        if (step_tile<ST, WALLS, LANGMUIR, kStep>(a.p, a.io, sm + cur * S::STAGE, PP, &bars[cur], (it >> 1) & 1, x0,
+                                                  y0)) {
+            // a copy timed out: stop this CTA, after waiting (bounded) for the copy in flight
+            if (threadIdx.x == 0 && slot[nxt] < ntiles) mbar_wait_bounded(&bars[nxt], ((it + 1) >> 1) & 1);
+            break;
+        }
+        // stage `cur`, its slot and PP are free again; order this CTA's generic accesses to the
+        // stage (the edge patch writes it) before the asynchronous TMA writes of the tile after next
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+    }
 }
 
 // ---- many lattices in one launch ----
@@ -836,7 +920,7 @@ __global__ void __launch_bounds__(NT, 4) batch_step_kernel(const __grid_constant
     io.out[0] = io.out[1] = io.out[2] = io.out[3] = io.out[4] = nullptr;
     io.seed = step_seed(d.steps + b.s);
     io.first = d.first && b.s == 0;
-    step_tile<ST, WALLS, LANGMUIR, kStep>(*sp, io, sm, x0, y0);
+    step_tile<ST, WALLS, LANGMUIR, kStep>(*sp, io, sm, reinterpret_cast<float2*>(sm + S::PP), mbar, 0, x0, y0);
 }
 
 // After a sequence of n launches: advance every descriptor by n steps.

@@ -26,13 +26,15 @@ LBM_NOALLOC_MAX_ROWS = 8192
 LBM_SCHED_MEMBER_ORDER, LBM_SCHED_LARGEST_FIRST, LBM_SCHED_EDGES_FIRST, LBM_SCHED_ROW_INTERLEAVED = 0, 1, 2, 3
 SCHEDULES = ("member_order", "largest_first", "edges_first", "row_interleaved")
 LBM_SERVE_FCFS, LBM_SERVE_SHORTEST_FIRST = 0, 1
+LBM_KERNEL_AUTO, LBM_KERNEL_TILE, LBM_KERNEL_PIPELINED = 0, 1, 2
+KERNELS = {"auto": LBM_KERNEL_AUTO, "tile": LBM_KERNEL_TILE, "pipelined": LBM_KERNEL_PIPELINED}
 POLICIES = {"fcfs": LBM_SERVE_FCFS, "shortest_first": LBM_SERVE_SHORTEST_FIRST}
 FIELDS = ("phi", "psi", "ux", "uy", "P")
 
 # Symbols declared in include/lbm.h (checked by the tests against the header and the library).
 EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_init_fields", "lbm_step", "lbm_get_moments",
            "lbm_reduce", "lbm_reduce_noalloc", "lbm_status", "lbm_state_bytes", "lbm_get_state", "lbm_set_state",
-           "lbm_steps_taken", "lbm_destroy", "lbm_last_error", "lbm_batch_tiles", "lbm_batch_workspace_bytes",
+           "lbm_steps_taken", "lbm_destroy", "lbm_last_error", "lbm_set_kernel", "lbm_get_kernel", "lbm_batch_tiles", "lbm_batch_workspace_bytes",
            "lbm_batch_create", "lbm_batch_set_members", "lbm_batch_set_schedule", "lbm_batch_step",
            "lbm_batch_autotune", "lbm_batch_launches", "lbm_batch_destroy", "lbm_server_workspace_bytes",
            "lbm_server_create", "lbm_server_submit", "lbm_server_poll", "lbm_server_get_stats",
@@ -101,6 +103,8 @@ def load(path: str | None = None):
         "lbm_steps_taken": [vp, C.POINTER(C.c_int64)],
         "lbm_destroy": [vp],
         "lbm_last_error": [],
+        "lbm_set_kernel": [vp, C.c_int],
+        "lbm_get_kernel": [vp, C.POINTER(C.c_int)],
         "lbm_batch_tiles": [C.POINTER(vp), C.c_int, C.POINTER(C.c_int64)],
         "lbm_batch_workspace_bytes": [C.c_int, C.c_int64, C.POINTER(sz)],
         "lbm_batch_create": [C.c_int, C.c_int64, vp, sz, vp, C.POINTER(vp)],
@@ -288,6 +292,16 @@ class Lattice:
     @property
     def steps(self) -> int:
         return lbm_steps_taken(self.handle)
+
+    @property
+    def kernel(self) -> str:
+        v = C.c_int()
+        _check(load().lbm_get_kernel(C.c_void_p(self.handle), C.byref(v)))
+        return {LBM_KERNEL_TILE: "tile", LBM_KERNEL_PIPELINED: "pipelined"}[v.value]
+
+    @kernel.setter
+    def kernel(self, name: str):
+        _check(load().lbm_set_kernel(C.c_void_p(self.handle), KERNELS[name]))
 
 
 def _handles(members):

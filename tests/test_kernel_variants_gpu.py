@@ -1,0 +1,74 @@
+"""The two step kernels (one CTA per tile; persistent CTAs with a double-buffered TMA pipeline)
+compute the same step bit for bit, in every storage mode, on ragged and full-size grids."""
+import pytest
+
+from paper_2408_15654_gb300 import lbm
+from paper_2408_15654_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lbm.load()
+    return torch
+
+
+def cases():
+    p, f = W.shear_drop(96, 40, R=9)
+    yield "shear_96x40", p, f
+    p, f = W.stationary_drop(70, 50, R=12)
+    yield "periodic_70x50_perturbed", p, W.perturbed(p, f, seed=1)
+    p, f = W.shear_drop(45, 19, R=6)
+    yield "walls_45x19_perturbed", p, W.perturbed(p, f, seed=2)
+    p, f = W.shear_drop(20, 6, R=2.5)
+    yield "below_one_tile", p, f
+
+
+def run(torch, p, f, kernel, steps):
+    g = lbm.Lattice(p)
+    g.kernel = kernel
+    g.init(**f)
+    g.step(steps)
+    torch.cuda.synchronize()
+    assert g.kernel == kernel
+    s = g.state()
+    g.close()
+    return s
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16", "fp16_fg", "bf16_fg"])
+def test_pipelined_equals_tile(torch, storage):
+    for name, p, f in cases():
+        q = dict(p, storage=storage)
+        g = lbm.Lattice(q)
+        try:
+            g.kernel = "pipelined"
+        except lbm.LBMError:
+            pytest.skip(f"the pipelined kernel does not fit for {storage}")
+        finally:
+            g.close()
+        assert run(torch, q, f, "tile", 9) == run(torch, q, f, "pipelined", 9), name
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16_fg"])
+def test_pipelined_equals_tile_full_size(torch, storage):
+    """2048 x 1024: every persistent CTA takes 13 or 14 tiles through both pipeline stages."""
+    p, f = W.shear_drop_large()
+    q = dict(p, storage=storage)
+    assert run(torch, q, f, "tile", 5) == run(torch, q, f, "pipelined", 5)
+
+
+def test_default_kernel_per_storage(torch):
+    p, f = W.stationary_drop(64, 64, R=14)
+    got = {}
+    for st in ("fp32", "fp16", "bf16", "fp16_fg", "bf16_fg"):
+        g = lbm.Lattice(dict(p, storage=st))
+        got[st] = g.kernel
+        g.kernel = "auto"
+        assert g.kernel == got[st]
+        g.close()
+    assert all(v == "tile" for v in got.values())
