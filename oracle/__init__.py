@@ -34,6 +34,7 @@ class _Params(C.Structure):
         ("sigma0", C.c_double), ("E0", C.c_double),
         ("gx", C.c_double), ("gy", C.c_double), ("rho0", C.c_double), ("n_eps", C.c_double),
         ("s_f", C.c_double * 5), ("s_g", C.c_double * 5), ("s_h", C.c_double * 5),
+        ("prescribed", C.c_int),
     ]
 
 
@@ -105,6 +106,7 @@ def make_params(p: dict) -> _Params:
     q.nx, q.ny = int(p["nx"]), int(p["ny"])
     q.walls = 1 if p.get("walls", False) else 0
     q.eos = EOS_LANGMUIR if p.get("eos", "linear") == "langmuir" else EOS_LINEAR
+    q.prescribed = 1 if p.get("velocity", "solved") == "prescribed" else 0
     for k in ("u_top", "u_bot", "phiA", "phiB", "rhoA", "rhoB", "muA", "muB", "W", "M_phi", "D",
               "sigma0", "E0", "gx", "gy", "rho0", "n_eps"):
         setattr(q, k, float(p[k]))

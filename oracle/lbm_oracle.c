@@ -46,6 +46,11 @@
  * convection-diffusion of a sine mode; Laplace jump (linear and Langmuir EOS); exact Couette flow;
  * Couette start-up; shear-wave viscous decay; Poiseuille profile under a body force; the closed
  * form of uniformly accelerated flow (pins K); wall channel = mirrored periodic domain.
+ * Prescribed-velocity mode (the convection test of Sec. 4): only f and g evolve, u is the imposed
+ * field given at initialisation (constant in time, so d_t(phi u) = u d_t phi), there is no h and
+ * P is reported as 0.  Pins: with u = 0 it equals the full model at rest with sigma0 = 0; a sine
+ * mode of psi is advected and damped as exp(-D k^2 t) sin(k (x - u t)); the centroid of a
+ * convected drop moves at u.
  * Parity unpinned: the terms that act only when rhoA != rhoB (mass flux S, grad rho in H, m2H and
  * P) are checked only through the moment conditions of h_eq and H, not by a closed-form solution.
  */
@@ -266,6 +271,7 @@ struct orc_sim {
     double *phi, *psi;             /* zeroth moments at the current time level */
     double *phi_prev, *psi_prev;   /* history (time level n - 1) */
     double *ux_prev, *uy_prev, *Sx_prev, *Sy_prev;
+    double *ux_imp, *uy_imp;       /* imposed velocity (prescribed mode) */
     int first;                     /* 1: no history yet, time derivatives are zero */
     long steps;
     int status;
@@ -326,8 +332,10 @@ orc_sim* orc_create(const orc_params* p) {
     s->uy_prev = calloc(N, sizeof(double));
     s->Sx_prev = calloc(N, sizeof(double));
     s->Sy_prev = calloc(N, sizeof(double));
+    s->ux_imp = calloc(N, sizeof(double));
+    s->uy_imp = calloc(N, sizeof(double));
     if (!s->f || !s->g || !s->h || !s->fs || !s->gs || !s->hs || !s->phi || !s->psi || !s->phi_prev ||
-        !s->psi_prev || !s->ux_prev || !s->uy_prev || !s->Sx_prev || !s->Sy_prev) {
+        !s->psi_prev || !s->ux_prev || !s->uy_prev || !s->Sx_prev || !s->Sy_prev || !s->ux_imp || !s->uy_imp) {
         orc_destroy(s);
         return NULL;
     }
@@ -342,6 +350,7 @@ void orc_destroy(orc_sim* s) {
     free(s->phi); free(s->psi);
     free(s->phi_prev); free(s->psi_prev);
     free(s->ux_prev); free(s->uy_prev); free(s->Sx_prev); free(s->Sy_prev);
+    free(s->ux_imp); free(s->uy_imp);
     free(s);
 }
 
@@ -366,8 +375,10 @@ int orc_init(orc_sim* s, const double* phi, const double* psi, const double* ux,
         for (int i = 0; i < 9; ++i) {
             s->f[i * N + k] = feq[i];
             s->g[i * N + k] = geq[i];
-            s->h[i * N + k] = heq[i];
+            s->h[i * N + k] = p->prescribed ? 0.0 : heq[i];
         }
+        s->ux_imp[k] = ux[k];
+        s->uy_imp[k] = uy[k];
     }
     s->first = 1;
     s->steps = 0;
@@ -456,7 +467,7 @@ static void cell_macros(orc_sim* s, int x, int y, cell_state* cs, orc_cell_out* 
     c->Sx = sfac * (gpx - Aterm * c->nx);
     c->Sy = sfac * (gpy - Aterm * c->ny);
 
-    /* 7. velocity and pressure (Sec. 3.3) */
+    /* 7. velocity and pressure (Sec. 3.3); in the prescribed mode u is the imposed field */
     double jx = 0.0, jy = 0.0, hsum = 0.0;
     for (int i = 0; i < 9; ++i) {
         const double hi = s->h[i * N + k];
@@ -464,8 +475,8 @@ static void cell_macros(orc_sim* s, int x, int y, cell_state* cs, orc_cell_out* 
         jy += CY[i] * hi;
         if (i != 0) hsum += hi;
     }
-    const double ux = (jx + 0.5 * Fx) / rho;
-    const double uy = (jy + 0.5 * Fy) / rho;
+    const double ux = p->prescribed ? s->ux_imp[k] : (jx + 0.5 * Fx) / rho;
+    const double uy = p->prescribed ? s->uy_imp[k] : (jy + 0.5 * Fy) / rho;
     c->ux = ux;
     c->uy = uy;
 
@@ -494,6 +505,7 @@ static void cell_macros(orc_sim* s, int x, int y, cell_state* cs, orc_cell_out* 
     const double ugr = ux * c->drho_x + uy * c->drho_y;
     const double jmS_u = (rho * ux - c->Sx) * ux + (rho * uy - c->Sy) * uy;
     c->P = CS2 / (1.0 - WGT[0]) * (hsum + 0.5 * ugr - WGT[0] * jmS_u / (2.0 * CS2) + K * 0.5 * dt_k);
+    if (p->prescribed) c->P = 0.0;
 
     if (out) {
         out->phi = phi;
@@ -566,7 +578,7 @@ int orc_step(orc_sim* s, long nsteps) {
                     }
                     s->fs[i * N + k] = s->f[i * N + k] + cf;
                     s->gs[i * N + k] = s->g[i * N + k] + cg;
-                    s->hs[i * N + k] = s->h[i * N + k] + ch;
+                    s->hs[i * N + k] = p->prescribed ? 0.0 : s->h[i * N + k] + ch;
                 }
                 rho_now[k] = cs.c.rho;
                 /* history for the next step's time derivatives (stored after the sweep) */
@@ -593,7 +605,8 @@ int orc_step(orc_sim* s, long nsteps) {
                         const double uw = yd_raw >= ny ? p->u_top : p->u_bot;
                         s->f[ib * N + k] = s->fs[i * N + k];
                         s->g[ib * N + k] = s->gs[i * N + k];
-                        s->h[ib * N + k] = s->hs[i * N + k] - 2.0 * WGT[i] * rho_now[k] * (CX[i] * uw) / CS2;
+                        s->h[ib * N + k] =
+                            p->prescribed ? 0.0 : s->hs[i * N + k] - 2.0 * WGT[i] * rho_now[k] * (CX[i] * uw) / CS2;
                     } else {
                         const long kd = (long)wrap(yd_raw, ny) * nx + xd;
                         s->f[i * N + kd] = s->fs[i * N + k];

@@ -24,6 +24,7 @@ typedef struct {
     double rho0;           /* constant in lambda_0 of h_eq */
     double n_eps;          /* |grad phi| threshold below which n = 0 */
     double s_f[5], s_g[5], s_h[5]; /* (s0, s1, s2, s3, s4); the transport entries are recomputed */
+    int prescribed;        /* 0: u from the flow populations; 1: u imposed (the initial ux, uy), no h */
 } orc_params;
 
 /* Everything the equilibria and source distributions of one cell depend on. */

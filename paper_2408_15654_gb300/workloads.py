@@ -15,6 +15,9 @@ Workloads (stand-ins for the paper's Sec. 4 benchmarks; the paper's comparison d
                      sigma0 = 0 so the flow stays at rest (Sec. 4.1)
   shear_drop         drop between walls moving at +/-U (Sec. 4.4): 512 x 256 with R = 40 and
                      2048 x 1024 with R = 160, Re = 1, Ca = 0.2, Langmuir EOS E0 = 0.2, psi0 = 0.3
+  convected_drop     a drop carried by an imposed uniform velocity (prescribed-velocity mode):
+                     the convection test of Sec. 4 (100 x 100, R = 20, u = (0.05, 0), psi = phi,
+                     M_phi = 1, D = 2 in lattice units)
   batch_instances    64 seeded drops of mixed sizes for the batched launch
   serving_requests   a seeded Poisson stream of sheared-drop jobs of mixed sizes, step counts and
                      storage modes, for the lattice server
@@ -38,7 +41,7 @@ def base_params(nx: int, ny: int, **kw) -> dict:
         nx=int(nx), ny=int(ny), walls=False, eos="linear", u_top=0.0, u_bot=0.0,
         phiA=1.0, phiB=0.0, rhoA=1.0, rhoB=1.0, muA=0.1, muB=0.1,
         W=4.0, M_phi=0.05, D=0.02, sigma0=1e-3, E0=0.5, gx=0.0, gy=0.0, rho0=1.0,
-        n_eps=1e-12, s_f=_UNIT_RATES, s_g=_UNIT_RATES, s_h=_FLOW_RATES,
+        n_eps=1e-12, s_f=_UNIT_RATES, s_g=_UNIT_RATES, s_h=_FLOW_RATES, velocity="solved",
     )
     for k, v in kw.items():
         if k not in p:
@@ -96,6 +99,15 @@ def surface_diffusion(n=256, R=60.0, W=4.0, D=0.05, M_phi=0.05):
     theta = polar_angle(n, n)
     psi = 0.5 * (1.0 + np.cos(theta)) * interface_weight(phi)
     return p, fields(phi, psi)
+
+
+def convected_drop(nx=100, ny=100, R=20.0, W=4.0, u=(0.05, 0.0), M_phi=1.0, D=2.0):
+    """Drop carried by the imposed uniform velocity u in a periodic box (prescribed-velocity mode,
+    no flow populations); psi starts equal to phi, as in the paper's convection test (Sec. 4:
+    R = 0.2 in the unit box at dx = 0.01, u = (0.5, 0) at dt = 0.001, M_phi = 0.1, D = 0.2)."""
+    p = base_params(nx, ny, W=W, M_phi=M_phi, D=D, sigma0=0.0, E0=0.0, velocity="prescribed")
+    phi = drop_phi(nx, ny, R, W)
+    return p, fields(phi, phi.copy(), ux=u[0], uy=u[1])
 
 
 def shear_params(nx, ny, R, U=0.01, Re=1.0, Ca=0.2, rho=1.0):

@@ -468,3 +468,62 @@ def test_langmuir_marangoni_and_laplace():
     dP = m["P"][r < R - 12].mean() - m["P"][r > R + 12].mean()
     seff = quad(lambda s: 0.75 * 1e-3 * (1 + 0.2 * math.log(1 - psi0 * _sech(s) ** 2)) * _sech(s) ** 4, -20, 20)[0]
     assert dP == pytest.approx(seff / R, rel=0.02)
+
+
+# ---- prescribed-velocity mode (the convection test of Sec. 4): f and g only, u imposed ----
+
+def test_prescribed_zero_velocity_equals_the_full_model_at_rest():
+    """With sigma0 = 0 and u = 0 the flow populations stay at rest, so the full model carries f and
+    g exactly as the prescribed mode does with u = 0 imposed."""
+    p, f = W.stationary_drop(48, 40, R=11, sigma0=0.0)
+    f = dict(f, ux=0.0, uy=0.0)
+    full = run(p, f, 150)
+    pres = run(dict(p, velocity="prescribed"), f, 150)
+    (fa, ga, _), (fb, gb, _) = full.populations(), pres.populations()
+    np.testing.assert_allclose(fb, fa, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(gb, ga, rtol=0, atol=1e-15)
+    assert np.abs(pres.moments()["P"]).max() == 0.0
+
+
+def test_prescribed_velocity_carries_a_sine_mode():
+    """Uniform phi (no interface): psi obeys the convection-diffusion equation with the imposed
+    velocity, psi = psi0 + a exp(-D k^2 t) sin(k (x - u t)); the transverse velocity component does
+    not touch an x mode."""
+    nx, ny, k_, u0, D, steps = 64, 4, 2 * np.pi / 64, 0.05, 0.05, 1000
+    p = dict(W.base_params(nx, ny, sigma0=0.0, D=D), velocity="prescribed")
+    x, _ = W.grid(nx, ny)
+    s = run(p, W.fields(np.zeros((ny, nx)), 0.2 + 0.1 * np.sin(k_ * x), ux=u0, uy=0.02), steps)
+    m = s.moments()
+    c = ((m["psi"].mean(axis=0) - 0.2) * np.exp(-1j * k_ * x[0])).sum() * 2 / nx
+    assert abs(c) / 0.1 == pytest.approx(math.exp(-D * k_ * k_ * steps), rel=2e-3)
+    expect = -np.pi / 2 - k_ * u0 * steps
+    assert abs(np.angle(np.exp(1j * (np.angle(c) - expect)))) < 5e-3
+    np.testing.assert_array_equal(m["ux"], u0)
+    np.testing.assert_array_equal(m["uy"], 0.02)
+
+
+def _circular_centroid(phi):
+    ny, nx = phi.shape
+    cx = np.angle((phi.sum(0) * np.exp(2j * np.pi * np.arange(nx) / nx)).sum()) * nx / (2 * np.pi)
+    cy = np.angle((phi.sum(1) * np.exp(2j * np.pi * np.arange(ny) / ny)).sum()) * ny / (2 * np.pi)
+    return cx, cy
+
+
+def test_prescribed_convected_drop_moves_with_the_imposed_velocity():
+    """The convection test of Sec. 4 (100 x 100, R = 20, u = (0.05, 0), psi = phi): over one period
+    (2000 steps) the drop's centroid moves by u t to within 0.5 % (the sharpening flux of the moving
+    interface makes the discrete drop lag by 0.27 %), the phase field keeps its mass and its area,
+    and the y centroid does not move."""
+    p, f = W.convected_drop()
+    s = run(p, f, 0)
+    m0 = s.moments()
+    cx0, cy0 = _circular_centroid(m0["phi"])
+    s.step(1000)
+    m1 = s.moments()
+    cx1, cy1 = _circular_centroid(m1["phi"])
+    assert (cx1 - cx0) % 100 == pytest.approx(50.0, rel=5e-3)
+    assert abs(cy1 - cy0) < 1e-9
+    assert m1["phi"].sum() == pytest.approx(m0["phi"].sum(), rel=1e-12)
+    assert m1["psi"].sum() == pytest.approx(m0["psi"].sum(), rel=1e-12)
+    assert (m1["phi"] > 0.5).sum() == pytest.approx((m0["phi"] > 0.5).sum(), rel=0.01)
+    assert np.abs(m1["P"]).max() == 0.0
