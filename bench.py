@@ -32,6 +32,7 @@ NX, NY = 2048, 1024
 BYTES_PER_LUP = 26 * 4 * 2 + 2 * 4 * 2  # 26 live float populations and 2 history floats, read + written
 BYTES_PER_LUP_16 = 26 * 2 * 2 + 2 * 4 * 2  # the same populations stored in 16 bits
 BYTES_PER_LUP_FG = 18 * 2 * 2 + 8 * 4 * 2 + 2 * 4 * 2  # f, g in 16 bits, h in FP32
+BYTES_PER_LUP_PRESCRIBED = {"fp32": 9 * 8 * 2 + 2 * 4 * 2, "fp16": 9 * 4 * 2 + 2 * 4 * 2}  # f, g and u only
 HALF_MODES = {"fp16": BYTES_PER_LUP_16, "bf16": BYTES_PER_LUP_16, "fp16_fg": BYTES_PER_LUP_FG,
               "bf16_fg": BYTES_PER_LUP_FG}
 METRIC = "MLUPS (3 lattices) and % HBM roofline, FP32 vs half-store; serving p50/p99"
@@ -339,6 +340,32 @@ def run_ours(args):
                     "frac_of_measured_hbm": hach / measured_peak()[0], "algorithmic_bytes_per_lup": bpl}
         hs.close()
 
+    # prescribed velocity (f and g only): the convection test's drop at 2048 x 1024
+    prescribed = {}
+    pp, pf = W.convected_drop(NX, NY, R=160.0)
+    for st, bpl in BYTES_PER_LUP_PRESCRIBED.items():
+        ps = lbm.Lattice(dict(pp, storage=st), stream=stream)
+        ps.init(**pf)
+        ps.step(args.warmup)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ps.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = barrier_max(e0.elapsed_time(e1), world)
+        if ps.status != lbm.LBM_OK:
+            raise RuntimeError(f"unstable state in the prescribed {st} benchmark: {lbm.lbm_last_error()}")
+        pach = cells * bpl / (e0.elapsed_time(e1) / args.steps * 1e-3) / 1e9
+        prescribed[st] = {"value": cells * args.steps * world / (pms * 1e-3) / 1e6, "unit": "MLUPS",
+                          "ms_per_step": pms / args.steps, "achieved_gbs": pach,
+                          "frac_of_measured_hbm": pach / measured_peak()[0], "algorithmic_bytes_per_lup": bpl}
+        ps.close()
+    if prescribed:
+        prescribed["workload"] = ("drop R=160 carried by an imposed u = (0.05, 0) on 2048x1024, periodic, "
+                                  "M_phi=1, D=2 (the convection test of Sec. 4 scaled up); f, g only")
+
     # many lattices at once: the 64-lattice mix, FP32 and FP16 storage
     batch = {}
     if args.batch_steps > 0:
@@ -395,6 +422,7 @@ def run_ours(args):
                          "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_lup": BYTES_PER_LUP},
             "half_store": half,
+            "prescribed_velocity": prescribed,
             "batch": batch,
             "serving": serving,
             "cpu_baseline": base,
@@ -403,6 +431,7 @@ def run_ours(args):
                     "job": f"lbm_init_fields(host) + lbm_step({args.steps}) + lbm_get_moments(host, all 5)"},
             "gpu_launches": args.steps,
             "gpu_launches_half_store": len(HALF_MODES) * args.steps,
+            "gpu_launches_prescribed": len(BYTES_PER_LUP_PRESCRIBED) * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -55,6 +55,12 @@ extern "C" {
 #define LBM_STORE_FP16_FG 3 /* f and g as FP16 deviations, h as float                        */
 #define LBM_STORE_BF16_FG 4 /* f and g as BF16 deviations, h as float                        */
 
+#define LBM_VELOCITY_SOLVED 0     /* u from the flow populations h (Sec. 3.3)                  */
+#define LBM_VELOCITY_PRESCRIBED 1 /* u imposed (the ux, uy given to lbm_init_fields, constant in
+                                     time); only f and g are stored and advanced, P is 0, the EOS
+                                     and the flow parameters are unused (the convection test of
+                                     Sec. 4)                                                   */
+
 #define LBM_MEM_HOST 0      /* pointer arguments are host memory (pageable or pinned)        */
 #define LBM_MEM_DEVICE 1    /* pointer arguments are device memory on the handle's device    */
 
@@ -81,7 +87,7 @@ typedef struct lbm_params {
     int32_t bc_y;           /* LBM_BC_PERIODIC or LBM_BC_WALLS                               */
     int32_t eos;            /* LBM_EOS_LINEAR or LBM_EOS_LANGMUIR                            */
     int32_t storage;        /* one of LBM_STORE_* (arithmetic is FP32 in every mode)         */
-    int32_t reserved;       /* must be 0                                                     */
+    int32_t velocity;       /* LBM_VELOCITY_SOLVED or LBM_VELOCITY_PRESCRIBED                */
     double u_top, u_bot;    /* x velocity of the top and bottom wall (LBM_BC_WALLS)          */
     double phiA, phiB;      /* order parameter of the pure phases (Sec. 2.1)                 */
     double rhoA, rhoB;      /* densities (Sec. 2.3, linear in phi)                           */
@@ -102,8 +108,9 @@ typedef struct lbm_handle lbm_handle;
  * parameters.
  * Layout: the workspace starts with the two population buffers, each B * ny * pitch bytes rounded
  * up to a multiple of 256, with pitch = nx rounded up to a multiple of 32 and B = 104 (FP32
- * storage), 52 (FP16, BF16) or 68 (FP16_FG, BF16_FG).  A buffer holds 9 planes of (f_i, g_i)
- * pairs followed by 8 planes h_1..h_8 (h_0 never influences the step), each plane ny rows of
+ * storage), 52 (FP16, BF16) or 68 (FP16_FG, BF16_FG); with LBM_VELOCITY_PRESCRIBED, 72 (FP32)
+ * or 36 (16-bit).  A buffer holds 9 planes of (f_i, g_i) pairs followed by 8 planes h_1..h_8
+ * (h_0 never influences the step; no h planes with a prescribed velocity), each plane ny rows of
  * pitch cells; after lbm_init_fields and k steps the current state is buffer k mod 2 (buffer 0
  * at offset 0).
  * FP32 storage holds the values.  16-bit storage (FP16 / BF16, arithmetic still FP32) holds

@@ -528,7 +528,7 @@ static void cell_macros(orc_sim* s, int x, int y, cell_state* cs, orc_cell_out* 
 static void status_check(orc_sim* s, const cell_state* cs) {
     const orc_cell_in* c = &cs->c;
     int bad = !isfinite(c->phi) || !isfinite(c->psi) || !isfinite(c->ux) || !isfinite(c->uy) || !isfinite(c->P);
-    if (s->p.eos == ORC_EOS_LANGMUIR && !(c->psi < 1.0)) bad = 1;
+    if (s->p.eos == ORC_EOS_LANGMUIR && !s->p.prescribed && !(c->psi < 1.0)) bad = 1; /* EOS unused if prescribed */
     if (bad) {
 #pragma omp atomic write
         s->status = 1;

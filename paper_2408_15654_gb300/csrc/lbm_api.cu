@@ -81,14 +81,7 @@ int encode_map(CUtensorMap* tm, void* base, int es, int nx, int ny, int planes, 
 // Opt the step-kernel instances of storage mode st into their shared memory; CTAs per SM of the
 // one-tile and of the pipelined kernels.
 int prepare_kernels(int st, int* blocks_per_sm, int* pipe_blocks_per_sm) {
-    cudaError_t e;
-    switch (st) {
-        case LBM_STORE_FP16: e = lbm::prepare_step_fp16(blocks_per_sm, pipe_blocks_per_sm); break;
-        case LBM_STORE_BF16: e = lbm::prepare_step_bf16(blocks_per_sm, pipe_blocks_per_sm); break;
-        case LBM_STORE_FP16_FG: e = lbm::prepare_step_fp16fg(blocks_per_sm, pipe_blocks_per_sm); break;
-        case LBM_STORE_BF16_FG: e = lbm::prepare_step_bf16fg(blocks_per_sm, pipe_blocks_per_sm); break;
-        default: e = lbm::prepare_step_fp32(blocks_per_sm, pipe_blocks_per_sm); break;
-    }
+    cudaError_t e = lbm::prepare_step(st, blocks_per_sm, pipe_blocks_per_sm);
     if (e != cudaSuccess) return fail(LBM_ECUDA, "kernel setup: %s", cudaGetErrorString(e));
     if (*blocks_per_sm < 1) return fail(LBM_ECUDA, "the step kernel does not fit on an SM");
     return LBM_OK;
@@ -104,7 +97,8 @@ int validate(const lbm_params* p) {
     if (p->eos != LBM_EOS_LINEAR && p->eos != LBM_EOS_LANGMUIR) return fail(LBM_EINVAL, "bad eos");
     if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16_FG)
         return fail(LBM_EINVAL, "storage mode %d not supported", p->storage);
-    if (p->reserved != 0) return fail(LBM_EINVAL, "reserved must be 0");
+    if (p->velocity != LBM_VELOCITY_SOLVED && p->velocity != LBM_VELOCITY_PRESCRIBED)
+        return fail(LBM_EINVAL, "bad velocity mode %d", p->velocity);
     if (!(p->phiA != p->phiB) || !(p->W > 0) || !(p->M_phi > 0) || !(p->D > 0))
         return fail(LBM_EINVAL, "need phiA != phiB, W > 0, M_phi > 0, D > 0");
     if (!(p->rhoA > 0) || p->rhoA != p->rhoB)
@@ -132,7 +126,7 @@ Layout layout_of(const lbm_params* p) {
     Layout L;
     L.pitch = (p->nx + 31) / 32 * 32;
     L.plane = (size_t)p->ny * L.pitch;
-    L.pops_bytes = align_up(L.plane * (size_t)lbm::pop_bytes_per_cell(p->storage));
+    L.pops_bytes = align_up(L.plane * (size_t)lbm::pop_bytes_per_cell(p->storage, p->velocity == LBM_VELOCITY_SOLVED));
     size_t off = 0;
     L.off_pops[0] = off; off += L.pops_bytes;
     L.off_pops[1] = off; off += L.pops_bytes;
@@ -248,14 +242,9 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
         a.tile_ctr_next = h->tile_ctr + ((h->steps + 1) & 1);
         h->last_pipe_step = h->steps;
     }
-    cudaError_t e;
-    switch (h->prm.storage) {
-        case LBM_STORE_FP16: e = lbm::launch_step_fp16(a, mode, walls, lang, grid, pipe, h->stream); break;
-        case LBM_STORE_BF16: e = lbm::launch_step_bf16(a, mode, walls, lang, grid, pipe, h->stream); break;
-        case LBM_STORE_FP16_FG: e = lbm::launch_step_fp16fg(a, mode, walls, lang, grid, pipe, h->stream); break;
-        case LBM_STORE_BF16_FG: e = lbm::launch_step_bf16fg(a, mode, walls, lang, grid, pipe, h->stream); break;
-        default: e = lbm::launch_step_fp32(a, mode, walls, lang, grid, pipe, h->stream); break;
-    }
+    const bool flow = h->prm.velocity == LBM_VELOCITY_SOLVED;
+    const lbm::Variant v{walls, flow && lang, flow};  // the EOS is unused with a prescribed velocity
+    cudaError_t e = lbm::launch_step(h->prm.storage, a, mode, v, grid, pipe, h->stream);
     if (e != cudaSuccess) return fail(LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
@@ -399,7 +388,8 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
         rc = encode_map(&h->tm_fg[b], h->pops[b], es_pair, p->nx, p->ny, lbm::kPairs, L.pitch, L.plane, lbm::BW,
                         lbm::BH, 1);
         char* hbase = static_cast<char*>(h->pops[b]) + (size_t)lbm::kPairs * L.plane * es_pair;
-        if (!rc) rc = encode_map(&h->tm_h[b], hbase, es_h, p->nx, p->ny, lbm::kHPlanes, L.pitch, L.plane, hbw, lbm::TY, 1);
+        if (!rc && p->velocity == LBM_VELOCITY_SOLVED)  // no h planes with a prescribed velocity
+            rc = encode_map(&h->tm_h[b], hbase, es_h, p->nx, p->ny, lbm::kHPlanes, L.pitch, L.plane, hbw, lbm::TY, 1);
     }
     for (int b = 0; b < 2 && !rc; ++b)
         rc = h16 ? encode_map(&h->tm_hist[b], h->hist[b], 8, p->nx, p->ny, 1, L.pitch, L.plane, lbm::BW, lbm::BH, 1)
@@ -453,6 +443,7 @@ int lbm_init_fields(lbm_handle* h, const double* phi, const double* psi, const d
     a.status = h->status;
     a.langmuir = h->prm.eos == LBM_EOS_LANGMUIR;
     a.walls = h->prm.bc_y == LBM_BC_WALLS;
+    a.flow = h->prm.velocity == LBM_VELOCITY_SOLVED;
     const dim3 block(32, 8), grid((h->prm.nx + 31) / 32, (h->prm.ny + 7) / 8);
     switch (h->prm.storage) {
         case LBM_STORE_FP16: lbm::init_kernel<lbm::kFP16><<<grid, block, 0, h->stream>>>(a); break;
@@ -556,7 +547,7 @@ static const uint64_t kStateMagic = 0x4c424d3253544154ull;  // "LBM2STAT"
 int lbm_state_bytes(const lbm_handle* h, size_t* bytes) {
     g_err.clear();
     if (!h || !bytes) return fail(LBM_EINVAL, "NULL argument");
-    *bytes = sizeof(StateHeader) + h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage) +
+    *bytes = sizeof(StateHeader) + h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage, h->prm.velocity == LBM_VELOCITY_SOLVED) +
              h->L.plane * sizeof(float2);
     return LBM_OK;
 }
@@ -571,7 +562,7 @@ int lbm_get_state(lbm_handle* h, void* host_blob, size_t bytes) {
     StateHeader hd{kStateMagic, h->prm.nx, h->prm.ny, h->L.pitch, h->first, h->steps};
     char* b = static_cast<char*>(host_blob);
     std::memcpy(b, &hd, sizeof(hd));
-    const size_t pb = h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage);
+    const size_t pb = h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage, h->prm.velocity == LBM_VELOCITY_SOLVED);
     LBM_CUDA(cudaMemcpyAsync(b + sizeof(hd), h->pops[h->cur], pb, cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(cudaMemcpyAsync(b + sizeof(hd) + pb, h->hist[h->cur], h->L.plane * sizeof(float2), cudaMemcpyDeviceToHost,
                              h->stream));
@@ -590,7 +581,7 @@ int lbm_set_state(lbm_handle* h, const void* host_blob, size_t bytes) {
     std::memcpy(&hd, b, sizeof(hd));
     if (hd.magic != kStateMagic || hd.nx != h->prm.nx || hd.ny != h->prm.ny || hd.pitch != h->L.pitch)
         return fail(LBM_EINVAL, "state blob does not match this handle");
-    const size_t pb = h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage);
+    const size_t pb = h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage, h->prm.velocity == LBM_VELOCITY_SOLVED);
     const int cur = (int)(hd.steps & 1);  // the current state after k steps is buffer k mod 2
     LBM_CUDA(cudaMemcpyAsync(h->pops[cur], b + sizeof(hd), pb, cudaMemcpyHostToDevice, h->stream));
     LBM_CUDA(cudaMemcpyAsync(h->hist[cur], b + sizeof(hd) + pb, h->L.plane * sizeof(float2), cudaMemcpyHostToDevice,

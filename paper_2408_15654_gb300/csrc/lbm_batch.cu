@@ -16,11 +16,21 @@ namespace {
 
 struct Group {
     int st;
-    bool walls, lang;
+    bool walls, lang, flow;
     int64_t off, count;  // tiles [off, off + count) of the tile list
 };
 
 int64_t tiles_of(const lbm_handle* h) { return (int64_t)h->tiles_x * h->tiles_y; }
+
+// Kernel variant of a lattice (the EOS is unused with a prescribed velocity).
+Group group_of(const lbm_handle* h) {
+    const bool flow = h->prm.velocity == LBM_VELOCITY_SOLVED;
+    return Group{h->prm.storage, h->prm.bc_y == LBM_BC_WALLS, flow && h->prm.eos == LBM_EOS_LANGMUIR, flow, 0, 0};
+}
+
+bool same_group(const Group& a, const Group& b) {
+    return a.st == b.st && a.walls == b.walls && a.lang == b.lang && a.flow == b.flow;
+}
 
 // Tile rows of one lattice in launch order: the two edge rows (which patch their boxes and run
 // longest) first, then the interior rows.
@@ -69,26 +79,22 @@ int build_tiles(lbm_batch* b) {
     // group keys in a fixed order
     std::vector<Group> groups;
     for (int k : order) {
-        const lbm_handle* h = b->members[k];
-        const int st = h->prm.storage;
-        const bool w = h->prm.bc_y == LBM_BC_WALLS, l = h->prm.eos == LBM_EOS_LANGMUIR;
+        const Group gk = group_of(b->members[k]);
         bool found = false;
-        for (const Group& g : groups) found = found || (g.st == st && g.walls == w && g.lang == l);
-        if (!found) groups.push_back(Group{st, w, l, 0, 0});
+        for (const Group& g : groups) found = found || same_group(g, gk);
+        if (!found) groups.push_back(gk);
     }
     std::sort(groups.begin(), groups.end(), [](const Group& a, const Group& c) {
-        return a.st != c.st ? a.st < c.st : (a.walls != c.walls ? a.walls < c.walls : a.lang < c.lang);
+        if (a.st != c.st) return a.st < c.st;
+        if (a.flow != c.flow) return a.flow < c.flow;
+        return a.walls != c.walls ? a.walls < c.walls : a.lang < c.lang;
     });
     std::vector<uint2> tiles;
     for (Group& g : groups) {
         g.off = (int64_t)tiles.size();
         std::vector<int> mem;
-        for (int k : order) {
-            const lbm_handle* h = b->members[k];
-            if (h->prm.storage == g.st && (h->prm.bc_y == LBM_BC_WALLS) == g.walls &&
-                (h->prm.eos == LBM_EOS_LANGMUIR) == g.lang)
-                mem.push_back(k);
-        }
+        for (int k : order)
+            if (same_group(group_of(b->members[k]), g)) mem.push_back(k);
         auto push_row = [&](int k, int ty) {
             const lbm_handle* h = b->members[k];
             for (int tx = 0; tx < h->tiles_x; ++tx) tiles.push_back(make_uint2((unsigned)k, (unsigned)tx | ((unsigned)ty << 16)));
@@ -162,7 +168,7 @@ int launch_one(lbm_batch* b, int s) {
         a.descs = b->d_desc;
         a.tiles = b->d_tiles + g.off;
         a.s = s;
-        cudaError_t e = lbm::launch_batch(g.st, a, g.walls, g.lang, (unsigned)g.count, b->stream);
+        cudaError_t e = lbm::launch_batch(g.st, a, lbm::Variant{g.walls, g.lang, g.flow}, (unsigned)g.count, b->stream);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "batch step launch: %s", cudaGetErrorString(e));
         b->launches++;
     }

@@ -90,9 +90,11 @@ template <> struct Traits<kBF16FG> {
     static constexpr float SF = 1.f, SG = 1.f, SH = 1.f;
 };
 
-// Bytes of one population buffer per cell: 9 (f, g) pairs + 8 h values.
-__host__ __device__ constexpr int pop_bytes_per_cell(int st) {
-    return st == kFP32 ? 9 * 8 + 8 * 4 : (st == kFP16 || st == kBF16 ? 9 * 4 + 8 * 2 : 9 * 4 + 8 * 4);
+// Bytes of one population buffer per cell: 9 (f, g) pairs + 8 h values (no h when the velocity
+// is prescribed).
+__host__ __device__ constexpr int pop_bytes_per_cell(int st, bool flow = true) {
+    return !flow ? (st == kFP32 ? 9 * 8 : 9 * 4)
+                 : (st == kFP32 ? 9 * 8 + 8 * 4 : (st == kFP16 || st == kBF16 ? 9 * 4 + 8 * 2 : 9 * 4 + 8 * 4));
 }
 __host__ __device__ constexpr bool pair_is_16bit(int st) { return st != kFP32; }
 __host__ __device__ constexpr bool h_is_16bit(int st) { return st == kFP16 || st == kBF16; }
@@ -144,6 +146,18 @@ static_assert(NRING <= NT, "one thread per ring cell");
 
 __host__ __device__ constexpr int round128(int b) { return (b + 127) / 128 * 128; }
 
+// Buffers of one step of one lattice.
+struct TileIO {
+    const void* __restrict__ src;
+    void* __restrict__ dst;
+    const float2* __restrict__ hist_src;  // (u_x, u_y) of the previous step
+    float2* __restrict__ hist_dst;        // (u_x, u_y) of this step (the other history buffer)
+    unsigned* __restrict__ status;
+    double* __restrict__ out[5];  // kMoments: phi, psi, ux, uy, P (dense ny x nx), may be null
+    unsigned seed;                // per-step salt of the stochastic rounding
+    int first;                    // 1 on the first step after initialisation (zero d/dt terms)
+};
+
 // Shared-memory layout (bytes) of one tile for storage mode ST.
 template <int ST> struct Smem {
     using T = Traits<ST>;
@@ -159,7 +173,8 @@ template <int ST> struct Smem {
     static constexpr int PP = HIST + round128(HIST_BYTES);
     static constexpr int BAR = PP + NE * 8;
     static constexpr int BYTES = BAR + 16;
-    static constexpr int PHYS = BYTES;                       // batched kernel: the instance's Phys
+    // batched kernel: the lattice's constants
+    static constexpr int PHYS = BYTES;
     static constexpr int BYTES_BATCH = PHYS + (int)((sizeof(Phys) + 15) / 16 * 16);
     // pipelined kernel: two stages of the TMA boxes ([0, PP) each), one (phi, psi) tile, two
     // mbarriers
@@ -170,19 +185,9 @@ template <int ST> struct Smem {
     static constexpr int BYTES_PIPE = PIPE_SLOT + 16;
     static constexpr unsigned TX_BYTES =
         (unsigned)(kPairs * FG_BOX * sizeof(typename T::P) + kHPlanes * H_BOX * sizeof(typename T::H) + HIST_BYTES);
+    static constexpr unsigned TX_BYTES_NOH = (unsigned)(kPairs * FG_BOX * sizeof(typename T::P) + HIST_BYTES);
 };
 
-// Buffers of one step of one lattice.
-struct TileIO {
-    const void* __restrict__ src;
-    void* __restrict__ dst;
-    const float2* __restrict__ hist_src;  // (u_x, u_y) of the previous step
-    float2* __restrict__ hist_dst;        // (u_x, u_y) of this step (the other history buffer)
-    unsigned* __restrict__ status;
-    double* __restrict__ out[5];  // kMoments: phi, psi, ux, uy, P (dense ny x nx), may be null
-    unsigned seed;                // per-step salt of the stochastic rounding
-    int first;                    // 1 on the first step after initialisation (zero d/dt terms)
-};
 
 struct StepArgs {
     CUtensorMap tm_fg;            // {nx, ny, 9} pairs, box {BW, BH, 1}
@@ -351,7 +356,7 @@ __device__ __forceinline__ void collide_pair(float2 q[9], float2 s, float2 sr, f
 // by the one the pull really reads there -- the periodic image, or across a wall the pulling
 // cell's own opposite slot (bounce-back).  Only the out-of-grid strips of each box are visited
 // (one warp per box); entries no valid pull reads are left as loaded.
-template <int ST, bool WALLS>
+template <int ST, bool WALLS, bool FLOW>
 __device__ void patch_edges(const Phys& p, const TileIO& io, unsigned char* sm, int x0, int y0) {
     using T = Traits<ST>;
     using S = Smem<ST>;
@@ -362,6 +367,7 @@ __device__ void patch_edges(const Phys& p, const TileIO& io, unsigned char* sm, 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NBOX = kPairs + kHPlanes + (S::kHalo ? 1 : 0);
     for (int pl = warp; pl < NBOX; pl += NT / 32) {
+        if (!FLOW && pl >= kPairs && pl < kPairs + kHPlanes) continue;  // no h boxes
         const int kind = pl < kPairs ? 0 : (pl < kPairs + kHPlanes ? 1 : 2);  // pair, h, history
         const int i = kind == 0 ? pl : (kind == 1 ? pl - kPairs + 1 : 0);      // direction
         const int bw = kind == 1 ? T::H_BW : BW;
@@ -441,17 +447,19 @@ __device__ __forceinline__ float load_h(const unsigned char* sm, const float2* H
 }
 
 // Stage the boxes of tile (x0, y0) with TMA on one mbarrier (called by one thread).
-template <int ST>
+template <int ST, bool FLOW>
 __device__ __forceinline__ void issue_tile_loads(unsigned char* sm, const CUtensorMap* tm_fg, const CUtensorMap* tm_h,
                                                  const CUtensorMap* tm_hist, int x0, int y0, unsigned long long* mbar) {
     using T = Traits<ST>;
     using S = Smem<ST>;
-    mbar_expect_tx(mbar, S::TX_BYTES);
+    mbar_expect_tx(mbar, FLOW ? S::TX_BYTES : S::TX_BYTES_NOH);
 #pragma unroll
     for (int i = 0; i < kPairs; ++i) tma_load_3d(sm + S::FG + i * S::FG_SLOT, tm_fg, x0 - 4, y0 - 1 - cy(i), i, mbar);
+    if constexpr (FLOW) {
 #pragma unroll
-    for (int i = 1; i < 9; ++i)
-        tma_load_3d(sm + S::H + (i - 1) * S::H_SLOT, tm_h, x0 - T::H_X0, y0 - cy(i), i - 1, mbar);
+        for (int i = 1; i < 9; ++i)
+            tma_load_3d(sm + S::H + (i - 1) * S::H_SLOT, tm_h, x0 - T::H_X0, y0 - cy(i), i - 1, mbar);
+    }
     if constexpr (S::kHalo) tma_load_3d(sm + S::HIST, tm_hist, x0 - 4, y0 - 1, 0, mbar);
     else tma_load_3d(sm + S::HIST, tm_hist, x0, y0, 0, mbar);
 }
@@ -464,7 +472,7 @@ __device__ __forceinline__ void issue_tile_loads(unsigned char* sm, const CUtens
 // 9-point stencils; the same boxes hold the own cell's unshifted post-collision values, whose sums
 // are phi and psi of the previous level (m*_0 = phi exactly, Sec. 3.1), so only u of the
 // previous level is stored.
-template <int ST, bool WALLS, bool LANGMUIR, int MODE>
+template <int ST, bool WALLS, bool LANGMUIR, int MODE, bool FLOW>
 __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsigned char* sm, float2* PP,
                                           unsigned long long* mbar, uint32_t parity, int x0, int y0) {
     using T = Traits<ST>;
@@ -476,7 +484,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     __syncthreads();
     bool abort = !mbar_wait_bounded(mbar, parity);
     if (x0 == 0 || x0 + TX + 8 > p.nx || y0 == 0 || y0 + TY + 2 > p.ny) {
-        if (!abort) patch_edges<ST, WALLS>(p, io, sm, x0, y0);
+        if (!abort) patch_edges<ST, WALLS, FLOW>(p, io, sm, x0, y0);
         abort = __syncthreads_or(abort);
     }
 
@@ -594,8 +602,8 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     const float2 uown = S::kHalo ? Hist[(ty + 1) * BW + tx + 4] : Hist[ty * TX + tx];
 
     // flow populations pulled from the staged boxes (16-bit: plus the source cell's 3 w rho c.u)
-    float h[9];
-    {
+    float h[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if constexpr (FLOW) {
         const bool bb_up = WALLS && y == 0;           // links 2, 5, 6 come from below the bottom wall
         const bool bb_dn = WALLS && y == p.ny - 1;    // links 4, 7, 8 come from above the top wall
         h[1] = load_h<ST, 1>(sm, Hist, p, tx, ty, false, uown);
@@ -608,12 +616,12 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         h[8] = load_h<ST, 8>(sm, Hist, p, tx, ty, bb_dn, uown);
     }
 
-    // velocity: rho u = sum c_i h_i + F/2 (Sec. 3.3)
+    // velocity: rho u = sum c_i h_i + F/2 (Sec. 3.3), or the imposed velocity (kept in the history)
     const float h13 = h[1] - h[3], h24 = h[2] - h[4], h57 = h[5] - h[7], h68 = h[6] - h[8];
     const float jx = h13 + (h57 - h68);
     const float jy = h24 + (h57 + h68);
-    const float ux = (jx + 0.5f * Fx) * p.inv_rho;
-    const float uy = (jy + 0.5f * Fy) * p.inv_rho;
+    const float ux = FLOW ? (jx + 0.5f * Fx) * p.inv_rho : uown.x;
+    const float uy = FLOW ? (jy + 0.5f * Fy) * p.inv_rho : uown.y;
 
     // previous level: (phi, psi) from the own cell's post-collision pairs, u from history
     float2 pprev = pp;
@@ -646,7 +654,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     // pressure (Eq. for P, Sec. 3.3) with K = w0/(c^2 - cs2) = 2/3:
     //   P = 3/5 [sum_{i>0} h_i - (2/3) rho |u|^2 + (1/3) d_t(rho |u|^2)]
     const float hsum = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
-    const float P_ = 0.6f * (hsum - (2.f / 3.f) * rho * (ux * ux + uy * uy) + (1.f / 3.f) * (dt_xx + dt_yy));
+    const float P_ = FLOW ? 0.6f * (hsum - (2.f / 3.f) * rho * (ux * ux + uy * uy) + (1.f / 3.f) * (dt_xx + dt_yy)) : 0.f;
 
     {
         // |u| >= 0.3, or a non-finite value (NaN fails every comparison; a NaN anywhere in the
@@ -690,82 +698,84 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
                 dfg[8 * p.plane] = enc_pair_rs<ST, 8>(q[8], key);
             }
         }
-        // ---- flow h (Sec. 3.3) ----
-        float s2, k2, s4, k4;
-        if (p.dmu == 0.f) {
-            s2 = p.s2h;
-            k2 = p.k2h;
-            s4 = p.s4h_eff;
-            k4 = p.k4h;
-        } else {
-            s2 = __frcp_rn(3.f * (p.muB + (phi - p.phiB) * p.inv_dphi * p.dmu) * p.inv_rho + 0.5f);
-            k2 = 1.f - 0.5f * s2;
-            s4 = p.tie_s4h ? s2 : p.s4h;
-            k4 = 1.f - 0.5f * s4;
-        }
-        const float s1 = p.s1h, s3 = p.s3h, k1 = p.k1h, k3 = p.k3h;
-        const float Jx = rho * ux, Jy = rho * uy;
-        // equilibrium moments: (., Jx, Jy, P + Jx ux, P + Jy uy, Jx uy, Jx/3, Jy/3, P/3 + J.u/3)
-        // source moments:      (., Fx, Fy, dt_xx, dt_yy, dt_xy, Fx/3, Fy/3, (dt_xx + dt_yy)/3)
-        const float ha = h[5] + h[7], hb = h[6] + h[8];
-        const float m5 = ha - hb, m8 = ha + hb, m6 = h57 - h68, m7 = h57 + h68;
-        const float m3 = (h[1] + h[3]) + m8, m4 = (h[2] + h[4]) + m8;
-        // increments dm_k = -s_k (m_k - m_eq_k) + (1 - s_k/2) m_src_k, then h* = h + M^-1 dm
-        const float d1 = k1 * Fx - s1 * (jx - Jx);
-        const float d2 = k1 * Fy - s1 * (jy - Jy);
-        const float d3 = k2 * dt_xx - s2 * (m3 - (P_ + Jx * ux));
-        const float d4 = k2 * dt_yy - s2 * (m4 - (P_ + Jy * uy));
-        const float d5 = k2 * dt_xy - s2 * (m5 - Jx * uy);
-        const float d6 = (1.f / 3.f) * (k3 * Fx - s3 * (3.f * m6 - Jx));
-        const float d7 = (1.f / 3.f) * (k3 * Fy - s3 * (3.f * m7 - Jy));
-        const float d8 = (1.f / 3.f) * (k4 * (dt_xx + dt_yy) - s4 * (3.f * m8 - (P_ + Jx * ux + Jy * uy)));
-        const float A = d1 - d6, B = d3 - d8, C = d2 - d7, D = d4 - d8;
-        const float E = d8 + d5, F = d8 - d5, G = d6 + d7, H = d7 - d6;
-        h[1] += 0.5f * (A + B);
-        h[3] += 0.5f * (B - A);
-        h[2] += 0.5f * (C + D);
-        h[4] += 0.5f * (D - C);
-        h[5] += 0.25f * (E + G);
-        h[7] += 0.25f * (E - G);
-        h[6] += 0.25f * (F + H);
-        h[8] += 0.25f * (F - H);
-        if (WALLS) {
-            // moving-wall term for the links that leave through a wall, folded in before storing:
-            // h_ibar(x_b, t+1) = h*_i(x_b, t) - 2 w_i rho c_i.u_w / cs2
-            if (y == 0) {
-                h[7] -= 6.f * wgt(7) * rho * (-1.f) * p.u_bot;
-                h[8] -= 6.f * wgt(8) * rho * (1.f) * p.u_bot;
+        // ---- flow h (Sec. 3.3); none when the velocity is prescribed ----
+        if constexpr (FLOW) {
+            float s2, k2, s4, k4;
+            if (p.dmu == 0.f) {
+                s2 = p.s2h;
+                k2 = p.k2h;
+                s4 = p.s4h_eff;
+                k4 = p.k4h;
+            } else {
+                s2 = __frcp_rn(3.f * (p.muB + (phi - p.phiB) * p.inv_dphi * p.dmu) * p.inv_rho + 0.5f);
+                k2 = 1.f - 0.5f * s2;
+                s4 = p.tie_s4h ? s2 : p.s4h;
+                k4 = 1.f - 0.5f * s4;
             }
-            if (y == p.ny - 1) {
-                h[5] -= 6.f * wgt(5) * rho * (1.f) * p.u_top;
-                h[6] -= 6.f * wgt(6) * rho * (-1.f) * p.u_top;
+            const float s1 = p.s1h, s3 = p.s3h, k1 = p.k1h, k3 = p.k3h;
+            const float Jx = rho * ux, Jy = rho * uy;
+            // equilibrium moments: (., Jx, Jy, P + Jx ux, P + Jy uy, Jx uy, Jx/3, Jy/3, P/3 + J.u/3)
+            // source moments:      (., Fx, Fy, dt_xx, dt_yy, dt_xy, Fx/3, Fy/3, (dt_xx + dt_yy)/3)
+            const float ha = h[5] + h[7], hb = h[6] + h[8];
+            const float m5 = ha - hb, m8 = ha + hb, m6 = h57 - h68, m7 = h57 + h68;
+            const float m3 = (h[1] + h[3]) + m8, m4 = (h[2] + h[4]) + m8;
+            // increments dm_k = -s_k (m_k - m_eq_k) + (1 - s_k/2) m_src_k, then h* = h + M^-1 dm
+            const float d1 = k1 * Fx - s1 * (jx - Jx);
+            const float d2 = k1 * Fy - s1 * (jy - Jy);
+            const float d3 = k2 * dt_xx - s2 * (m3 - (P_ + Jx * ux));
+            const float d4 = k2 * dt_yy - s2 * (m4 - (P_ + Jy * uy));
+            const float d5 = k2 * dt_xy - s2 * (m5 - Jx * uy);
+            const float d6 = (1.f / 3.f) * (k3 * Fx - s3 * (3.f * m6 - Jx));
+            const float d7 = (1.f / 3.f) * (k3 * Fy - s3 * (3.f * m7 - Jy));
+            const float d8 = (1.f / 3.f) * (k4 * (dt_xx + dt_yy) - s4 * (3.f * m8 - (P_ + Jx * ux + Jy * uy)));
+            const float A = d1 - d6, B = d3 - d8, C = d2 - d7, D = d4 - d8;
+            const float E = d8 + d5, F = d8 - d5, G = d6 + d7, H = d7 - d6;
+            h[1] += 0.5f * (A + B);
+            h[3] += 0.5f * (B - A);
+            h[2] += 0.5f * (C + D);
+            h[4] += 0.5f * (D - C);
+            h[5] += 0.25f * (E + G);
+            h[7] += 0.25f * (E - G);
+            h[6] += 0.25f * (F + H);
+            h[8] += 0.25f * (F - H);
+            if (WALLS) {
+                // moving-wall term for the links that leave through a wall, folded in before storing:
+                // h_ibar(x_b, t+1) = h*_i(x_b, t) - 2 w_i rho c_i.u_w / cs2
+                if (y == 0) {
+                    h[7] -= 6.f * wgt(7) * rho * (-1.f) * p.u_bot;
+                    h[8] -= 6.f * wgt(8) * rho * (1.f) * p.u_bot;
+                }
+                if (y == p.ny - 1) {
+                    h[5] -= 6.f * wgt(5) * rho * (1.f) * p.u_top;
+                    h[6] -= 6.f * wgt(6) * rho * (-1.f) * p.u_top;
+                }
             }
-        }
-        using Hv = typename T::H;
-        Hv* __restrict__ dh = reinterpret_cast<Hv*>(static_cast<P*>(io.dst) + (size_t)kPairs * p.plane) + cell;
-        if constexpr (!T::kH16) {
-#pragma unroll
-            for (int i = 1; i < 9; ++i) dh[(size_t)(i - 1) * p.plane] = h[i];
-        } else {
-            // every slot is stored relative to this cell's new u (what the next step reads back):
-            // raw = (h_i / w_i - 3 rho c_i.u) S_h, two links per stochastic conversion
-            const float vx = p.kh3 * T::SH * ux, vy = p.kh3 * T::SH * uy;
-            constexpr float e1 = T::SH / wgt(1), e5 = T::SH / wgt(5);
-            const uint32_t b12 = cvt_rs2<typename T::P>(fmaf(h[1], e1, -vx), fmaf(h[2], e1, -vy), rbits_of(key, 9));
-            const uint32_t b34 = cvt_rs2<typename T::P>(fmaf(h[3], e1, vx), fmaf(h[4], e1, vy), rbits_of(key, 10));
-            const uint32_t b56 =
-                cvt_rs2<typename T::P>(fmaf(h[5], e5, -(vx + vy)), fmaf(h[6], e5, vx - vy), rbits_of(key, 11));
-            const uint32_t b78 =
-                cvt_rs2<typename T::P>(fmaf(h[7], e5, vx + vy), fmaf(h[8], e5, vy - vx), rbits_of(key, 12));
-            unsigned short* dh16 = reinterpret_cast<unsigned short*>(dh);
-            dh16[0 * p.plane] = (unsigned short)(b12 & 0xFFFFu);
-            dh16[1 * p.plane] = (unsigned short)(b12 >> 16);
-            dh16[2 * p.plane] = (unsigned short)(b34 & 0xFFFFu);
-            dh16[3 * p.plane] = (unsigned short)(b34 >> 16);
-            dh16[4 * p.plane] = (unsigned short)(b56 & 0xFFFFu);
-            dh16[5 * p.plane] = (unsigned short)(b56 >> 16);
-            dh16[6 * p.plane] = (unsigned short)(b78 & 0xFFFFu);
-            dh16[7 * p.plane] = (unsigned short)(b78 >> 16);
+            using Hv = typename T::H;
+            Hv* __restrict__ dh = reinterpret_cast<Hv*>(static_cast<P*>(io.dst) + (size_t)kPairs * p.plane) + cell;
+            if constexpr (!T::kH16) {
+    #pragma unroll
+                for (int i = 1; i < 9; ++i) dh[(size_t)(i - 1) * p.plane] = h[i];
+            } else {
+                // every slot is stored relative to this cell's new u (what the next step reads back):
+                // raw = (h_i / w_i - 3 rho c_i.u) S_h, two links per stochastic conversion
+                const float vx = p.kh3 * T::SH * ux, vy = p.kh3 * T::SH * uy;
+                constexpr float e1 = T::SH / wgt(1), e5 = T::SH / wgt(5);
+                const uint32_t b12 = cvt_rs2<typename T::P>(fmaf(h[1], e1, -vx), fmaf(h[2], e1, -vy), rbits_of(key, 9));
+                const uint32_t b34 = cvt_rs2<typename T::P>(fmaf(h[3], e1, vx), fmaf(h[4], e1, vy), rbits_of(key, 10));
+                const uint32_t b56 =
+                    cvt_rs2<typename T::P>(fmaf(h[5], e5, -(vx + vy)), fmaf(h[6], e5, vx - vy), rbits_of(key, 11));
+                const uint32_t b78 =
+                    cvt_rs2<typename T::P>(fmaf(h[7], e5, vx + vy), fmaf(h[8], e5, vy - vx), rbits_of(key, 12));
+                unsigned short* dh16 = reinterpret_cast<unsigned short*>(dh);
+                dh16[0 * p.plane] = (unsigned short)(b12 & 0xFFFFu);
+                dh16[1 * p.plane] = (unsigned short)(b12 >> 16);
+                dh16[2 * p.plane] = (unsigned short)(b34 & 0xFFFFu);
+                dh16[3 * p.plane] = (unsigned short)(b34 >> 16);
+                dh16[4 * p.plane] = (unsigned short)(b56 & 0xFFFFu);
+                dh16[5 * p.plane] = (unsigned short)(b56 >> 16);
+                dh16[6 * p.plane] = (unsigned short)(b78 & 0xFFFFu);
+                dh16[7 * p.plane] = (unsigned short)(b78 >> 16);
+            }
         }
         io.hist_dst[cell] = make_float2(ux, uy);
     }
@@ -773,7 +783,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
 }
 
 // One step (or the moments) of one lattice: one TX x TY tile per CTA.
-template <int ST, bool WALLS, bool LANGMUIR, int MODE>
+template <int ST, bool WALLS, bool LANGMUIR, int MODE, bool FLOW>
 __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ StepArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + Smem<ST>::BAR);
@@ -790,8 +800,9 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
     // grid frees, and wait here until the previous step's writes are complete and visible.
     cudaTriggerProgrammaticLaunchCompletion();
     cudaGridDependencySynchronize();
-    if (threadIdx.x == 0) issue_tile_loads<ST>(sm, &a.tm_fg, &a.tm_h, &a.tm_hist, x0, y0, mbar);
-    step_tile<ST, WALLS, LANGMUIR, MODE>(a.p, a.io, sm, reinterpret_cast<float2*>(sm + Smem<ST>::PP), mbar, 0, x0, y0);
+    if (threadIdx.x == 0) issue_tile_loads<ST, FLOW>(sm, &a.tm_fg, &a.tm_h, &a.tm_hist, x0, y0, mbar);
+    step_tile<ST, WALLS, LANGMUIR, MODE, FLOW>(a.p, a.io, sm, reinterpret_cast<float2*>(sm + Smem<ST>::PP), mbar, 0, x0,
+                                               y0);
 }
 
 // Tile k of a grid of ntx x nty tiles: rows in the order first, last, then the interior (the two
@@ -808,7 +819,7 @@ __device__ __forceinline__ void tile_origin(int k, int ntx, int nty, int& x0, in
 // current one, so the copy latency hides behind the arithmetic.  Claiming tiles one at a time
 // balances the longer edge tiles across the CTAs.  Thread 0 claims a tile one iteration before
 // it needs it, so the atomic's latency also hides behind a tile's work.
-template <int ST, bool WALLS, bool LANGMUIR>
+template <int ST, bool WALLS, bool LANGMUIR, bool FLOW>
 __global__ void __launch_bounds__(NT, 4) step_kernel_pipe(const __grid_constant__ StepArgs a, int ntx, int nty) {
     using S = Smem<ST>;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -831,7 +842,7 @@ __global__ void __launch_bounds__(NT, 4) step_kernel_pipe(const __grid_constant_
         if (k0 < ntiles) {
             int x0, y0;
             tile_origin((int)k0, ntx, nty, x0, y0);
-            issue_tile_loads<ST>(sm, &a.tm_fg, &a.tm_h, &a.tm_hist, x0, y0, &bars[0]);
+            issue_tile_loads<ST, FLOW>(sm, &a.tm_fg, &a.tm_h, &a.tm_hist, x0, y0, &bars[0]);
             ahead = atomicAdd(a.tile_ctr, 1u);
         } else {
             ahead = ntiles;
@@ -848,14 +859,14 @@ __global__ void __launch_bounds__(NT, 4) step_kernel_pipe(const __grid_constant_
             if (ahead < ntiles) {
                 int xn, yn;
                 tile_origin((int)ahead, ntx, nty, xn, yn);
-                issue_tile_loads<ST>(sm + nxt * S::STAGE, &a.tm_fg, &a.tm_h, &a.tm_hist, xn, yn, &bars[nxt]);
+                issue_tile_loads<ST, FLOW>(sm + nxt * S::STAGE, &a.tm_fg, &a.tm_h, &a.tm_hist, xn, yn, &bars[nxt]);
                 ahead = atomicAdd(a.tile_ctr, 1u);
             }
         }
         int x0, y0;
         tile_origin((int)k, ntx, nty, x0, y0);
-        if (step_tile<ST, WALLS, LANGMUIR, kStep>(a.p, a.io, sm + cur * S::STAGE, PP, &bars[cur], (it >> 1) & 1, x0,
-                                                  y0)) {
+        if (step_tile<ST, WALLS, LANGMUIR, kStep, FLOW>(a.p, a.io, sm + cur * S::STAGE, PP, &bars[cur], (it >> 1) & 1,
+                                                        x0, y0)) {
             // a copy timed out: stop this CTA, after waiting (bounded) for the copy in flight
             if (threadIdx.x == 0 && slot[nxt] < ntiles) mbar_wait_bounded(&bars[nxt], ((it + 1) >> 1) & 1);
             break;
@@ -890,7 +901,7 @@ struct BatchArgs {
     int s;
 };
 
-template <int ST, bool WALLS, bool LANGMUIR>
+template <int ST, bool WALLS, bool LANGMUIR, bool FLOW>
 __global__ void __launch_bounds__(NT, 4) batch_step_kernel(const __grid_constant__ BatchArgs b) {
     using S = Smem<ST>;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -909,7 +920,7 @@ __global__ void __launch_bounds__(NT, 4) batch_step_kernel(const __grid_constant
     if (threadIdx.x == 0) {
         mbar_init(mbar, 1);
         fence_mbar_init();
-        issue_tile_loads<ST>(sm, &d.tm_fg[cur], &d.tm_h[cur], &d.tm_hist[cur], x0, y0, mbar);
+        issue_tile_loads<ST, FLOW>(sm, &d.tm_fg[cur], &d.tm_h[cur], &d.tm_hist[cur], x0, y0, mbar);
     }
     TileIO io;
     io.src = d.pops[cur];
@@ -920,7 +931,7 @@ __global__ void __launch_bounds__(NT, 4) batch_step_kernel(const __grid_constant
     io.out[0] = io.out[1] = io.out[2] = io.out[3] = io.out[4] = nullptr;
     io.seed = step_seed(d.steps + b.s);
     io.first = d.first && b.s == 0;
-    step_tile<ST, WALLS, LANGMUIR, kStep>(*sp, io, sm, reinterpret_cast<float2*>(sm + S::PP), mbar, 0, x0, y0);
+    step_tile<ST, WALLS, LANGMUIR, kStep, FLOW>(*sp, io, sm, reinterpret_cast<float2*>(sm + S::PP), mbar, 0, x0, y0);
 }
 
 // After a sequence of n launches: advance every descriptor by n steps.
@@ -945,6 +956,7 @@ struct InitArgs {
     unsigned* __restrict__ status;
     int langmuir;
     int walls;
+    int flow;                     // 0: prescribed velocity, no h populations
 };
 
 template <int ST>
@@ -989,7 +1001,7 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
         else
             fg[(size_t)slot * p.plane + cell] = pack2<P>(
                 make_float2((float)((feq / w - p.phi_ref) * T::SF), (float)(geq / w * T::SG)));
-        if (slot == 0) continue;
+        if (slot == 0 || !a.flow) continue;
         if constexpr (!T::kH16) {
             hp[(size_t)(slot - 1) * p.plane + cell] = (Hv)heq;
         } else {

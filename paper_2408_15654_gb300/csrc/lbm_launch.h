@@ -1,6 +1,8 @@
-// Launch helpers of the step kernel, one translation unit per storage mode
+// Launch helpers of the step kernels, one translation unit per storage mode
 // (step_fp32.cu, step_fp16.cu, step_bf16.cu, step_fp16fg.cu, step_bf16fg.cu) so that the
-// instances compile in parallel.
+// instances compile in parallel.  Each storage mode has six kernel variants: walls or periodic y,
+// Langmuir or linear EOS with the flow solved, and walls or periodic y with the velocity
+// prescribed (no flow populations; the EOS is not used there).
 #pragma once
 #include <cstring>
 
@@ -8,148 +10,147 @@
 
 namespace lbm {
 
-// Every step launch uses programmatic dependent launch: the kernel waits (griddepcontrol.wait)
-// for the previous grid before touching memory, so the next launch may be scheduled during the
-// tail of this one.
-// grid = (tiles along x, tiles along y).  A step (mode kStep) with pipe_ctas > 0 runs the
-// persistent pipelined kernel on pipe_ctas CTAs instead of one CTA per tile.
-template <int ST>
-cudaError_t launch_step_impl(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, int pipe_ctas,
-                             cudaStream_t stream) {
+// Runtime flags of a launch, mapped to the kernel variant.
+struct Variant {
+    bool walls, langmuir, flow;
+};
+
+// Calls f.template operator()<WALLS, LANGMUIR, FLOW>() for the variant's template arguments.
+template <typename F>
+cudaError_t dispatch_variant(const Variant& v, F&& f) {
+    if (v.flow) {
+        if (v.walls && v.langmuir) return f.template operator()<true, true, true>();
+        if (v.walls) return f.template operator()<true, false, true>();
+        if (v.langmuir) return f.template operator()<false, true, true>();
+        return f.template operator()<false, false, true>();
+    }
+    if (v.walls) return f.template operator()<true, false, false>();
+    return f.template operator()<false, false, false>();
+}
+
+inline cudaLaunchConfig_t pdl_config(dim3 grid, size_t smem, cudaStream_t stream, cudaLaunchAttribute* attr) {
+    // Every launch uses programmatic dependent launch: the kernel waits (griddepcontrol.wait) for
+    // the previous grid before touching memory, so the next launch may be scheduled during the
+    // tail of this one.
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = grid;
     cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = Smem<ST>::BYTES;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    return cfg;
+}
+
+// grid = (tiles along x, tiles along y).  A step (mode kStep) with pipe_ctas > 0 runs the
+// persistent pipelined kernel on pipe_ctas CTAs instead of one CTA per tile.
+template <int ST>
+cudaError_t launch_step_impl(const StepArgs& a, int mode, const Variant& v, dim3 grid, int pipe_ctas,
+                             cudaStream_t stream) {
+    cudaLaunchAttribute attr[1];
     if (mode == kStep && pipe_ctas > 0) {
         const int ntx = (int)grid.x, nty = (int)grid.y;
-        cfg.gridDim = dim3((unsigned)pipe_ctas);
-        cfg.dynamicSmemBytes = Smem<ST>::BYTES_PIPE;
-        if (walls && langmuir) return cudaLaunchKernelEx(&cfg, step_kernel_pipe<ST, true, true>, a, ntx, nty);
-        if (walls) return cudaLaunchKernelEx(&cfg, step_kernel_pipe<ST, true, false>, a, ntx, nty);
-        if (langmuir) return cudaLaunchKernelEx(&cfg, step_kernel_pipe<ST, false, true>, a, ntx, nty);
-        return cudaLaunchKernelEx(&cfg, step_kernel_pipe<ST, false, false>, a, ntx, nty);
+        cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)pipe_ctas), Smem<ST>::BYTES_PIPE, stream, attr);
+        return dispatch_variant(v, [&]<bool W, bool L, bool F>() {
+            return cudaLaunchKernelEx(&cfg, step_kernel_pipe<ST, W, L, F>, a, ntx, nty);
+        });
     }
-#define LBM_LAUNCH_CASE(W_, L_)                                                              \
-    do {                                                                                     \
-        if (mode == kStep) return cudaLaunchKernelEx(&cfg, step_kernel<ST, W_, L_, kStep>, a);      \
-        return cudaLaunchKernelEx(&cfg, step_kernel<ST, W_, L_, kMoments>, a);               \
-    } while (0)
-    if (walls && langmuir) LBM_LAUNCH_CASE(true, true);
-    if (walls) LBM_LAUNCH_CASE(true, false);
-    if (langmuir) LBM_LAUNCH_CASE(false, true);
-    LBM_LAUNCH_CASE(false, false);
-#undef LBM_LAUNCH_CASE
+    cudaLaunchConfig_t cfg = pdl_config(grid, Smem<ST>::BYTES, stream, attr);
+    return dispatch_variant(v, [&]<bool W, bool L, bool F>() {
+        if (mode == kStep) return cudaLaunchKernelEx(&cfg, step_kernel<ST, W, L, kStep, F>, a);
+        return cudaLaunchKernelEx(&cfg, step_kernel<ST, W, L, kMoments, F>, a);
+    });
 }
 
-template <int ST, bool W_, bool L_, int M_>
-cudaError_t prepare_one(int* bps) {
-    auto k = step_kernel<ST, W_, L_, M_>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, NT, Smem<ST>::BYTES);
-}
-
-template <int ST, bool W_, bool L_>
-cudaError_t prepare_pipe_one(int* bps) {
-    auto k = step_kernel_pipe<ST, W_, L_>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES_PIPE);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, NT, Smem<ST>::BYTES_PIPE);
-}
-
-// Opt the instances of storage mode ST into their dynamic shared memory; resident CTAs per SM of
-// the one-tile kernels and of the pipelined kernels (the minimum over the instances).
+// Opt every variant of storage mode ST into its dynamic shared memory; resident CTAs per SM of the
+// one-tile and of the pipelined kernels (the minimum over the variants).
 template <int ST>
 cudaError_t prepare_step_impl(int* blocks_per_sm, int* pipe_blocks_per_sm) {
-    int b[8] = {0};
-    cudaError_t e = prepare_one<ST, false, false, kStep>(&b[0]);
-    if (e == cudaSuccess) e = prepare_one<ST, false, true, kStep>(&b[1]);
-    if (e == cudaSuccess) e = prepare_one<ST, true, false, kStep>(&b[2]);
-    if (e == cudaSuccess) e = prepare_one<ST, true, true, kStep>(&b[3]);
-    if (e == cudaSuccess) e = prepare_one<ST, false, false, kMoments>(&b[4]);
-    if (e == cudaSuccess) e = prepare_one<ST, false, true, kMoments>(&b[5]);
-    if (e == cudaSuccess) e = prepare_one<ST, true, false, kMoments>(&b[6]);
-    if (e == cudaSuccess) e = prepare_one<ST, true, true, kMoments>(&b[7]);
-    int m = b[0];
-    for (int k = 1; k < 8; ++k) m = b[k] < m ? b[k] : m;
-    *blocks_per_sm = m;
-    int q[4] = {0, 0, 0, 0};
-    if (e == cudaSuccess) e = prepare_pipe_one<ST, false, false>(&q[0]);
-    if (e == cudaSuccess) e = prepare_pipe_one<ST, false, true>(&q[1]);
-    if (e == cudaSuccess) e = prepare_pipe_one<ST, true, false>(&q[2]);
-    if (e == cudaSuccess) e = prepare_pipe_one<ST, true, true>(&q[3]);
-    m = q[0];
-    for (int k = 1; k < 4; ++k) m = q[k] < m ? q[k] : m;
-    *pipe_blocks_per_sm = m;
+    int tile = 1 << 30, pipe = 1 << 30;
+    auto one = [&]<bool W, bool L, bool F>() -> cudaError_t {
+        int b = 0;
+        auto k0 = step_kernel<ST, W, L, kStep, F>;
+        auto k1 = step_kernel<ST, W, L, kMoments, F>;
+        auto kp = step_kernel_pipe<ST, W, L, F>;
+        cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES_PIPE);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k0, NT, Smem<ST>::BYTES);
+        tile = b < tile ? b : tile;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1, NT, Smem<ST>::BYTES);
+        tile = b < tile ? b : tile;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kp, NT, Smem<ST>::BYTES_PIPE);
+        pipe = b < pipe ? b : pipe;
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+        const Variant v{k == 0 || k == 1 || k == 4, k == 0 || k == 2, k < 4};
+        e = dispatch_variant(v, one);
+    }
+    *blocks_per_sm = tile;
+    *pipe_blocks_per_sm = pipe;
     return e;
 }
 
-// One launch of the many-lattice kernel over `ntiles` tiles (all lattices of one storage mode,
-// boundary kind and EOS).
+// One launch of the many-lattice kernel over `ntiles` tiles (all lattices of one variant).
 template <int ST>
-cudaError_t launch_batch_impl(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t stream) {
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3(ntiles);
-    cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = Smem<ST>::BYTES_BATCH;
-    cfg.stream = stream;
+cudaError_t launch_batch_impl(const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t stream) {
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (walls && langmuir) return cudaLaunchKernelEx(&cfg, batch_step_kernel<ST, true, true>, b);
-    if (walls) return cudaLaunchKernelEx(&cfg, batch_step_kernel<ST, true, false>, b);
-    if (langmuir) return cudaLaunchKernelEx(&cfg, batch_step_kernel<ST, false, true>, b);
-    return cudaLaunchKernelEx(&cfg, batch_step_kernel<ST, false, false>, b);
-}
-
-template <int ST, bool W_, bool L_>
-cudaError_t prepare_batch_one() {
-    return cudaFuncSetAttribute(batch_step_kernel<ST, W_, L_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Smem<ST>::BYTES_BATCH);
+    cudaLaunchConfig_t cfg = pdl_config(dim3(ntiles), Smem<ST>::BYTES_BATCH, stream, attr);
+    return dispatch_variant(v, [&]<bool W, bool L, bool F>() {
+        return cudaLaunchKernelEx(&cfg, batch_step_kernel<ST, W, L, F>, b);
+    });
 }
 
 template <int ST>
 cudaError_t prepare_batch_impl() {
-    cudaError_t e = prepare_batch_one<ST, false, false>();
-    if (e == cudaSuccess) e = prepare_batch_one<ST, false, true>();
-    if (e == cudaSuccess) e = prepare_batch_one<ST, true, false>();
-    if (e == cudaSuccess) e = prepare_batch_one<ST, true, true>();
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+        const Variant v{k == 0 || k == 1 || k == 4, k == 0 || k == 2, k < 4};
+        e = dispatch_variant(v, [&]<bool W, bool L, bool F>() {
+            return cudaFuncSetAttribute(batch_step_kernel<ST, W, L, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        Smem<ST>::BYTES_BATCH);
+        });
+    }
     return e;
 }
 
 // Entry points of the per-storage translation units; st is the storage mode.
-cudaError_t launch_batch(int st, const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s);
+cudaError_t launch_step(int st, const StepArgs& a, int mode, const Variant& v, dim3 grid, int pipe, cudaStream_t s);
+cudaError_t prepare_step(int st, int* blocks_per_sm, int* pipe_blocks_per_sm);
+cudaError_t launch_batch(int st, const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t s);
 cudaError_t prepare_batch(int st);
 
-cudaError_t launch_step_fp32(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, int pipe, cudaStream_t s);
-cudaError_t launch_step_fp16(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, int pipe, cudaStream_t s);
-cudaError_t launch_step_bf16(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, int pipe, cudaStream_t s);
-cudaError_t launch_step_fp16fg(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, int pipe, cudaStream_t s);
-cudaError_t launch_step_bf16fg(const StepArgs& a, int mode, bool walls, bool langmuir, dim3 grid, int pipe, cudaStream_t s);
-cudaError_t prepare_step_fp32(int* blocks_per_sm, int* pipe_blocks_per_sm);
-cudaError_t prepare_step_fp16(int* blocks_per_sm, int* pipe_blocks_per_sm);
-cudaError_t prepare_step_bf16(int* blocks_per_sm, int* pipe_blocks_per_sm);
-cudaError_t prepare_step_fp16fg(int* blocks_per_sm, int* pipe_blocks_per_sm);
-cudaError_t prepare_step_bf16fg(int* blocks_per_sm, int* pipe_blocks_per_sm);
-cudaError_t launch_batch_fp32(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s);
-cudaError_t launch_batch_fp16(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s);
-cudaError_t launch_batch_bf16(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s);
-cudaError_t launch_batch_fp16fg(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s);
-cudaError_t launch_batch_bf16fg(const BatchArgs& b, bool walls, bool langmuir, unsigned ntiles, cudaStream_t s);
-cudaError_t prepare_batch_fp32();
-cudaError_t prepare_batch_fp16();
-cudaError_t prepare_batch_bf16();
-cudaError_t prepare_batch_fp16fg();
-cudaError_t prepare_batch_bf16fg();
+#define LBM_DECLARE_STORAGE(name)                                                                                  \
+    cudaError_t launch_step_##name(const StepArgs& a, int mode, const Variant& v, dim3 grid, int pipe,              \
+                                   cudaStream_t s);                                                                \
+    cudaError_t prepare_step_##name(int* blocks_per_sm, int* pipe_blocks_per_sm);                                   \
+    cudaError_t launch_batch_##name(const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t s);         \
+    cudaError_t prepare_batch_##name();
+LBM_DECLARE_STORAGE(fp32)
+LBM_DECLARE_STORAGE(fp16)
+LBM_DECLARE_STORAGE(bf16)
+LBM_DECLARE_STORAGE(fp16fg)
+LBM_DECLARE_STORAGE(bf16fg)
+#undef LBM_DECLARE_STORAGE
+
+// Body of a per-storage translation unit.
+#define LBM_DEFINE_STORAGE(name, ST)                                                                               \
+    cudaError_t launch_step_##name(const StepArgs& a, int mode, const Variant& v, dim3 grid, int pipe,              \
+                                   cudaStream_t s) {                                                               \
+        return launch_step_impl<ST>(a, mode, v, grid, pipe, s);                                                   \
+    }                                                                                                              \
+    cudaError_t prepare_step_##name(int* blocks_per_sm, int* pipe_blocks_per_sm) {                                  \
+        return prepare_step_impl<ST>(blocks_per_sm, pipe_blocks_per_sm);                                          \
+    }                                                                                                              \
+    cudaError_t launch_batch_##name(const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t s) {        \
+        return launch_batch_impl<ST>(b, v, ntiles, s);                                                            \
+    }                                                                                                              \
+    cudaError_t prepare_batch_##name() { return prepare_batch_impl<ST>(); }
 
 }  // namespace lbm

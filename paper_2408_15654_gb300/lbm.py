@@ -20,6 +20,7 @@ LBM_STORE_FP32, LBM_STORE_FP16, LBM_STORE_BF16, LBM_STORE_FP16_FG, LBM_STORE_BF1
 STORAGE = {"fp32": LBM_STORE_FP32, "fp16": LBM_STORE_FP16, "bf16": LBM_STORE_BF16,
            "fp16_fg": LBM_STORE_FP16_FG, "bf16_fg": LBM_STORE_BF16_FG}
 LBM_MEM_HOST, LBM_MEM_DEVICE = 0, 1
+LBM_VELOCITY_SOLVED, LBM_VELOCITY_PRESCRIBED = 0, 1
 LBM_PHI, LBM_PSI, LBM_UX, LBM_UY, LBM_P = 1, 2, 4, 8, 16
 LBM_SUM_PHI, LBM_SUM_PSI = 0, 1
 LBM_NOALLOC_MAX_ROWS = 8192
@@ -44,7 +45,7 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_init_fields", "lbm_step", "
 class lbm_params(C.Structure):
     _fields_ = [
         ("nx", C.c_int32), ("ny", C.c_int32), ("bc_y", C.c_int32), ("eos", C.c_int32),
-        ("storage", C.c_int32), ("reserved", C.c_int32),
+        ("storage", C.c_int32), ("velocity", C.c_int32),
         ("u_top", C.c_double), ("u_bot", C.c_double),
         ("phiA", C.c_double), ("phiB", C.c_double), ("rhoA", C.c_double), ("rhoB", C.c_double),
         ("muA", C.c_double), ("muB", C.c_double), ("W", C.c_double), ("M_phi", C.c_double),
@@ -147,7 +148,7 @@ def make_params(p: dict) -> lbm_params:
     q.eos = LBM_EOS_LANGMUIR if p.get("eos", "linear") == "langmuir" else LBM_EOS_LINEAR
     st = p.get("storage", LBM_STORE_FP32)
     q.storage = STORAGE[st] if isinstance(st, str) else int(st)
-    q.reserved = 0
+    q.velocity = LBM_VELOCITY_PRESCRIBED if p.get("velocity", "solved") == "prescribed" else LBM_VELOCITY_SOLVED
     for k in ("u_top", "u_bot", "phiA", "phiB", "rhoA", "rhoB", "muA", "muB", "W", "M_phi", "D",
               "sigma0", "E0", "gx", "gy", "n_eps"):
         setattr(q, k, float(p[k]))

@@ -67,9 +67,17 @@ def test_workspace_bytes_without_gpu():
     assert nfg < 2 * 68 * 256 * pitch + 2 * 256 * pitch * 8 + 64 * 1024
 
 
+def test_prescribed_velocity_workspace_has_no_flow_planes():
+    p, _ = W.convected_drop(512, 256)
+    full = lbm.lbm_workspace_bytes(lbm.make_params(dict(p, velocity="solved")))
+    pres = lbm.lbm_workspace_bytes(lbm.make_params(p))
+    assert full - pres == 2 * 8 * 4 * 256 * 512
+
+
 @pytest.mark.parametrize("bad", [dict(nx=1), dict(ny=0), dict(rhoA=2.0), dict(W=0.0), dict(M_phi=-1.0),
                                  dict(D=0.0), dict(muA=0.0), dict(s_f=(1, 1, 2.5, 1, 1)),
-                                 dict(sigma0=float("nan")), dict(storage=7)])
+                                 dict(sigma0=float("nan")), dict(storage=7),
+                                 dict(velocity="sideways")])
 def test_parameter_validation(bad):
     p, _ = W.stationary_drop(32, 32, R=8)
     p.update(bad)
