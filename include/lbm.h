@@ -106,13 +106,15 @@ typedef struct lbm_handle lbm_handle;
 /* Bytes of device workspace lbm_create needs for these parameters: two population buffers, two
  * velocity-history buffers, a status word and the reduction partials.  Returns LBM_EINVAL for bad
  * parameters.
- * Layout: the workspace starts with the two population buffers, each B * ny * pitch bytes rounded
- * up to a multiple of 256, with pitch = nx rounded up to a multiple of 32 and B = 104 (FP32
- * storage), 52 (FP16, BF16) or 68 (FP16_FG, BF16_FG); with LBM_VELOCITY_PRESCRIBED, 72 (FP32)
- * or 36 (16-bit).  A buffer holds 9 planes of (f_i, g_i) pairs followed by 8 planes h_1..h_8
- * (h_0 never influences the step; no h planes with a prescribed velocity), each plane ny rows of
- * pitch cells; after lbm_init_fields and k steps the current state is buffer k mod 2 (buffer 0
- * at offset 0).
+ * Layout: the workspace starts with the two population buffers, each B * (ny + 4) * pitch bytes
+ * rounded up to a multiple of 256, with pitch = nx + 10 rounded up to a multiple of 32 and
+ * B = 104 (FP32 storage), 52 (FP16, BF16) or 68 (FP16_FG, BF16_FG); with
+ * LBM_VELOCITY_PRESCRIBED, 72 (FP32) or 36 (16-bit).  A buffer holds 9 planes of (f_i, g_i)
+ * pairs followed by 8 planes h_1..h_8 (h_0 never influences the step; no h planes with a
+ * prescribed velocity), each plane ny + 4 rows of pitch cells: cell (x, y) is at row y + 2,
+ * column x + 8, inside a ghost frame of copies (periodic images; bounce-back values in the rows
+ * next to walls) that the library maintains.  After lbm_init_fields and k steps the current
+ * state is buffer k mod 2 (buffer 0 at offset 0).
  * FP32 storage holds the values.  16-bit storage (FP16 / BF16, arithmetic still FP32) holds
  * each value divided by its lattice weight w_i, as a scaled deviation from a reference (the
  * _FG modes store only f and g this way and h as FP32 values):
@@ -123,8 +125,8 @@ typedef struct lbm_handle lbm_handle;
  * part of h (about 1e-5) above the 16-bit rounding of the velocity part (about 1e-3).  Steps
  * store 16-bit values with stochastic rounding, its random bits a hash of the cell index and
  * the step count (so a run is deterministic and a restored state continues bit for bit).  The
- * velocity history (two buffers of ny x pitch float pairs, alternating like the populations)
- * follows the population buffers. */
+ * velocity history (two buffers of (ny + 4) x pitch float pairs in the same frame, alternating
+ * like the populations) follows the population buffers. */
 int lbm_workspace_bytes(const lbm_params* p, size_t* bytes);
 
 /* Create a handle on the current CUDA device.
@@ -173,7 +175,8 @@ int lbm_reduce(lbm_handle* h, int what, double* out);
  * already in device memory.  This call sums phi (LBM_SUM_PHI) or psi (LBM_SUM_PSI) of that buffer
  * in FP64 exactly like lbm_reduce, with its partial sums in a fixed device array compiled into the
  * library instead of a workspace.
- *   d_pops: device pointer to one FP32-storage population buffer of an nx x ny grid (read only).
+ *   d_pops: device pointer to one FP32-storage population buffer of an nx x ny grid, in the
+ *           layout of lbm_workspace_bytes (read only).
  *   out:    host memory, receives the sum.
  *   cuda_stream: stream on which the work is enqueued; the call waits for it (synchronous).
  * Limit: ny <= LBM_NOALLOC_MAX_ROWS (one partial sum per row); larger grids return LBM_EINVAL

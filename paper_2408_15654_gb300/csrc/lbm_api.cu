@@ -59,7 +59,8 @@ int get_encoder(EncodeTiledFn* fn) {
 }
 
 // 3-D tensor map {nx, ny, planes} of elements of es bytes (8: float pairs, 4: floats or
-// 16-bit pairs, 2: 16-bit values); pitch and plane stride counted in elements.
+// 16-bit pairs, 2: 16-bit values); pitch and plane stride counted in elements.  The maps of the
+// step cover whole planes including the ghost frame (nx = pitch, ny = rows of a plane).
 int encode_map(CUtensorMap* tm, void* base, int es, int nx, int ny, int planes, int pitch, size_t plane,
                unsigned bw, unsigned bh, unsigned bp) {
     EncodeTiledFn enc;
@@ -122,10 +123,18 @@ int validate(const lbm_params* p) {
     return LBM_OK;
 }
 
+// Plane geometry: the grid inside its ghost frame (lbm::kGX columns left, at least 2 right,
+// lbm::kGY rows above and below), pitch a multiple of 32 cells.
+void frame_of(int nx, int ny, int* pitch, size_t* plane, long long* org) {
+    *pitch = (nx + lbm::kGX + 2 + 31) / 32 * 32;
+    *plane = (size_t)(ny + 2 * lbm::kGY) * (size_t)*pitch;
+    *org = (long long)lbm::kGY * *pitch + lbm::kGX;
+}
+
 Layout layout_of(const lbm_params* p) {
     Layout L;
-    L.pitch = (p->nx + 31) / 32 * 32;
-    L.plane = (size_t)p->ny * L.pitch;
+    long long org = 0;
+    frame_of(p->nx, p->ny, &L.pitch, &L.plane, &org);
     L.pops_bytes = align_up(L.plane * (size_t)lbm::pop_bytes_per_cell(p->storage, p->velocity == LBM_VELOCITY_SOLVED));
     size_t off = 0;
     L.off_pops[0] = off; off += L.pops_bytes;
@@ -156,6 +165,7 @@ lbm::Phys make_phys(const lbm_params* p, const Layout& L) {
     f.ny = p->ny;
     f.pitch = L.pitch;
     f.plane = (long long)L.plane;
+    f.org = (long long)lbm::kGY * L.pitch + lbm::kGX;
     f.phiA = (float)p->phiA;
     f.phiB = (float)p->phiB;
     f.inv_dphi = (float)(1.0 / dphi);
@@ -251,19 +261,20 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
 
 // FP64 sum of phi (lane 0) or psi (lane 1) of a population buffer into partials[0..blocks),
 // then partials[blocks] ... written to *dres.
-int launch_reduce(int st, const void* pops, int lane, int nx, int ny, int pitch, size_t plane, const lbm::Phys& ph,
+int launch_reduce(int st, const void* pops, int lane, int nx, int ny, int pitch, size_t plane, long long org,
+                  const lbm::Phys& ph,
                   int blocks, double* partials, double* dres, cudaStream_t stream) {
     // the pair planes of the FG modes are stored like those of the all-16-bit modes
     const long long pl = (long long)plane;
     if (st == LBM_STORE_FP16 || st == LBM_STORE_FP16_FG)
         lbm::reduce_partial_kernel<lbm::kFP16><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch, pl,
-                                                                                           ph, partials);
+                                                                                           org, ph, partials);
     else if (st == LBM_STORE_BF16 || st == LBM_STORE_BF16_FG)
         lbm::reduce_partial_kernel<lbm::kBF16><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch, pl,
-                                                                                           ph, partials);
+                                                                                           org, ph, partials);
     else
         lbm::reduce_partial_kernel<lbm::kFP32><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch, pl,
-                                                                                           ph, partials);
+                                                                                           org, ph, partials);
     LBM_CUDA(cudaGetLastError());
     lbm::reduce_final_kernel<<<1, lbm::kReduceThreads, 0, stream>>>(partials, blocks, dres);
     LBM_CUDA(cudaGetLastError());
@@ -326,11 +337,14 @@ int lbm_reduce_noalloc(const void* d_pops, int nx, int ny, int what, void* cuda_
     double* scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
     if (rc) return rc;
-    const int pitch = (nx + 31) / 32 * 32;
+    int pitch = 0;
+    size_t plane = 0;
+    long long org = 0;
+    frame_of(nx, ny, &pitch, &plane, &org);
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     lbm::Phys ph;
     std::memset(&ph, 0, sizeof(ph));
-    rc = launch_reduce(LBM_STORE_FP32, d_pops, what == LBM_SUM_PSI ? 1 : 0, nx, ny, pitch, (size_t)ny * pitch, ph, ny,
+    rc = launch_reduce(LBM_STORE_FP32, d_pops, what == LBM_SUM_PSI ? 1 : 0, nx, ny, pitch, plane, org, ph, ny,
                        scratch, scratch + LBM_NOALLOC_MAX_ROWS, stream);
     if (rc) return rc;
     LBM_CUDA(cudaMemcpyAsync(out, scratch + LBM_NOALLOC_MAX_ROWS, sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -385,15 +399,15 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
     const int es_pair = pair16 ? 4 : 8, es_h = h16 ? 2 : 4;
     const unsigned hbw = h16 ? lbm::Traits<lbm::kFP16>::H_BW : lbm::Traits<lbm::kFP32>::H_BW;
     for (int b = 0; b < 2 && !rc; ++b) {
-        rc = encode_map(&h->tm_fg[b], h->pops[b], es_pair, p->nx, p->ny, lbm::kPairs, L.pitch, L.plane, lbm::BW,
+        rc = encode_map(&h->tm_fg[b], h->pops[b], es_pair, L.pitch, p->ny + 2 * lbm::kGY, lbm::kPairs, L.pitch, L.plane, lbm::BW,
                         lbm::BH, 1);
         char* hbase = static_cast<char*>(h->pops[b]) + (size_t)lbm::kPairs * L.plane * es_pair;
         if (!rc && p->velocity == LBM_VELOCITY_SOLVED)  // no h planes with a prescribed velocity
-            rc = encode_map(&h->tm_h[b], hbase, es_h, p->nx, p->ny, lbm::kHPlanes, L.pitch, L.plane, hbw, lbm::TY, 1);
+            rc = encode_map(&h->tm_h[b], hbase, es_h, L.pitch, p->ny + 2 * lbm::kGY, lbm::kHPlanes, L.pitch, L.plane, hbw, lbm::TY, 1);
     }
     for (int b = 0; b < 2 && !rc; ++b)
-        rc = h16 ? encode_map(&h->tm_hist[b], h->hist[b], 8, p->nx, p->ny, 1, L.pitch, L.plane, lbm::BW, lbm::BH, 1)
-                  : encode_map(&h->tm_hist[b], h->hist[b], 8, p->nx, p->ny, 1, L.pitch, L.plane, lbm::TX, lbm::TY, 1);
+        rc = h16 ? encode_map(&h->tm_hist[b], h->hist[b], 8, L.pitch, p->ny + 2 * lbm::kGY, 1, L.pitch, L.plane, lbm::BW, lbm::BH, 1)
+                  : encode_map(&h->tm_hist[b], h->hist[b], 8, L.pitch, p->ny + 2 * lbm::kGY, 1, L.pitch, L.plane, lbm::TX, lbm::TY, 1);
     if (rc) {
         delete h;
         return rc;
@@ -518,7 +532,7 @@ int lbm_reduce(lbm_handle* h, int what, double* out) {
     const int blocks = h->prm.ny < lbm::kMaxPartials ? h->prm.ny : lbm::kMaxPartials;
     double* dres = h->partials + lbm::kMaxPartials;
     int rc = launch_reduce(h->prm.storage, h->pops[h->cur], what == LBM_SUM_PSI ? 1 : 0, h->prm.nx, h->prm.ny,
-                           h->L.pitch, h->L.plane, h->phys, blocks, h->partials, dres, h->stream);
+                           h->L.pitch, h->L.plane, h->phys.org, h->phys, blocks, h->partials, dres, h->stream);
     if (rc) return rc;
     LBM_CUDA(cudaMemcpyAsync(out, dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     unsigned st = 0;

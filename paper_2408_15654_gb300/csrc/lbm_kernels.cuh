@@ -1,16 +1,18 @@
 // Device code of the fused three-population lattice-Boltzmann step (arXiv 2408.15654).
 //
-// Data layout in HBM (one population buffer, ny rows x `pitch` cells per plane):
+// Data layout in HBM (one population buffer; each plane ny + 4 rows x `pitch` cells, the grid
+// inside a ghost frame, see kGX / kGY):
 //   9 pair planes  (f_i, g_i), i = 0..8      phase field (Sec. 3.1) and surfactant (Sec. 3.2)
-//   8 planes       h_1..h_8                  flow (Sec. 3.3)
+//   8 planes       h_1..h_8                  flow (Sec. 3.3; absent with a prescribed velocity)
 // f_i and g_i stream along the same link, so they travel and collide together: one access per
 // pair, and Blackwell's packed FP32x2 arithmetic runs both collisions at once.  h_0 is never
 // stored: column 0 of M^-1 is e_0 and rows 1..8 of M do not see h_0, so h_0 feeds only itself
 // (Sec. 3.3, Sec. 4).  The u history is one float2 plane (u_x, u_y) per buffer.
 // A buffer holds the post-collision populations of the previous step at the cell that produced
 // them; a step pulls q_i(x) = q*_i(x - c_i) ("pull" streaming), so it writes only its own cell
-// and two buffers alternate.  Across a wall the missing link is the cell's own opposite slot,
-// into which the previous step already folded the moving-wall term (half-way bounce-back, Sec. 4).
+// (and the ghost-frame copies of it) and two buffers alternate.  Across a wall the missing link
+// is the puller's own opposite slot, with the moving-wall term folded in (half-way bounce-back,
+// Sec. 4), which the previous step also wrote into the wall's ghost row.
 //
 // Storage modes: FP32; FP16 or BF16 for all 26 populations; FP16 or BF16 for the 18 of f and g
 // with h kept in FP32.  16-bit values are stored divided by their lattice weight, as scaled
@@ -99,10 +101,20 @@ __host__ __device__ constexpr int pop_bytes_per_cell(int st, bool flow = true) {
 __host__ __device__ constexpr bool pair_is_16bit(int st) { return st != kFP32; }
 __host__ __device__ constexpr bool h_is_16bit(int st) { return st == kFP16 || st == kBF16; }
 
+// Ghost frame of every plane: cell (x, y) sits at row y + kGY, column x + kGX of a plane of
+// (ny + 2 kGY) rows x pitch columns.  Columns -2, -1, nx, nx + 1 and, for periodic y, rows -2,
+// -1, ny, ny + 1 hold the periodic images of the cells they stand for; with walls, rows -1 and
+// ny hold, in the planes of the links that cross the wall, the bounce-back value for the pull
+// (the puller's own post-collision opposite slot).  Every value a pull or the one-cell ring of a
+// tile reads is then at its plain position, and the TMA boxes need no patching.  kGX = 8 keeps
+// the x coordinate of every box a multiple of 16 bytes (boxes start 4 or 8 cells left of a tile).
+constexpr int kGX = 8, kGY = 2;
+
 // Physical constants in FP32, precomputed on the host from lbm_params.
 struct Phys {
     int nx, ny, pitch, pad0;
-    long long plane;          // cells per plane (ny * pitch)
+    long long plane;          // cells per plane ((ny + 2 kGY) * pitch)
+    long long org;            // index of cell (0, 0): kGY * pitch + kGX
     float phiA, phiB, inv_dphi;
     float cA;                 // 4 / (W dphi):  A = cA (phiA - phi)(phi - phiB), B = cA psi (phiA + phiB - 2 phi)
     float cap_k, c16W, W;     // capillary: cap_k sigma [c16W (phiA-phi)(phi-phiB)(phiA+phiB-2phi) - W lap phi]
@@ -234,12 +246,32 @@ template <typename T> __device__ __forceinline__ T pack1(float v);
 template <> __device__ __forceinline__ float pack1<float>(float v) { return v; }
 template <> __device__ __forceinline__ __half pack1<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 pack1<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+// a 16-bit pattern as a storage value
+template <typename T> __device__ __forceinline__ T bits_to(uint32_t b);
+template <> __device__ __forceinline__ __half bits_to<__half>(uint32_t b) { return __ushort_as_half((unsigned short)b); }
+template <> __device__ __forceinline__ __nv_bfloat16 bits_to<__nv_bfloat16>(uint32_t b) {
+    return __ushort_as_bfloat16((unsigned short)b);
+}
+template <> __device__ __forceinline__ float bits_to<float>(uint32_t b) { return __uint_as_float(b); }
 
 // (f_i, g_i) from storage: the values (FP32), or the deviations (f_i - w_i phi_ref, g_i) (16-bit)
+// Decoding multiplies by w_i / S, which is not a binary fraction (w_i = 4/9, 1/9, 1/36): the FP32
+// constant would carry the same relative error (~1e-8) into every decoded value of link i at
+// every step, and that error would add up coherently in the totals of phi and psi.  The constant
+// is therefore split into a head and a tail (dd_hi + dd_lo = w_i / S to ~2^-48) and applied with
+// one extra fused multiply-add, so that only the final rounding remains.
+__host__ __device__ constexpr double wgt_d(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+__host__ __device__ constexpr float dd_hi(double x) { return (float)x; }
+__host__ __device__ constexpr float dd_lo(double x) { return (float)(x - (double)(float)x); }
 template <int ST, int I> __device__ __forceinline__ float2 dec_pair(typename Traits<ST>::P v) {
     using T = Traits<ST>;
-    if constexpr (!T::kPair16) return v;
-    else return mul2(raw2(v), make_float2(wgt(I) / T::SF, wgt(I) / T::SG));
+    if constexpr (!T::kPair16) {
+        return v;
+    } else {
+        constexpr double df = wgt_d(I) / T::SF, dg = wgt_d(I) / T::SG;
+        const float2 r = raw2(v);
+        return fma2(r, make_float2(dd_hi(df), dd_hi(dg)), mul2(r, make_float2(dd_lo(df), dd_lo(dg))));
+    }
 }
 // 3 w_i rho c_i.u: the first-order velocity part of h_eq removed before 16-bit storage
 template <int I> __device__ __forceinline__ float h_vel(float2 u, const Phys& p) {
@@ -272,7 +304,7 @@ __device__ __forceinline__ uint32_t rbits_of(uint32_t key, int k) { return __fun
 // (f_i, g_i) deviations to stochastically rounded 16-bit storage
 template <int ST, int I> __device__ __forceinline__ typename Traits<ST>::P enc_pair_rs(float2 q, uint32_t key) {
     using T = Traits<ST>;
-    const float2 v = mul2(q, make_float2(T::SF / wgt(I), T::SG / wgt(I)));
+    const float2 v = mul2(q, make_float2((float)(T::SF / wgt_d(I)), (float)(T::SG / wgt_d(I))));
     const uint32_t bits = cvt_rs2<typename T::P>(v.x, v.y, rbits_of(key, I));
     return *reinterpret_cast<const typename T::P*>(&bits);
 }
@@ -352,84 +384,6 @@ __device__ __forceinline__ void collide_pair(float2 q[9], float2 s, float2 sr, f
     q[8] = fma2(quarter, sub2(F, H), q[8]);
 }
 
-// Tiles whose boxes reach outside the grid: replace every staged value whose source lies outside
-// by the one the pull really reads there -- the periodic image, or across a wall the pulling
-// cell's own opposite slot (bounce-back).  Only the out-of-grid strips of each box are visited
-// (one warp per box); entries no valid pull reads are left as loaded.
-template <int ST, bool WALLS, bool FLOW>
-__device__ void patch_edges(const Phys& p, const TileIO& io, unsigned char* sm, int x0, int y0) {
-    using T = Traits<ST>;
-    using S = Smem<ST>;
-    using P = typename T::P;
-    using Hv = typename T::H;
-    const P* __restrict__ srcFG = static_cast<const P*>(io.src);
-    const Hv* __restrict__ srcH = reinterpret_cast<const Hv*>(srcFG + (size_t)kPairs * p.plane);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int NBOX = kPairs + kHPlanes + (S::kHalo ? 1 : 0);
-    for (int pl = warp; pl < NBOX; pl += NT / 32) {
-        if (!FLOW && pl >= kPairs && pl < kPairs + kHPlanes) continue;  // no h boxes
-        const int kind = pl < kPairs ? 0 : (pl < kPairs + kHPlanes ? 1 : 2);  // pair, h, history
-        const int i = kind == 0 ? pl : (kind == 1 ? pl - kPairs + 1 : 0);      // direction
-        const int bw = kind == 1 ? T::H_BW : BW;
-        const int xoff = kind == 1 ? T::H_X0 : 4;
-        const int rows = kind == 1 ? TY : BH;
-        const int gy0 = (kind == 1 ? y0 : y0 - 1) - cy(i);   // global row of box row 0
-        const int cL = min(bw, max(0, xoff - x0));           // box columns [0, cL) lie left of x = 0
-        const int cR = max(cL, min(bw, p.nx - x0 + xoff));   // box columns [cR, bw) lie right of nx - 1
-        const int rB = min(rows, max(0, -gy0));              // box rows [0, rB) lie below y = 0
-        const int rT = max(rB, min(rows, p.ny - gy0));       // box rows [rT, rows) lie above ny - 1
-        const int ncol = cL + (bw - cR), w = cR - cL;
-        const int n1 = rows * ncol, n2 = (rB + rows - rT) * w;
-        for (int k = lane; k < n1 + n2; k += 32) {
-            int r, c;
-            if (k < n1) {
-                r = k / ncol;
-                const int j = k - r * ncol;
-                c = j < cL ? j : cR + (j - cL);
-            } else {
-                const int kk = k - n1, rr = kk / w;
-                c = cL + (kk - rr * w);
-                r = rr < rB ? rr : rT + (rr - rB);
-            }
-            const int gx = x0 - xoff + c, gy = gy0 + r;
-            const bool yin = gy >= 0 && gy < p.ny;
-            // the cell that reads this entry must be one the tile uses
-            if (kind == 0) {
-                const int ex = c - 3 + cx(i);
-                if (ex < 0 || ex >= EX) continue;
-            } else if (kind == 1) {
-                const int tx = c - xoff + cx(i);
-                if (tx < 0 || tx >= TX) continue;
-            }
-            int si = i, sx, sy;
-            if (WALLS) {
-                const int py = gy + cy(i);
-                if (py < 0 || py >= p.ny) continue;  // reader is a ring cell beyond a wall (mirrored)
-                if (!yin) {
-                    if (kind == 2) continue;          // across a wall the h pull uses the own u
-                    si = opp(i);
-                    sx = wrapg(gx + cx(i), p.nx);
-                    sy = py;
-                } else {
-                    sx = wrapg(gx, p.nx);
-                    sy = gy;
-                }
-            } else {
-                sx = wrapg(gx, p.nx);
-                sy = wrapg(gy, p.ny);
-            }
-            const size_t cell = (size_t)sy * p.pitch + sx;
-            if (kind == 0)
-                reinterpret_cast<P*>(sm + S::FG + pl * S::FG_SLOT)[r * bw + c] = srcFG[(size_t)si * p.plane + cell];
-            else if (kind == 1)
-                reinterpret_cast<Hv*>(sm + S::H + (pl - kPairs) * S::H_SLOT)[r * bw + c] =
-                    srcH[(size_t)(si - 1) * p.plane + cell];
-            else
-                reinterpret_cast<float2*>(sm + S::HIST)[r * bw + c] = io.hist_src[cell];
-        }
-    }
-}
-
 template <int ST, int I>
 __device__ __forceinline__ float load_h(const unsigned char* sm, const float2* Hist, const Phys& p, int tx, int ty,
                                         bool bb, float2 uown) {
@@ -442,7 +396,9 @@ __device__ __forceinline__ float load_h(const unsigned char* sm, const float2* H
         // the slot was stored with the first-order velocity part of the cell that stored it:
         // the source cell x - c_i, or across a wall the own cell (whose opposite slot it is)
         const float2 us = bb ? make_float2(-uown.x, -uown.y) : Hist[(ty + 1 - cy(I)) * BW + tx + 4 - cx(I)];
-        return fmaf(raw1(v), wgt(I) / T::SH, h_vel<I>(us, p));
+        constexpr double dh = wgt_d(I) / T::SH;
+        const float r = raw1(v);
+        return fmaf(r, dd_hi(dh), fmaf(r, dd_lo(dh), h_vel<I>(us, p)));
     }
 }
 
@@ -454,21 +410,21 @@ __device__ __forceinline__ void issue_tile_loads(unsigned char* sm, const CUtens
     using S = Smem<ST>;
     mbar_expect_tx(mbar, FLOW ? S::TX_BYTES : S::TX_BYTES_NOH);
 #pragma unroll
-    for (int i = 0; i < kPairs; ++i) tma_load_3d(sm + S::FG + i * S::FG_SLOT, tm_fg, x0 - 4, y0 - 1 - cy(i), i, mbar);
+    for (int i = 0; i < kPairs; ++i)
+        tma_load_3d(sm + S::FG + i * S::FG_SLOT, tm_fg, x0 - 4 + kGX, y0 - 1 - cy(i) + kGY, i, mbar);
     if constexpr (FLOW) {
 #pragma unroll
         for (int i = 1; i < 9; ++i)
-            tma_load_3d(sm + S::H + (i - 1) * S::H_SLOT, tm_h, x0 - T::H_X0, y0 - cy(i), i - 1, mbar);
+            tma_load_3d(sm + S::H + (i - 1) * S::H_SLOT, tm_h, x0 - T::H_X0 + kGX, y0 - cy(i) + kGY, i - 1, mbar);
     }
-    if constexpr (S::kHalo) tma_load_3d(sm + S::HIST, tm_hist, x0 - 4, y0 - 1, 0, mbar);
-    else tma_load_3d(sm + S::HIST, tm_hist, x0, y0, 0, mbar);
+    if constexpr (S::kHalo) tma_load_3d(sm + S::HIST, tm_hist, x0 - 4 + kGX, y0 - 1 + kGY, 0, mbar);
+    else tma_load_3d(sm + S::HIST, tm_hist, x0 + kGX, y0 + kGY, 0, mbar);
 }
 
 // One fused step (kStep) or the macroscopic fields of the current level (kMoments) for one tile,
 // after one thread has issued the tile's TMA loads into `stage` on `mbar`, whose phase of this
 // tile has parity `parity`; PP holds the tile's (phi, psi).  Returns true (uniformly) if a copy
-// did not arrive within its bounded wait (nothing stored).  Edge tiles patch wrapped and bounced
-// entries.  The pulled (f, g) of the tile and of a one-cell ring give (phi, psi) for the
+// did not arrive within its bounded wait (nothing stored).  The pulled (f, g) of the tile and of a one-cell ring give (phi, psi) for the
 // 9-point stencils; the same boxes hold the own cell's unshifted post-collision values, whose sums
 // are phi and psi of the previous level (m*_0 = phi exactly, Sec. 3.1), so only u of the
 // previous level is stored.
@@ -483,10 +439,6 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     const int t = threadIdx.x;
     __syncthreads();
     bool abort = !mbar_wait_bounded(mbar, parity);
-    if (x0 == 0 || x0 + TX + 8 > p.nx || y0 == 0 || y0 + TY + 2 > p.ny) {
-        if (!abort) patch_edges<ST, WALLS, FLOW>(p, io, sm, x0, y0);
-        abort = __syncthreads_or(abort);
-    }
 
     const int tx = t % TX, ty = t / TX;
     const int x = x0 + tx, y = y0 + ty;
@@ -664,7 +616,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         if (bad) atomicOr(io.status, kStatusUnstable);
     }
 
-    const size_t cell = (size_t)y * p.pitch + x;
+    const size_t cell = (size_t)(p.org + (long long)y * p.pitch + x);
     if constexpr (MODE == kMoments) {
         const size_t o = (size_t)y * p.nx + x;
         if (io.out[0]) io.out[0][o] = phi;
@@ -673,8 +625,11 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         if (io.out[3]) io.out[3][o] = uy;
         if (io.out[4]) io.out[4][o] = P_;
     } else {
+        using Hv = typename T::H;
         uint32_t key = 0;
         if constexpr (T::kPair16) key = cell_key((uint32_t)cell, io.seed);
+        P outp[9];  // the stored (f_i, g_i)
+        Hv outh[8]; // the stored h_1..h_8
         // ---- f (Sec. 3.1) and g (Sec. 3.2) together; sources cs2 V = d_t(s u) + cs2 (A or B) n ----
         {
             const float2 vx = fma2(make_float2(Aterm, Bterm), bc(nx_ * (1.f / 3.f)), dtX);
@@ -682,20 +637,19 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
             collide_pair(q, pp, sub2(pp, ref), ux, uy, vx, vy, make_float2(p.nS1[0], p.nS1[1]),
                          make_float2(p.nS2[0], p.nS2[1]), make_float2(p.nS3[0], p.nS3[1]),
                          make_float2(p.nS4[0], p.nS4[1]), make_float2(p.K1[0], p.K1[1]), make_float2(p.K3[0], p.K3[1]));
-            P* __restrict__ dfg = static_cast<P*>(io.dst) + cell;
             if constexpr (!T::kPair16) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) dfg[(size_t)i * p.plane] = q[i];
+                for (int i = 0; i < 9; ++i) outp[i] = q[i];
             } else {
-                dfg[0 * p.plane] = enc_pair_rs<ST, 0>(q[0], key);
-                dfg[1 * p.plane] = enc_pair_rs<ST, 1>(q[1], key);
-                dfg[2 * p.plane] = enc_pair_rs<ST, 2>(q[2], key);
-                dfg[3 * p.plane] = enc_pair_rs<ST, 3>(q[3], key);
-                dfg[4 * p.plane] = enc_pair_rs<ST, 4>(q[4], key);
-                dfg[5 * p.plane] = enc_pair_rs<ST, 5>(q[5], key);
-                dfg[6 * p.plane] = enc_pair_rs<ST, 6>(q[6], key);
-                dfg[7 * p.plane] = enc_pair_rs<ST, 7>(q[7], key);
-                dfg[8 * p.plane] = enc_pair_rs<ST, 8>(q[8], key);
+                outp[0] = enc_pair_rs<ST, 0>(q[0], key);
+                outp[1] = enc_pair_rs<ST, 1>(q[1], key);
+                outp[2] = enc_pair_rs<ST, 2>(q[2], key);
+                outp[3] = enc_pair_rs<ST, 3>(q[3], key);
+                outp[4] = enc_pair_rs<ST, 4>(q[4], key);
+                outp[5] = enc_pair_rs<ST, 5>(q[5], key);
+                outp[6] = enc_pair_rs<ST, 6>(q[6], key);
+                outp[7] = enc_pair_rs<ST, 7>(q[7], key);
+                outp[8] = enc_pair_rs<ST, 8>(q[8], key);
             }
         }
         // ---- flow h (Sec. 3.3); none when the velocity is prescribed ----
@@ -750,34 +704,102 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
                     h[6] -= 6.f * wgt(6) * rho * (-1.f) * p.u_top;
                 }
             }
-            using Hv = typename T::H;
-            Hv* __restrict__ dh = reinterpret_cast<Hv*>(static_cast<P*>(io.dst) + (size_t)kPairs * p.plane) + cell;
             if constexpr (!T::kH16) {
     #pragma unroll
-                for (int i = 1; i < 9; ++i) dh[(size_t)(i - 1) * p.plane] = h[i];
+                for (int i = 1; i < 9; ++i) outh[i - 1] = h[i];
             } else {
                 // every slot is stored relative to this cell's new u (what the next step reads back):
                 // raw = (h_i / w_i - 3 rho c_i.u) S_h, two links per stochastic conversion
                 const float vx = p.kh3 * T::SH * ux, vy = p.kh3 * T::SH * uy;
-                constexpr float e1 = T::SH / wgt(1), e5 = T::SH / wgt(5);
+                constexpr float e1 = (float)(T::SH / wgt_d(1)), e5 = (float)(T::SH / wgt_d(5));  // exact
                 const uint32_t b12 = cvt_rs2<typename T::P>(fmaf(h[1], e1, -vx), fmaf(h[2], e1, -vy), rbits_of(key, 9));
                 const uint32_t b34 = cvt_rs2<typename T::P>(fmaf(h[3], e1, vx), fmaf(h[4], e1, vy), rbits_of(key, 10));
                 const uint32_t b56 =
                     cvt_rs2<typename T::P>(fmaf(h[5], e5, -(vx + vy)), fmaf(h[6], e5, vx - vy), rbits_of(key, 11));
                 const uint32_t b78 =
                     cvt_rs2<typename T::P>(fmaf(h[7], e5, vx + vy), fmaf(h[8], e5, vy - vx), rbits_of(key, 12));
-                unsigned short* dh16 = reinterpret_cast<unsigned short*>(dh);
-                dh16[0 * p.plane] = (unsigned short)(b12 & 0xFFFFu);
-                dh16[1 * p.plane] = (unsigned short)(b12 >> 16);
-                dh16[2 * p.plane] = (unsigned short)(b34 & 0xFFFFu);
-                dh16[3 * p.plane] = (unsigned short)(b34 >> 16);
-                dh16[4 * p.plane] = (unsigned short)(b56 & 0xFFFFu);
-                dh16[5 * p.plane] = (unsigned short)(b56 >> 16);
-                dh16[6 * p.plane] = (unsigned short)(b78 & 0xFFFFu);
-                dh16[7 * p.plane] = (unsigned short)(b78 >> 16);
+                outh[0] = bits_to<Hv>(b12 & 0xFFFFu);
+                outh[1] = bits_to<Hv>(b12 >> 16);
+                outh[2] = bits_to<Hv>(b34 & 0xFFFFu);
+                outh[3] = bits_to<Hv>(b34 >> 16);
+                outh[4] = bits_to<Hv>(b56 & 0xFFFFu);
+                outh[5] = bits_to<Hv>(b56 >> 16);
+                outh[6] = bits_to<Hv>(b78 & 0xFFFFu);
+                outh[7] = bits_to<Hv>(b78 >> 16);
             }
         }
-        io.hist_dst[cell] = make_float2(ux, uy);
+        // ---- stores: the own cell, its periodic images in the ghost frame, and at a wall the
+        //      bounce-back ghosts of the links that cross it ----
+        P* __restrict__ dfg = static_cast<P*>(io.dst);
+        Hv* __restrict__ dh = reinterpret_cast<Hv*>(dfg + (size_t)kPairs * p.plane);
+        const long long pl = p.plane;
+        auto put = [&](long long c) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) dfg[i * pl + c] = outp[i];
+            if constexpr (FLOW) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) dh[i * pl + c] = outh[i];
+            }
+        };
+        const bool xl = x <= 1, xr = x >= p.nx - 2;
+        const bool yl = !WALLS && y <= 1, yr = !WALLS && y >= p.ny - 2;
+        const long long DX = p.nx, DY = (long long)p.ny * p.pitch;
+        put((long long)cell);
+        if (xl | xr | yl | yr) {
+            if (xl) put(cell + DX);
+            if (xr) put(cell - DX);
+            if (yl) {
+                put(cell + DY);
+                if (xl) put(cell + DY + DX);
+                if (xr) put(cell + DY - DX);
+            }
+            if (yr) {
+                put(cell - DY);
+                if (xl) put(cell - DY + DX);
+                if (xr) put(cell - DY - DX);
+            }
+        }
+        if (WALLS && (y == 0 || y == p.ny - 1)) {
+            // the pull of link i across the wall, at (x - c_ix, -1) or (x - c_ix, ny) in plane i,
+            // reads this cell's post-collision opposite slot (half-way bounce-back, Sec. 4)
+            auto bb = [&](int i, int io_, int col, long long c) {
+                const int nx = p.nx;
+                auto one = [&](long long d) {
+                    dfg[i * pl + d] = outp[io_];
+                    if constexpr (FLOW) dh[(i - 1) * pl + d] = outh[io_ - 1];
+                };
+                one(c);
+                if (col <= 1) one(c + nx);
+                if (col >= nx - 2) one(c - nx);
+            };
+            const long long pt = p.pitch;
+            if (y == 0) {
+                bb(2, 4, x, cell - pt);
+                bb(5, 7, x - 1, cell - pt - 1);
+                bb(6, 8, x + 1, cell - pt + 1);
+            } else {
+                bb(4, 2, x, cell + pt);
+                bb(7, 5, x + 1, cell + pt + 1);
+                bb(8, 6, x - 1, cell + pt - 1);
+            }
+        }
+        const float2 un = make_float2(ux, uy);
+        io.hist_dst[cell] = un;
+        if constexpr (S::kHalo) {
+            // the 16-bit h decode reads the neighbours' u, across periodic edges too
+            if (xl) io.hist_dst[cell + DX] = un;
+            if (xr) io.hist_dst[cell - DX] = un;
+            if (yl) {
+                io.hist_dst[cell + DY] = un;
+                if (xl) io.hist_dst[cell + DY + DX] = un;
+                if (xr) io.hist_dst[cell + DY - DX] = un;
+            }
+            if (yr) {
+                io.hist_dst[cell - DY] = un;
+                if (xl) io.hist_dst[cell - DY + DX] = un;
+                if (xr) io.hist_dst[cell - DY - DX] = un;
+            }
+        }
     }
     return false;
 }
@@ -787,8 +809,8 @@ template <int ST, bool WALLS, bool LANGMUIR, int MODE, bool FLOW>
 __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ StepArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + Smem<ST>::BAR);
-    // The first and the last tile row (whose boxes need edge patching, and so run longest) are
-    // launched first, so that the last wave holds interior tiles only.
+    // The first and the last tile row (whose cells also write the ghost frame, and so run longest)
+    // are launched first, so that the last wave holds interior tiles only.
     const int ntr = gridDim.y;
     const int tr = blockIdx.y == 0 ? 0 : (blockIdx.y == 1 ? ntr - 1 : (int)blockIdx.y - 1);
     const int x0 = blockIdx.x * TX, y0 = tr * TY;
@@ -806,7 +828,7 @@ __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ Ste
 }
 
 // Tile k of a grid of ntx x nty tiles: rows in the order first, last, then the interior (the two
-// edge rows, which patch their boxes, run first).
+// edge rows, whose cells also write the ghost frame, run first).
 __device__ __forceinline__ void tile_origin(int k, int ntx, int nty, int& x0, int& y0) {
     const int r = k / ntx, c = k - r * ntx;
     const int tr = r == 0 ? 0 : (r == 1 ? nty - 1 : r - 1);
@@ -817,7 +839,7 @@ __device__ __forceinline__ void tile_origin(int k, int ntx, int nty, int& x0, in
 // One step of one lattice by a persistent grid: each CTA claims tiles from an atomic counter
 // and stages its next tile's boxes with TMA into the other of two buffers while it computes the
 // current one, so the copy latency hides behind the arithmetic.  Claiming tiles one at a time
-// balances the longer edge tiles across the CTAs.  Thread 0 claims a tile one iteration before
+// balances the longer edge tiles (ghost-frame writes) across the CTAs.  Thread 0 claims a tile one iteration before
 // it needs it, so the atomic's latency also hides behind a tile's work.
 template <int ST, bool WALLS, bool LANGMUIR, bool FLOW>
 __global__ void __launch_bounds__(NT, 4) step_kernel_pipe(const __grid_constant__ StepArgs a, int ntx, int nty) {
@@ -871,10 +893,7 @@ __global__ void __launch_bounds__(NT, 4) step_kernel_pipe(const __grid_constant_
             if (threadIdx.x == 0 && slot[nxt] < ntiles) mbar_wait_bounded(&bars[nxt], ((it + 1) >> 1) & 1);
             break;
         }
-        // stage `cur`, its slot and PP are free again; order this CTA's generic accesses to the
-        // stage (the edge patch writes it) before the asynchronous TMA writes of the tile after next
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
+        __syncthreads();  // stage `cur` (only read by this CTA), its slot and PP are free again
     }
 }
 
@@ -984,37 +1003,69 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
         const double feq = w * phi * (1.0 + 3.0 * cu);
         const double geq = w * psi * (1.0 + 3.0 * cu);
         const double heq = w * (3.0 * P_ + 3.0 * rho * cu + 4.5 * rho * (cu * cu - uu / 3.0));
-        // the first pull at x for direction i reads slot i of x - c_i, or, across a wall, the
-        // opposite slot of x itself (same weight)
-        int sx = x - cx(i), sy = y - cy(i), slot = i;
-        if (a.walls && (sy < 0 || sy >= p.ny)) {
-            sx = x;
-            sy = y;
-            slot = opp(i);
+        // The first pull at x for direction i reads plane i at x - c_i: there, and at every
+        // periodic image of that position in the ghost frame, store this cell's equilibrium value.
+        // Across a wall x - c_i is in the wall's ghost row, which holds this cell's bounce-back
+        // value (its own opposite slot, same weight).
+        int sx = x - cx(i), sy = y - cy(i), enc = i;
+        const bool wall_ghost = a.walls && (sy < 0 || sy >= p.ny);
+        if (wall_ghost) {
+            enc = opp(i);
         } else {
             sx = (sx + p.nx) % p.nx;
             sy = (sy + p.ny) % p.ny;
         }
-        const size_t cell = (size_t)sy * p.pitch + sx;
+        P vfg;
         if constexpr (!T::kPair16)
-            fg[(size_t)slot * p.plane + cell] = make_float2((float)feq, (float)geq);
+            vfg = make_float2((float)feq, (float)geq);
         else
-            fg[(size_t)slot * p.plane + cell] = pack2<P>(
-                make_float2((float)((feq / w - p.phi_ref) * T::SF), (float)(geq / w * T::SG)));
-        if (slot == 0 || !a.flow) continue;
-        if constexpr (!T::kH16) {
-            hp[(size_t)(slot - 1) * p.plane + cell] = (Hv)heq;
-        } else {
-            // stored relative to the storing cell's velocity, as the step will read it back:
-            // the source cell for a plain link, this cell for a slot across a wall
-            const size_t so = (size_t)sy * p.nx + sx;
-            const double sux = (float)a.ux[so], suy = (float)a.uy[so];
-            const double vel = 3.0 * rho * (cx(slot) * sux + cy(slot) * suy);
-            hp[(size_t)(slot - 1) * p.plane + cell] = pack1<Hv>((float)((heq / w - vel) * T::SH));
+            vfg = pack2<P>(make_float2((float)((feq / w - p.phi_ref) * T::SF), (float)(geq / w * T::SG)));
+        Hv vh{};
+        if (i > 0 && a.flow) {
+            if constexpr (!T::kH16) {
+                vh = (Hv)heq;
+            } else {
+                // stored relative to the storing cell's velocity, as the step will read it back:
+                // the source cell for a plain link, this cell (slot opp(i)) across a wall
+                const size_t so = wall_ghost ? o : (size_t)sy * p.nx + sx;
+                const double sux = (float)a.ux[so], suy = (float)a.uy[so];
+                const double vel = 3.0 * rho * (cx(enc) * sux + cy(enc) * suy);
+                vh = pack1<Hv>((float)((heq / w - vel) * T::SH));
+            }
+        }
+        auto at = [&](int c, int r) {
+            const long long k = p.org + (long long)r * p.pitch + c;
+            fg[(long long)i * p.plane + k] = vfg;
+            if (i > 0 && a.flow) hp[(long long)(i - 1) * p.plane + k] = vh;
+        };
+        auto row = [&](int c, int r) {
+            at(c, r);
+            if (c <= 1) at(c + p.nx, r);
+            if (c >= p.nx - 2) at(c - p.nx, r);
+        };
+        row(sx, sy);
+        if (!a.walls) {
+            if (sy <= 1) row(sx, sy + p.ny);
+            if (sy >= p.ny - 2) row(sx, sy - p.ny);
         }
     }
-    const size_t cell = (size_t)y * p.pitch + x;
-    a.hist[cell] = make_float2((float)ux, (float)uy);
+    const float2 u0 = make_float2((float)ux, (float)uy);
+    auto hist_at = [&](int c, int r) { a.hist[p.org + (long long)r * p.pitch + c] = u0; };
+    auto hist_row = [&](int c, int r) {
+        hist_at(c, r);
+        if (c <= 1) hist_at(c + p.nx, r);
+        if (c >= p.nx - 2) hist_at(c - p.nx, r);
+    };
+    if constexpr (Smem<ST>::kHalo) {
+        // the images exist where the step maintains them (the 16-bit h decode reads them)
+        hist_row(x, y);
+        if (!a.walls) {
+            if (y <= 1) hist_row(x, y + p.ny);
+            if (y >= p.ny - 2) hist_row(x, y - p.ny);
+        }
+    } else {
+        hist_at(x, y);
+    }
 }
 
 // ---- FP64 sums of phi or psi: every population slot is pulled exactly once per step, so the
@@ -1041,7 +1092,8 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
 template <int ST>
 __global__ void __launch_bounds__(kReduceThreads) reduce_partial_kernel(const void* __restrict__ pops, int lane,
                                                                         int nx, int ny, int pitch, long long plane,
-                                                                        Phys p, double* __restrict__ partials) {
+                                                                        long long org, Phys p,
+                                                                        double* __restrict__ partials) {
     using T = Traits<ST>;
     using P = typename T::P;
     __shared__ double smem[32];
@@ -1051,7 +1103,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partial_kernel(const vo
     for (int y = blockIdx.x; y < ny; y += gridDim.x) {
         for (int k = threadIdx.x; k < kPairs * nx; k += blockDim.x) {
             const int i = k / nx, x = k - i * nx;
-            const float2 v = raw2(pairs[(size_t)i * plane + (size_t)y * pitch + x]);
+            const float2 v = raw2(pairs[(size_t)i * plane + (size_t)(org + (long long)y * pitch + x)]);
             if constexpr (!T::kPair16) {
                 acc += (double)(lane ? v.y : v.x);
             } else {

@@ -148,7 +148,9 @@ def make_params(p: dict) -> lbm_params:
     q.eos = LBM_EOS_LANGMUIR if p.get("eos", "linear") == "langmuir" else LBM_EOS_LINEAR
     st = p.get("storage", LBM_STORE_FP32)
     q.storage = STORAGE[st] if isinstance(st, str) else int(st)
-    q.velocity = LBM_VELOCITY_PRESCRIBED if p.get("velocity", "solved") == "prescribed" else LBM_VELOCITY_SOLVED
+    v = p.get("velocity", "solved")
+    q.velocity = int(v) if not isinstance(v, str) else {"solved": LBM_VELOCITY_SOLVED,
+                                                        "prescribed": LBM_VELOCITY_PRESCRIBED}[v]
     for k in ("u_top", "u_bot", "phiA", "phiB", "rhoA", "rhoB", "muA", "muB", "W", "M_phi", "D",
               "sigma0", "E0", "gx", "gy", "n_eps"):
         setattr(q, k, float(p[k]))

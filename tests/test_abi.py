@@ -51,33 +51,35 @@ def test_struct_layout_matches_header(tmp_path, name):
 def test_workspace_bytes_without_gpu():
     p, _ = W.shear_drop(512, 256)
     n = lbm.lbm_workspace_bytes(lbm.make_params(p))
-    pitch = 512
+    # planes of (256 + 4) rows x pitch cells, pitch = 512 + 10 rounded up to 32 (the ghost frame)
+    pitch, rows = 544, 260
+    cells = pitch * rows
     # two buffers of 26 float planes, two (u_x, u_y) history buffers, status and partials
-    assert n >= 2 * 26 * 256 * pitch * 4 + 2 * 256 * pitch * 8
-    assert n < 2 * 26 * 256 * pitch * 4 + 2 * 256 * pitch * 8 + 64 * 1024
+    assert n >= 2 * 26 * cells * 4 + 2 * cells * 8
+    assert n < 2 * 26 * cells * 4 + 2 * cells * 8 + 64 * 1024
     # 16-bit storage halves the population buffers
     p["storage"] = "fp16"
     n16 = lbm.lbm_workspace_bytes(lbm.make_params(p))
-    assert n16 >= 2 * 13 * 256 * pitch * 4 + 2 * 256 * pitch * 8
-    assert n16 < 2 * 13 * 256 * pitch * 4 + 2 * 256 * pitch * 8 + 64 * 1024
+    assert n16 >= 2 * 13 * cells * 4 + 2 * cells * 8
+    assert n16 < 2 * 13 * cells * 4 + 2 * cells * 8 + 64 * 1024
     # f and g in 16 bits, h in FP32: 68 bytes per cell and buffer
     p["storage"] = "bf16_fg"
     nfg = lbm.lbm_workspace_bytes(lbm.make_params(p))
-    assert nfg >= 2 * 68 * 256 * pitch + 2 * 256 * pitch * 8
-    assert nfg < 2 * 68 * 256 * pitch + 2 * 256 * pitch * 8 + 64 * 1024
+    assert nfg >= 2 * 68 * cells + 2 * cells * 8
+    assert nfg < 2 * 68 * cells + 2 * cells * 8 + 64 * 1024
 
 
 def test_prescribed_velocity_workspace_has_no_flow_planes():
     p, _ = W.convected_drop(512, 256)
     full = lbm.lbm_workspace_bytes(lbm.make_params(dict(p, velocity="solved")))
     pres = lbm.lbm_workspace_bytes(lbm.make_params(p))
-    assert full - pres == 2 * 8 * 4 * 256 * 512
+    assert full - pres == 2 * 8 * 4 * 260 * 544
 
 
 @pytest.mark.parametrize("bad", [dict(nx=1), dict(ny=0), dict(rhoA=2.0), dict(W=0.0), dict(M_phi=-1.0),
                                  dict(D=0.0), dict(muA=0.0), dict(s_f=(1, 1, 2.5, 1, 1)),
                                  dict(sigma0=float("nan")), dict(storage=7),
-                                 dict(velocity="sideways")])
+                                 dict(velocity=2)])
 def test_parameter_validation(bad):
     p, _ = W.stationary_drop(32, 32, R=8)
     p.update(bad)

@@ -27,8 +27,8 @@ def _cuda():
 
 def current_buffer(sim: "lbm.Lattice") -> int:
     """Device address of the handle's current population buffer (layout of lbm_workspace_bytes)."""
-    pitch = (sim.nx + 31) // 32 * 32
-    buf = (26 * sim.ny * pitch * 4 + 255) // 256 * 256
+    pitch = (sim.nx + 10 + 31) // 32 * 32  # the grid inside its ghost frame
+    buf = (26 * (sim.ny + 4) * pitch * 4 + 255) // 256 * 256
     return sim.workspace.data_ptr() + (sim.steps % 2) * buf
 
 
