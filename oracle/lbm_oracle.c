@@ -51,8 +51,12 @@
  * P is reported as 0.  Pins: with u = 0 it equals the full model at rest with sigma0 = 0; a sine
  * mode of psi is advected and damped as exp(-D k^2 t) sin(k (x - u t)); the centroid of a
  * convected drop moves at u.
- * Parity unpinned: the terms that act only when rhoA != rhoB (mass flux S, grad rho in H, m2H and
- * P) are checked only through the moment conditions of h_eq and H, not by a closed-form solution.
+ * The terms that act only when rhoA != rhoB (mass flux S, grad rho in H, m2H and P, the S history)
+ * have no closed form at a finite interface width; they are pinned by closed forms of the continuum
+ * equations that the discrete solution must approach as the interface is resolved: a layered
+ * gravity-driven channel (second order), uniform translation of a drop and of a relaxing slab
+ * (where S is parallel to u), and hydrostatic layers.  Dropping S from h_eq, the grad rho part of
+ * m2H or u.grad rho from P, or taking u = sum c h + F/2 without 1/rho, each fails one of them.
  */
 #include <math.h>
 #include <stdlib.h>
