@@ -79,9 +79,10 @@ extern "C" {
  * recomputed by the library and ignored here:
  *   1/s1^f = M_phi/cs2 + 1/2,  1/s1^g = D/cs2 + 1/2 (Eq. for s1^g),  1/s2^h = mu/(rho cs2) + 1/2.
  * A value s_h[4] <= 0 means s4^h = s2^h (recommended: keeps plane Couette flow exact).
- * Requirements: nx >= 2, ny >= 2, phiA != phiB, W > 0, M_phi > 0, D > 0, rhoA = rhoB > 0,
+ * Requirements: nx >= 2, ny >= 2, phiA != phiB, W > 0, M_phi > 0, D > 0, rhoA, rhoB > 0,
  * muA, muB > 0, all rates in (0, 2) (s_h[4] may be <= 0), storage one of LBM_STORE_*.
- * (Density ratio != 1 is not supported by this build: lbm_create returns LBM_EINVAL.)        */
+ * With rhoA != rhoB the step includes the mass flux S, the grad rho terms of H, m2H and P and
+ * the time derivative of S (Sec. 2.3, 3.3); the workspace then holds a mass-flux history too.  */
 typedef struct lbm_params {
     int32_t nx, ny;         /* grid size                                                     */
     int32_t bc_y;           /* LBM_BC_PERIODIC or LBM_BC_WALLS                               */
@@ -126,7 +127,8 @@ typedef struct lbm_handle lbm_handle;
  * store 16-bit values with stochastic rounding, its random bits a hash of the cell index and
  * the step count (so a run is deterministic and a restored state continues bit for bit).  The
  * velocity history (two buffers of (ny + 4) x pitch float pairs in the same frame, alternating
- * like the populations) follows the population buffers. */
+ * like the populations) follows the population buffers; with rhoA != rhoB (and a solved flow) two
+ * more such buffers hold the mass flux S of the last step. */
 int lbm_workspace_bytes(const lbm_params* p, size_t* bytes);
 
 /* Create a handle on the current CUDA device.

@@ -102,8 +102,7 @@ int validate(const lbm_params* p) {
         return fail(LBM_EINVAL, "bad velocity mode %d", p->velocity);
     if (!(p->phiA != p->phiB) || !(p->W > 0) || !(p->M_phi > 0) || !(p->D > 0))
         return fail(LBM_EINVAL, "need phiA != phiB, W > 0, M_phi > 0, D > 0");
-    if (!(p->rhoA > 0) || p->rhoA != p->rhoB)
-        return fail(LBM_EINVAL, "density ratio != 1 is not supported by this build (rhoA = rhoB > 0 required)");
+    if (!(p->rhoA > 0) || !(p->rhoB > 0)) return fail(LBM_EINVAL, "densities must be > 0");
     if (!(p->muA > 0) || !(p->muB > 0)) return fail(LBM_EINVAL, "viscosities must be > 0");
     const double* rs[3] = {p->s_f, p->s_g, p->s_h};
     for (int k = 0; k < 3; ++k)
@@ -141,6 +140,10 @@ Layout layout_of(const lbm_params* p) {
     L.off_pops[1] = off; off += L.pops_bytes;
     L.off_hist[0] = off; off += align_up(L.plane * sizeof(float2));
     L.off_hist[1] = off; off += align_up(L.plane * sizeof(float2));
+    // mass-flux history, only with a density ratio (and a solved flow)
+    L.shist_bytes = (p->rhoA != p->rhoB && p->velocity == LBM_VELOCITY_SOLVED) ? align_up(L.plane * sizeof(float2)) : 0;
+    L.off_shist[0] = off; off += L.shist_bytes;
+    L.off_shist[1] = off; off += L.shist_bytes;
     L.off_status = off; off += kAlign;
     L.off_partials = off; off += align_up(lbm::kMaxPartials * sizeof(double) + sizeof(double));
     L.total = off;
@@ -178,6 +181,10 @@ lbm::Phys make_phys(const lbm_params* p, const Layout& L) {
     f.E0 = (float)p->E0;
     f.rho = (float)p->rhoA;
     f.inv_rho = (float)(1.0 / p->rhoA);
+    f.var_rho = p->rhoA != p->rhoB ? 1 : 0;
+    f.rhoB = (float)p->rhoB;
+    f.drho = (float)((p->rhoA - p->rhoB) / dphi);
+    f.sfac = (float)(p->M_phi * (p->rhoA - p->rhoB) / dphi);
     f.muB = (float)p->muB;
     f.dmu = (float)(p->muA - p->muB);
     f.s2h = (float)(1.0 / (3.0 * p->muB / p->rhoA + 0.5));
@@ -208,9 +215,13 @@ lbm::Phys make_phys(const lbm_params* p, const Layout& L) {
     // 16-bit storage: references of the stored deviations (the scales are compile-time
     // constants of each mode)
     f.phi_ref = (float)(0.5 * (p->phiA + p->phiB));
-    f.kh_axis = (float)(3.0 / 9.0 * p->rhoA);
-    f.kh_diag = (float)(3.0 / 36.0 * p->rhoA);
-    f.kh3 = (float)(3.0 * p->rhoA);
+    // 16-bit h: the velocity part removed before storage uses one reference density, so that the
+    // decoder reproduces it exactly (with a density ratio it only approximates the local
+    // 3 w_i rho c_i.u, which costs accuracy, not correctness)
+    const double rho_ref = 0.5 * (p->rhoA + p->rhoB);
+    f.kh_axis = (float)(3.0 / 9.0 * rho_ref);
+    f.kh_diag = (float)(3.0 / 36.0 * rho_ref);
+    f.kh3 = (float)(3.0 * rho_ref);
     f.u_top = (float)p->u_top;
     f.u_bot = (float)p->u_bot;
     f.n_eps2 = (float)(p->n_eps * p->n_eps);
@@ -234,6 +245,8 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
     a.io.dst = h->pops[h->cur ^ 1];
     a.io.hist_src = h->hist[h->cur];
     a.io.hist_dst = h->hist[h->cur ^ 1];
+    a.io.shist_src = h->shist[h->cur];
+    a.io.shist_dst = h->shist[h->cur ^ 1];
     a.io.status = h->status;
     // salt of the stochastic rounding: a function of the step count, so a restored checkpoint
     // continues bit for bit
@@ -253,7 +266,7 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
         h->last_pipe_step = h->steps;
     }
     const bool flow = h->prm.velocity == LBM_VELOCITY_SOLVED;
-    const lbm::Variant v{walls, flow && lang, flow};  // the EOS is unused with a prescribed velocity
+    const lbm::Variant v{walls, flow && lang, flow, h->phys.var_rho != 0};  // EOS unused if prescribed
     cudaError_t e = lbm::launch_step(h->prm.storage, a, mode, v, grid, pipe, h->stream);
     if (e != cudaSuccess) return fail(LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
     return LBM_OK;
@@ -387,6 +400,8 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
     h->pops[1] = h->ws + L.off_pops[1];
     h->hist[0] = reinterpret_cast<float2*>(h->ws + L.off_hist[0]);
     h->hist[1] = reinterpret_cast<float2*>(h->ws + L.off_hist[1]);
+    h->shist[0] = L.shist_bytes ? reinterpret_cast<float2*>(h->ws + L.off_shist[0]) : nullptr;
+    h->shist[1] = L.shist_bytes ? reinterpret_cast<float2*>(h->ws + L.off_shist[1]) : nullptr;
     h->status = reinterpret_cast<unsigned*>(h->ws + L.off_status);
     h->tile_ctr = h->status + 2;
     h->last_pipe_step = -2;
@@ -550,7 +565,8 @@ int lbm_status(lbm_handle* h) {
     return status_code(st);
 }
 
-// State blob: header, then the current population buffer, then the u history.
+// State blob: header, then the current population buffer, then the u history (and, with a
+// density ratio, the mass-flux history).
 struct StateHeader {
     uint64_t magic;
     int32_t nx, ny, pitch, first;
@@ -561,8 +577,9 @@ static const uint64_t kStateMagic = 0x4c424d3253544154ull;  // "LBM2STAT"
 int lbm_state_bytes(const lbm_handle* h, size_t* bytes) {
     g_err.clear();
     if (!h || !bytes) return fail(LBM_EINVAL, "NULL argument");
-    *bytes = sizeof(StateHeader) + h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage, h->prm.velocity == LBM_VELOCITY_SOLVED) +
-             h->L.plane * sizeof(float2);
+    *bytes = sizeof(StateHeader) +
+             h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage, h->prm.velocity == LBM_VELOCITY_SOLVED) +
+             h->L.plane * sizeof(float2) * (h->shist[0] ? 2 : 1);
     return LBM_OK;
 }
 
@@ -580,6 +597,9 @@ int lbm_get_state(lbm_handle* h, void* host_blob, size_t bytes) {
     LBM_CUDA(cudaMemcpyAsync(b + sizeof(hd), h->pops[h->cur], pb, cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(cudaMemcpyAsync(b + sizeof(hd) + pb, h->hist[h->cur], h->L.plane * sizeof(float2), cudaMemcpyDeviceToHost,
                              h->stream));
+    if (h->shist[0])
+        LBM_CUDA(cudaMemcpyAsync(b + sizeof(hd) + pb + h->L.plane * sizeof(float2), h->shist[h->cur],
+                                 h->L.plane * sizeof(float2), cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
@@ -600,6 +620,9 @@ int lbm_set_state(lbm_handle* h, const void* host_blob, size_t bytes) {
     LBM_CUDA(cudaMemcpyAsync(h->pops[cur], b + sizeof(hd), pb, cudaMemcpyHostToDevice, h->stream));
     LBM_CUDA(cudaMemcpyAsync(h->hist[cur], b + sizeof(hd) + pb, h->L.plane * sizeof(float2), cudaMemcpyHostToDevice,
                              h->stream));
+    if (h->shist[0])
+        LBM_CUDA(cudaMemcpyAsync(h->shist[cur], b + sizeof(hd) + pb + h->L.plane * sizeof(float2),
+                                 h->L.plane * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
     LBM_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
     h->cur = cur;

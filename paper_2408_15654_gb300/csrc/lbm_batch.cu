@@ -16,7 +16,7 @@ namespace {
 
 struct Group {
     int st;
-    bool walls, lang, flow;
+    bool walls, lang, flow, var_rho;
     int64_t off, count;  // tiles [off, off + count) of the tile list
 };
 
@@ -25,11 +25,12 @@ int64_t tiles_of(const lbm_handle* h) { return (int64_t)h->tiles_x * h->tiles_y;
 // Kernel variant of a lattice (the EOS is unused with a prescribed velocity).
 Group group_of(const lbm_handle* h) {
     const bool flow = h->prm.velocity == LBM_VELOCITY_SOLVED;
-    return Group{h->prm.storage, h->prm.bc_y == LBM_BC_WALLS, flow && h->prm.eos == LBM_EOS_LANGMUIR, flow, 0, 0};
+    return Group{h->prm.storage, h->prm.bc_y == LBM_BC_WALLS, flow && h->prm.eos == LBM_EOS_LANGMUIR, flow,
+                 flow && h->phys.var_rho != 0, 0, 0};
 }
 
 bool same_group(const Group& a, const Group& b) {
-    return a.st == b.st && a.walls == b.walls && a.lang == b.lang && a.flow == b.flow;
+    return a.st == b.st && a.walls == b.walls && a.lang == b.lang && a.flow == b.flow && a.var_rho == b.var_rho;
 }
 
 // Tile rows of one lattice in launch order: the two edge rows (which patch their boxes and run
@@ -87,6 +88,7 @@ int build_tiles(lbm_batch* b) {
     std::sort(groups.begin(), groups.end(), [](const Group& a, const Group& c) {
         if (a.st != c.st) return a.st < c.st;
         if (a.flow != c.flow) return a.flow < c.flow;
+        if (a.var_rho != c.var_rho) return a.var_rho < c.var_rho;
         return a.walls != c.walls ? a.walls < c.walls : a.lang < c.lang;
     });
     std::vector<uint2> tiles;
@@ -147,6 +149,7 @@ int upload_descs(lbm_batch* b) {
             d.tm_hist[j] = h->tm_hist[j];
             d.pops[j] = h->pops[j];
             d.hist[j] = h->hist[j];
+            d.shist[j] = h->shist[j];
         }
         d.p = h->phys;
         d.status = h->status;
@@ -168,7 +171,7 @@ int launch_one(lbm_batch* b, int s) {
         a.descs = b->d_desc;
         a.tiles = b->d_tiles + g.off;
         a.s = s;
-        cudaError_t e = lbm::launch_batch(g.st, a, lbm::Variant{g.walls, g.lang, g.flow}, (unsigned)g.count, b->stream);
+        cudaError_t e = lbm::launch_batch(g.st, a, lbm::Variant{g.walls, g.lang, g.flow, g.var_rho}, (unsigned)g.count, b->stream);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "batch step launch: %s", cudaGetErrorString(e));
         b->launches++;
     }

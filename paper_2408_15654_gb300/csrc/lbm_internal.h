@@ -20,7 +20,7 @@ struct Layout {
     int pitch;
     size_t plane;       // cells per plane
     size_t pops_bytes;  // one population buffer
-    size_t off_pops[2], off_hist[2], off_status, off_partials, total;
+    size_t off_pops[2], off_hist[2], off_shist[2], shist_bytes, off_status, off_partials, total;
 };
 
 }  // namespace lbm_host
@@ -39,6 +39,7 @@ struct lbm_handle {
     char* ws;
     void* pops[2];
     float2* hist[2];         // u history, alternating with the population buffers
+    float2* shist[2];        // mass-flux history (density ratio != 1), else null
     unsigned* status;
     unsigned* tile_ctr;      // two tile counters of the pipelined kernel (status region + 8 bytes)
     int64_t last_pipe_step;  // step index of the last pipelined launch (-2: none since a reset)

@@ -135,9 +135,16 @@ struct Phys {
     float phi_ref;            // (phiA + phiB) / 2
     float kh_axis, kh_diag;   // 3 w_i rho for axis and diagonal links (h decode)
     float kh3;                // 3 rho (h encode, before the scale)
+    // density ratio != 1 (Sec. 2.3): rho = rhoB + (phi - phiB) drho, S = sfac [grad phi - A n]
+    int var_rho;              // 1: rhoA != rhoB (rho, inv_rho above unused by its kernels)
+    float rhoB, drho, sfac;   // drho = (rhoA - rhoB) / dphi; sfac = M_phi drho
 };
 
 enum Mode { kStep = 0, kMoments = 1 };
+
+// Flow variant of a kernel (template argument FLOW): the velocity prescribed (no h), solved by h
+// with a uniform density, or solved with a density ratio (mass flux S and the grad rho terms).
+enum Flow { kFlowPrescribed = 0, kFlowUniform = 1, kFlowVarRho = 2 };
 
 // Tile geometry.  A CTA of NT threads owns a TX x TY tile, one cell per thread.  TMA stages:
 //   pair plane i: box of BW x BH pairs,    row r, col c <-> (x0 - 4 + c, y0 - 1 - cy(i) + r)
@@ -164,6 +171,8 @@ struct TileIO {
     void* __restrict__ dst;
     const float2* __restrict__ hist_src;  // (u_x, u_y) of the previous step
     float2* __restrict__ hist_dst;        // (u_x, u_y) of this step (the other history buffer)
+    const float2* __restrict__ shist_src; // mass flux (S_x, S_y) of the previous step (density ratio != 1)
+    float2* __restrict__ shist_dst;       // (S_x, S_y) of this step
     unsigned* __restrict__ status;
     double* __restrict__ out[5];  // kMoments: phi, psi, ux, uy, P (dense ny x nx), may be null
     unsigned seed;                // per-step salt of the stochastic rounding
@@ -403,7 +412,7 @@ __device__ __forceinline__ float load_h(const unsigned char* sm, const float2* H
 }
 
 // Stage the boxes of tile (x0, y0) with TMA on one mbarrier (called by one thread).
-template <int ST, bool FLOW>
+template <int ST, int FLOW>
 __device__ __forceinline__ void issue_tile_loads(unsigned char* sm, const CUtensorMap* tm_fg, const CUtensorMap* tm_h,
                                                  const CUtensorMap* tm_hist, int x0, int y0, unsigned long long* mbar) {
     using T = Traits<ST>;
@@ -428,7 +437,7 @@ __device__ __forceinline__ void issue_tile_loads(unsigned char* sm, const CUtens
 // 9-point stencils; the same boxes hold the own cell's unshifted post-collision values, whose sums
 // are phi and psi of the previous level (m*_0 = phi exactly, Sec. 3.1), so only u of the
 // previous level is stored.
-template <int ST, bool WALLS, bool LANGMUIR, int MODE, bool FLOW>
+template <int ST, bool WALLS, bool LANGMUIR, int MODE, int FLOW>
 __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsigned char* sm, float2* PP,
                                           unsigned long long* mbar, uint32_t parity, int x0, int y0) {
     using T = Traits<ST>;
@@ -443,6 +452,10 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     const int tx = t % TX, ty = t / TX;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = (x < p.nx) && (y < p.ny);
+    // mass flux of the previous step (density ratio != 1 only; the own cell's, read early so that
+    // its latency overlaps the stencil work)
+    float2 Sp = make_float2(0.f, 0.f);
+    if (FLOW == kFlowVarRho && !io.first && active) Sp = io.shist_src[p.org + (long long)y * p.pitch + x];
     // (phi, psi) references of the stored deviations (zero for FP32 storage)
     const float2 ref = T::kPair16 ? make_float2(p.phi_ref, 0.f) : make_float2(0.f, 0.f);
 
@@ -544,11 +557,21 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         sigma = p.sigma0 * (1.f - p.E0 * psi);
         dsig = -p.sigma0 * p.E0;
     }
+    // density (Sec. 2.3): rho(phi), its gradient by the chain rule, and the mass flux S
+    constexpr bool var = FLOW == kFlowVarRho;
+    const float rho_v = var ? p.rhoB + (phi - p.phiB) * p.drho : 0.f;  // local density (ratio != 1)
+    float grx = 0.f, gry = 0.f, Sx = 0.f, Sy = 0.f;
+    if (var) {
+        grx = p.drho * gpx;
+        gry = p.drho * gpy;
+        Sx = p.sfac * (gpx - Aterm * nx_);
+        Sy = p.sfac * (gpy - Aterm * ny_);
+    }
     const float gsgx = dsig * gsx, gsgy = dsig * gsy;
     const float cap = p.cap_k * sigma * (p.c16W * dA * dB * sym - p.W * lap);
     const float sdg = gsgx * gpx + gsgy * gpy;
-    const float Fx = cap * gpx + p.mar_k * (g2 * gsgx - sdg * gpx) + p.rho * p.gx;
-    const float Fy = cap * gpy + p.mar_k * (g2 * gsgy - sdg * gpy) + p.rho * p.gy;
+    const float Fx = cap * gpx + p.mar_k * (g2 * gsgx - sdg * gpx) + (var ? rho_v : p.rho) * p.gx;
+    const float Fy = cap * gpy + p.mar_k * (g2 * gsgy - sdg * gpy) + (var ? rho_v : p.rho) * p.gy;
 
     // own u of the previous level (also the encoding velocity of the own slots across a wall)
     const float2 uown = S::kHalo ? Hist[(ty + 1) * BW + tx + 4] : Hist[ty * TX + tx];
@@ -572,8 +595,9 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     const float h13 = h[1] - h[3], h24 = h[2] - h[4], h57 = h[5] - h[7], h68 = h[6] - h[8];
     const float jx = h13 + (h57 - h68);
     const float jy = h24 + (h57 + h68);
-    const float ux = FLOW ? (jx + 0.5f * Fx) * p.inv_rho : uown.x;
-    const float uy = FLOW ? (jy + 0.5f * Fy) * p.inv_rho : uown.y;
+    const float inv_rho = var ? __frcp_rn(rho_v) : p.inv_rho;
+    const float ux = FLOW ? (jx + 0.5f * Fx) * inv_rho : uown.x;
+    const float uy = FLOW ? (jy + 0.5f * Fy) * inv_rho : uown.y;
 
     // previous level: (phi, psi) from the own cell's post-collision pairs, u from history
     float2 pprev = pp;
@@ -595,18 +619,36 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         uyp = uown.y;
     }
 
-    // time derivatives, backward difference over one step: d_t(phi u), d_t(psi u) as pairs
-    const float rho = p.rho;
+    // time derivatives, backward difference over one step: d_t(phi u), d_t(psi u) as pairs, and
+    // d_t(rho u u - (S u + u S)/2) (Sec. 3.3)
+    const float rho = var ? rho_v : p.rho;
     const float2 dtX = fma2(pp, bc(ux), mul2(pprev, bc(-uxp)));
     const float2 dtY = fma2(pp, bc(uy), mul2(pprev, bc(-uyp)));
-    const float dt_xx = rho * (ux * ux - uxp * uxp);
-    const float dt_yy = rho * (uy * uy - uyp * uyp);
-    const float dt_xy = rho * (ux * uy - uxp * uyp);
+    float dt_xx, dt_yy, dt_xy, ugr = 0.f;
+    if (!var) {
+        dt_xx = rho * (ux * ux - uxp * uxp);
+        dt_yy = rho * (uy * uy - uyp * uyp);
+        dt_xy = rho * (ux * uy - uxp * uyp);
+    } else {
+        const float rp = p.rhoB + (pprev.x - p.phiB) * p.drho;  // rho of the previous level
+        const float Sxp = io.first ? Sx : Sp.x, Syp = io.first ? Sy : Sp.y;
+        dt_xx = (rho * ux - Sx) * ux - (rp * uxp - Sxp) * uxp;
+        dt_yy = (rho * uy - Sy) * uy - (rp * uyp - Syp) * uyp;
+        dt_xy = (rho * ux * uy - 0.5f * (Sx * uy + ux * Sy)) - (rp * uxp * uyp - 0.5f * (Sxp * uyp + uxp * Syp));
+        ugr = ux * grx + uy * gry;
+    }
 
     // pressure (Eq. for P, Sec. 3.3) with K = w0/(c^2 - cs2) = 2/3:
-    //   P = 3/5 [sum_{i>0} h_i - (2/3) rho |u|^2 + (1/3) d_t(rho |u|^2)]
+    //   P = 3/5 [sum_{i>0} h_i + u.grad rho / 2 - (2/3) (rho u - S).u + (1/3) d_t(rho u.u - S.u)]
     const float hsum = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
-    const float P_ = FLOW ? 0.6f * (hsum - (2.f / 3.f) * rho * (ux * ux + uy * uy) + (1.f / 3.f) * (dt_xx + dt_yy)) : 0.f;
+    float P_ = 0.f;
+    if (FLOW) {
+        if (!var)
+            P_ = 0.6f * (hsum - (2.f / 3.f) * rho * (ux * ux + uy * uy) + (1.f / 3.f) * (dt_xx + dt_yy));
+        else
+            P_ = 0.6f * (hsum + 0.5f * ugr - (2.f / 3.f) * ((rho * ux - Sx) * ux + (rho * uy - Sy) * uy) +
+                         (1.f / 3.f) * (dt_xx + dt_yy));
+    }
 
     {
         // |u| >= 0.3, or a non-finite value (NaN fails every comparison; a NaN anywhere in the
@@ -655,33 +697,53 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         // ---- flow h (Sec. 3.3); none when the velocity is prescribed ----
         if constexpr (FLOW) {
             float s2, k2, s4, k4;
-            if (p.dmu == 0.f) {
+            if (p.dmu == 0.f && !var) {
                 s2 = p.s2h;
                 k2 = p.k2h;
                 s4 = p.s4h_eff;
                 k4 = p.k4h;
             } else {
-                s2 = __frcp_rn(3.f * (p.muB + (phi - p.phiB) * p.inv_dphi * p.dmu) * p.inv_rho + 0.5f);
+                s2 = __frcp_rn(3.f * (p.muB + (phi - p.phiB) * p.inv_dphi * p.dmu) * (var ? inv_rho : p.inv_rho) + 0.5f);
                 k2 = 1.f - 0.5f * s2;
                 s4 = p.tie_s4h ? s2 : p.s4h;
                 k4 = 1.f - 0.5f * s4;
             }
             const float s1 = p.s1h, s3 = p.s3h, k1 = p.k1h, k3 = p.k3h;
             const float Jx = rho * ux, Jy = rho * uy;
-            // equilibrium moments: (., Jx, Jy, P + Jx ux, P + Jy uy, Jx uy, Jx/3, Jy/3, P/3 + J.u/3)
-            // source moments:      (., Fx, Fy, dt_xx, dt_yy, dt_xy, Fx/3, Fy/3, (dt_xx + dt_yy)/3)
+            // equilibrium moments, Q = (rho u - S) u:
+            //   (., Jx, Jy, P + Q_xx, P + Q_yy, (Q_xy + Q_yx)/2, Jx/3, Jy/3, P/3 + (Q_xx + Q_yy)/3)
+            // source moments of H, m2H = d_t(rho u u - (S u + u S)/2) + cs2 (u grad rho + grad rho u):
+            //   (., Fx, Fy, m2H_xx + u.grad rho/3, m2H_yy + u.grad rho/3, m2H_xy, Fx/3, Fy/3,
+            //    (m2H_xx + m2H_yy)/3 + u.grad rho/9)
             const float ha = h[5] + h[7], hb = h[6] + h[8];
             const float m5 = ha - hb, m8 = ha + hb, m6 = h57 - h68, m7 = h57 + h68;
             const float m3 = (h[1] + h[3]) + m8, m4 = (h[2] + h[4]) + m8;
             // increments dm_k = -s_k (m_k - m_eq_k) + (1 - s_k/2) m_src_k, then h* = h + M^-1 dm
             const float d1 = k1 * Fx - s1 * (jx - Jx);
             const float d2 = k1 * Fy - s1 * (jy - Jy);
-            const float d3 = k2 * dt_xx - s2 * (m3 - (P_ + Jx * ux));
-            const float d4 = k2 * dt_yy - s2 * (m4 - (P_ + Jy * uy));
-            const float d5 = k2 * dt_xy - s2 * (m5 - Jx * uy);
+            float d3, d4, d5, d8;
+            float qxx = 0.f, qyy = 0.f, mxx = 0.f, myy = 0.f;
+            if constexpr (!var) {
+                d3 = k2 * dt_xx - s2 * (m3 - (P_ + Jx * ux));
+                d4 = k2 * dt_yy - s2 * (m4 - (P_ + Jy * uy));
+                d5 = k2 * dt_xy - s2 * (m5 - Jx * uy);
+            } else {
+                qxx = (Jx - Sx) * ux;
+                qyy = (Jy - Sy) * uy;
+                const float qxy = Jx * uy - 0.5f * (Sx * uy + Sy * ux);
+                mxx = dt_xx + (2.f / 3.f) * ux * grx;
+                myy = dt_yy + (2.f / 3.f) * uy * gry;
+                const float mxy = dt_xy + (1.f / 3.f) * (ux * gry + uy * grx);
+                d3 = k2 * (mxx + (1.f / 3.f) * ugr) - s2 * (m3 - (P_ + qxx));
+                d4 = k2 * (myy + (1.f / 3.f) * ugr) - s2 * (m4 - (P_ + qyy));
+                d5 = k2 * mxy - s2 * (m5 - qxy);
+            }
             const float d6 = (1.f / 3.f) * (k3 * Fx - s3 * (3.f * m6 - Jx));
             const float d7 = (1.f / 3.f) * (k3 * Fy - s3 * (3.f * m7 - Jy));
-            const float d8 = (1.f / 3.f) * (k4 * (dt_xx + dt_yy) - s4 * (3.f * m8 - (P_ + Jx * ux + Jy * uy)));
+            if constexpr (!var)
+                d8 = (1.f / 3.f) * (k4 * (dt_xx + dt_yy) - s4 * (3.f * m8 - (P_ + Jx * ux + Jy * uy)));
+            else  // 3 x the eighth source moment (mxx + myy)/3 + u.grad rho/9
+                d8 = (1.f / 3.f) * (k4 * ((mxx + myy) + (1.f / 3.f) * ugr) - s4 * (3.f * m8 - (P_ + qxx + qyy)));
             const float A = d1 - d6, B = d3 - d8, C = d2 - d7, D = d4 - d8;
             const float E = d8 + d5, F = d8 - d5, G = d6 + d7, H = d7 - d6;
             h[1] += 0.5f * (A + B);
@@ -785,6 +847,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         }
         const float2 un = make_float2(ux, uy);
         io.hist_dst[cell] = un;
+        if (var) io.shist_dst[cell] = make_float2(Sx, Sy);
         if constexpr (S::kHalo) {
             // the 16-bit h decode reads the neighbours' u, across periodic edges too
             if (xl) io.hist_dst[cell + DX] = un;
@@ -805,7 +868,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
 }
 
 // One step (or the moments) of one lattice: one TX x TY tile per CTA.
-template <int ST, bool WALLS, bool LANGMUIR, int MODE, bool FLOW>
+template <int ST, bool WALLS, bool LANGMUIR, int MODE, int FLOW>
 __global__ void __launch_bounds__(NT, 4) step_kernel(const __grid_constant__ StepArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + Smem<ST>::BAR);
@@ -841,7 +904,7 @@ __device__ __forceinline__ void tile_origin(int k, int ntx, int nty, int& x0, in
 // current one, so the copy latency hides behind the arithmetic.  Claiming tiles one at a time
 // balances the longer edge tiles (ghost-frame writes) across the CTAs.  Thread 0 claims a tile one iteration before
 // it needs it, so the atomic's latency also hides behind a tile's work.
-template <int ST, bool WALLS, bool LANGMUIR, bool FLOW>
+template <int ST, bool WALLS, bool LANGMUIR, int FLOW>
 __global__ void __launch_bounds__(NT, 4) step_kernel_pipe(const __grid_constant__ StepArgs a, int ntx, int nty) {
     using S = Smem<ST>;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -906,6 +969,7 @@ struct alignas(64) InstDesc {
     Phys p;
     void* pops[2];
     float2* hist[2];
+    float2* shist[2];  // mass-flux history (density ratio != 1), else null
     unsigned* status;
     long long steps;
     int cur;
@@ -920,7 +984,7 @@ struct BatchArgs {
     int s;
 };
 
-template <int ST, bool WALLS, bool LANGMUIR, bool FLOW>
+template <int ST, bool WALLS, bool LANGMUIR, int FLOW>
 __global__ void __launch_bounds__(NT, 4) batch_step_kernel(const __grid_constant__ BatchArgs b) {
     using S = Smem<ST>;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -946,6 +1010,8 @@ __global__ void __launch_bounds__(NT, 4) batch_step_kernel(const __grid_constant
     io.dst = d.pops[cur ^ 1];
     io.hist_src = d.hist[cur];
     io.hist_dst = d.hist[cur ^ 1];
+    io.shist_src = d.shist[cur];
+    io.shist_dst = d.shist[cur ^ 1];
     io.status = d.status;
     io.out[0] = io.out[1] = io.out[2] = io.out[3] = io.out[4] = nullptr;
     io.seed = step_seed(d.steps + b.s);
@@ -992,7 +1058,8 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
     bool bad = !(isfinite(phi) && isfinite(psi) && isfinite(ux) && isfinite(uy) && isfinite(P_));
     if (a.langmuir) bad = bad || !(psi < 1.0);
     if (bad) atomicOr(a.status, kStatusUnstable);
-    const double rho = p.rho;
+    // local density (the equilibrium is taken without the mass-flux terms, S = 0)
+    const double rho = p.var_rho ? (double)p.rhoB + (phi - (double)p.phiB) * (double)p.drho : (double)p.rho;
     const double uu = ux * ux + uy * uy;
     P* fg = static_cast<P*>(a.dst);
     Hv* hp = reinterpret_cast<Hv*>(fg + (size_t)kPairs * p.plane);

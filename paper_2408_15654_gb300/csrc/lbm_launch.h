@@ -1,8 +1,8 @@
 // Launch helpers of the step kernels, one translation unit per storage mode
 // (step_fp32.cu, step_fp16.cu, step_bf16.cu, step_fp16fg.cu, step_bf16fg.cu) so that the
-// instances compile in parallel.  Each storage mode has six kernel variants: walls or periodic y,
-// Langmuir or linear EOS with the flow solved, and walls or periodic y with the velocity
-// prescribed (no flow populations; the EOS is not used there).
+// instances compile in parallel.  Each storage mode has ten kernel variants: walls or periodic y
+// and Langmuir or linear EOS with the flow solved at uniform density or with a density ratio, and
+// walls or periodic y with the velocity prescribed (no flow populations; the EOS is unused).
 #pragma once
 #include <cstring>
 
@@ -12,21 +12,35 @@ namespace lbm {
 
 // Runtime flags of a launch, mapped to the kernel variant.
 struct Variant {
-    bool walls, langmuir, flow;
+    bool walls, langmuir, flow, var_rho;
 };
 
-// Calls f.template operator()<WALLS, LANGMUIR, FLOW>() for the variant's template arguments.
+// Calls f.template operator()<WALLS, LANGMUIR, FLOW>() for the variant's template arguments (the
+// EOS is unused with a prescribed velocity).
 template <typename F>
 cudaError_t dispatch_variant(const Variant& v, F&& f) {
-    if (v.flow) {
-        if (v.walls && v.langmuir) return f.template operator()<true, true, true>();
-        if (v.walls) return f.template operator()<true, false, true>();
-        if (v.langmuir) return f.template operator()<false, true, true>();
-        return f.template operator()<false, false, true>();
+    if (v.flow && v.var_rho) {
+        if (v.walls && v.langmuir) return f.template operator()<true, true, kFlowVarRho>();
+        if (v.walls) return f.template operator()<true, false, kFlowVarRho>();
+        if (v.langmuir) return f.template operator()<false, true, kFlowVarRho>();
+        return f.template operator()<false, false, kFlowVarRho>();
     }
-    if (v.walls) return f.template operator()<true, false, false>();
-    return f.template operator()<false, false, false>();
+    if (v.flow) {
+        if (v.walls && v.langmuir) return f.template operator()<true, true, kFlowUniform>();
+        if (v.walls) return f.template operator()<true, false, kFlowUniform>();
+        if (v.langmuir) return f.template operator()<false, true, kFlowUniform>();
+        return f.template operator()<false, false, kFlowUniform>();
+    }
+    if (v.walls) return f.template operator()<true, false, kFlowPrescribed>();
+    return f.template operator()<false, false, kFlowPrescribed>();
 }
+
+// The ten variants, for set-up loops.
+inline Variant variant_of(int k) {
+    if (k < 8) return Variant{(k & 1) != 0, (k & 2) != 0, true, k >= 4};
+    return Variant{k == 8, false, false, false};
+}
+constexpr int kVariants = 10;
 
 inline cudaLaunchConfig_t pdl_config(dim3 grid, size_t smem, cudaStream_t stream, cudaLaunchAttribute* attr) {
     // Every launch uses programmatic dependent launch: the kernel waits (griddepcontrol.wait) for
@@ -54,12 +68,12 @@ cudaError_t launch_step_impl(const StepArgs& a, int mode, const Variant& v, dim3
     if (mode == kStep && pipe_ctas > 0) {
         const int ntx = (int)grid.x, nty = (int)grid.y;
         cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)pipe_ctas), Smem<ST>::BYTES_PIPE, stream, attr);
-        return dispatch_variant(v, [&]<bool W, bool L, bool F>() {
+        return dispatch_variant(v, [&]<bool W, bool L, int F>() {
             return cudaLaunchKernelEx(&cfg, step_kernel_pipe<ST, W, L, F>, a, ntx, nty);
         });
     }
     cudaLaunchConfig_t cfg = pdl_config(grid, Smem<ST>::BYTES, stream, attr);
-    return dispatch_variant(v, [&]<bool W, bool L, bool F>() {
+    return dispatch_variant(v, [&]<bool W, bool L, int F>() {
         if (mode == kStep) return cudaLaunchKernelEx(&cfg, step_kernel<ST, W, L, kStep, F>, a);
         return cudaLaunchKernelEx(&cfg, step_kernel<ST, W, L, kMoments, F>, a);
     });
@@ -70,7 +84,7 @@ cudaError_t launch_step_impl(const StepArgs& a, int mode, const Variant& v, dim3
 template <int ST>
 cudaError_t prepare_step_impl(int* blocks_per_sm, int* pipe_blocks_per_sm) {
     int tile = 1 << 30, pipe = 1 << 30;
-    auto one = [&]<bool W, bool L, bool F>() -> cudaError_t {
+    auto one = [&]<bool W, bool L, int F>() -> cudaError_t {
         int b = 0;
         auto k0 = step_kernel<ST, W, L, kStep, F>;
         auto k1 = step_kernel<ST, W, L, kMoments, F>;
@@ -88,10 +102,7 @@ cudaError_t prepare_step_impl(int* blocks_per_sm, int* pipe_blocks_per_sm) {
         return e;
     };
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
-        const Variant v{k == 0 || k == 1 || k == 4, k == 0 || k == 2, k < 4};
-        e = dispatch_variant(v, one);
-    }
+    for (int k = 0; k < kVariants && e == cudaSuccess; ++k) e = dispatch_variant(variant_of(k), one);
     *blocks_per_sm = tile;
     *pipe_blocks_per_sm = pipe;
     return e;
@@ -102,7 +113,7 @@ template <int ST>
 cudaError_t launch_batch_impl(const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t stream) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = pdl_config(dim3(ntiles), Smem<ST>::BYTES_BATCH, stream, attr);
-    return dispatch_variant(v, [&]<bool W, bool L, bool F>() {
+    return dispatch_variant(v, [&]<bool W, bool L, int F>() {
         return cudaLaunchKernelEx(&cfg, batch_step_kernel<ST, W, L, F>, b);
     });
 }
@@ -110,9 +121,8 @@ cudaError_t launch_batch_impl(const BatchArgs& b, const Variant& v, unsigned nti
 template <int ST>
 cudaError_t prepare_batch_impl() {
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
-        const Variant v{k == 0 || k == 1 || k == 4, k == 0 || k == 2, k < 4};
-        e = dispatch_variant(v, [&]<bool W, bool L, bool F>() {
+    for (int k = 0; k < kVariants && e == cudaSuccess; ++k) {
+        e = dispatch_variant(variant_of(k), [&]<bool W, bool L, int F>() {
             return cudaFuncSetAttribute(batch_step_kernel<ST, W, L, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         Smem<ST>::BYTES_BATCH);
         });

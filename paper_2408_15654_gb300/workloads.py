@@ -18,6 +18,8 @@ Workloads (stand-ins for the paper's Sec. 4 benchmarks; the paper's comparison d
   convected_drop     a drop carried by an imposed uniform velocity (prescribed-velocity mode):
                      the convection test of Sec. 4 (100 x 100, R = 20, u = (0.05, 0), psi = phi,
                      M_phi = 1, D = 2 in lattice units)
+  rising_bubble      the single rising bubble of Sec. 4 (density and viscosity ratio 10, Re = 35,
+                     Pe = 10, Bo = 10, linear EOS)
   batch_instances    64 seeded drops of mixed sizes for the batched launch
   serving_requests   a seeded Poisson stream of sheared-drop jobs of mixed sizes, step counts and
                      storage modes, for the lattice server
@@ -99,6 +101,24 @@ def surface_diffusion(n=256, R=60.0, W=4.0, D=0.05, M_phi=0.05):
     theta = polar_angle(n, n)
     psi = 0.5 * (1.0 + np.cos(theta)) * interface_weight(phi)
     return p, fields(phi, psi)
+
+
+def rising_bubble(R=60.0, W=4.0, E0=0.5, psi0=1.0, Re=35.0, Pe=10.0, Bo=10.0, M_phi=0.05):
+    """Single rising bubble (Sec. 4): a bubble of fluid B (phi = phiB = 0; rhoB = rhoA/10,
+    muB = muA/10) of radius R at (2R, 2R) in a 4R x 8R box, walls at rest below and above, periodic
+    in x, gravity -y, linear EOS, psi = psi0 sech^2 on the interface.  Lattice units with the
+    paper's diffusive scaling dt = dx^2 at dx = 0.25/R: the velocity scale sqrt(2 g R) = 0.7 (in
+    the paper's units) becomes 0.175/R, and mu_A, sigma0 and D follow from Re, Bo and Pe.  The
+    phase-field mobility is not given; M_phi = 0.05 as for the other workloads."""
+    nx, ny = int(round(4 * R)), int(round(8 * R))
+    U = 0.175 / R
+    g = U * U / (2.0 * R)
+    muA = 2.0 * R * U / Re
+    sigma0 = 4.0 * g * R * R / Bo
+    p = base_params(nx, ny, walls=True, rhoA=1.0, rhoB=0.1, muA=muA, muB=0.1 * muA, sigma0=sigma0,
+                    E0=E0, eos="linear", gy=-g, W=W, M_phi=M_phi, D=2.0 * R * U / Pe)
+    phi = 1.0 - drop_phi(nx, ny, R, W, xc=nx / 2.0 - 0.5, yc=2.0 * R - 0.5)  # walls at y = -1/2, ny - 1/2
+    return p, fields(phi, psi0 * interface_weight(phi))
 
 
 def convected_drop(nx=100, ny=100, R=20.0, W=4.0, u=(0.05, 0.0), M_phi=1.0, D=2.0):

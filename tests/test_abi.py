@@ -76,7 +76,7 @@ def test_prescribed_velocity_workspace_has_no_flow_planes():
     assert full - pres == 2 * 8 * 4 * 260 * 544
 
 
-@pytest.mark.parametrize("bad", [dict(nx=1), dict(ny=0), dict(rhoA=2.0), dict(W=0.0), dict(M_phi=-1.0),
+@pytest.mark.parametrize("bad", [dict(nx=1), dict(ny=0), dict(rhoB=0.0), dict(W=0.0), dict(M_phi=-1.0),
                                  dict(D=0.0), dict(muA=0.0), dict(s_f=(1, 1, 2.5, 1, 1)),
                                  dict(sigma0=float("nan")), dict(storage=7),
                                  dict(velocity=2)])
@@ -95,3 +95,11 @@ def test_calls_reject_null_handle():
     assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
     assert lib.lbm_reduce(None, 0, None) == lbm.LBM_EINVAL
     assert lib.lbm_destroy(None) == lbm.LBM_OK
+
+
+def test_density_ratio_workspace_has_a_mass_flux_history():
+    p, _ = W.rising_bubble(16.0)
+    var = lbm.lbm_workspace_bytes(lbm.make_params(p))
+    uni = lbm.lbm_workspace_bytes(lbm.make_params(dict(p, rhoB=p["rhoA"])))
+    pitch, rows = (64 + 10 + 31) // 32 * 32, 128 + 4
+    assert var - uni == 2 * ((pitch * rows * 8 + 255) // 256 * 256)
