@@ -240,6 +240,13 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// explicitly rounded scalar arithmetic (never contracted): the density-ratio terms are written
+// with these, so that every kernel instantiating them rounds in the one order written here
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 // ---- storage conversions ----
 __device__ __forceinline__ float2 raw2(float2 v) { return v; }
 __device__ __forceinline__ float2 raw2(__half2 v) { return __half22float2(v); }
@@ -559,19 +566,25 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     }
     // density (Sec. 2.3): rho(phi), its gradient by the chain rule, and the mass flux S
     constexpr bool var = FLOW == kFlowVarRho;
-    const float rho_v = var ? p.rhoB + (phi - p.phiB) * p.drho : 0.f;  // local density (ratio != 1)
+    const float rho_v = var ? rfma(rsub(phi, p.phiB), p.drho, p.rhoB) : 0.f;  // local density (ratio != 1)
     float grx = 0.f, gry = 0.f, Sx = 0.f, Sy = 0.f;
     if (var) {
-        grx = p.drho * gpx;
-        gry = p.drho * gpy;
-        Sx = p.sfac * (gpx - Aterm * nx_);
-        Sy = p.sfac * (gpy - Aterm * ny_);
+        grx = rmul(p.drho, gpx);
+        gry = rmul(p.drho, gpy);
+        Sx = rmul(p.sfac, rfma(-Aterm, nx_, gpx));
+        Sy = rmul(p.sfac, rfma(-Aterm, ny_, gpy));
     }
     const float gsgx = dsig * gsx, gsgy = dsig * gsy;
     const float cap = p.cap_k * sigma * (p.c16W * dA * dB * sym - p.W * lap);
     const float sdg = gsgx * gpx + gsgy * gpy;
-    const float Fx = cap * gpx + p.mar_k * (g2 * gsgx - sdg * gpx) + (var ? rho_v : p.rho) * p.gx;
-    const float Fy = cap * gpy + p.mar_k * (g2 * gsgy - sdg * gpy) + (var ? rho_v : p.rho) * p.gy;
+    float Fx, Fy;
+    if constexpr (!var) {
+        Fx = cap * gpx + p.mar_k * (g2 * gsgx - sdg * gpx) + p.rho * p.gx;
+        Fy = cap * gpy + p.mar_k * (g2 * gsgy - sdg * gpy) + p.rho * p.gy;
+    } else {
+        Fx = rfma(rho_v, p.gx, rfma(cap, gpx, rmul(p.mar_k, rfma(g2, gsgx, -rmul(sdg, gpx)))));
+        Fy = rfma(rho_v, p.gy, rfma(cap, gpy, rmul(p.mar_k, rfma(g2, gsgy, -rmul(sdg, gpy)))));
+    }
 
     // own u of the previous level (also the encoding velocity of the own slots across a wall)
     const float2 uown = S::kHalo ? Hist[(ty + 1) * BW + tx + 4] : Hist[ty * TX + tx];
@@ -625,17 +638,25 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     const float2 dtX = fma2(pp, bc(ux), mul2(pprev, bc(-uxp)));
     const float2 dtY = fma2(pp, bc(uy), mul2(pprev, bc(-uyp)));
     float dt_xx, dt_yy, dt_xy, ugr = 0.f;
+    // Q = (rho u - S) u of this level (density ratio only): diagonal and symmetrised off-diagonal
+    float Jx = 0.f, Jy = 0.f, qxx = 0.f, qyy = 0.f, qxy = 0.f;
     if (!var) {
         dt_xx = rho * (ux * ux - uxp * uxp);
         dt_yy = rho * (uy * uy - uyp * uyp);
         dt_xy = rho * (ux * uy - uxp * uyp);
     } else {
-        const float rp = p.rhoB + (pprev.x - p.phiB) * p.drho;  // rho of the previous level
+        Jx = rmul(rho, ux);
+        Jy = rmul(rho, uy);
+        qxx = rmul(rsub(Jx, Sx), ux);
+        qyy = rmul(rsub(Jy, Sy), uy);
+        qxy = rfma(Jx, uy, -rmul(0.5f, rfma(Sx, uy, rmul(Sy, ux))));
+        const float rp = rfma(rsub(pprev.x, p.phiB), p.drho, p.rhoB);  // rho of the previous level
         const float Sxp = io.first ? Sx : Sp.x, Syp = io.first ? Sy : Sp.y;
-        dt_xx = (rho * ux - Sx) * ux - (rp * uxp - Sxp) * uxp;
-        dt_yy = (rho * uy - Sy) * uy - (rp * uyp - Syp) * uyp;
-        dt_xy = (rho * ux * uy - 0.5f * (Sx * uy + ux * Sy)) - (rp * uxp * uyp - 0.5f * (Sxp * uyp + uxp * Syp));
-        ugr = ux * grx + uy * gry;
+        const float Jxp = rmul(rp, uxp), Jyp = rmul(rp, uyp);
+        dt_xx = rsub(qxx, rmul(rsub(Jxp, Sxp), uxp));
+        dt_yy = rsub(qyy, rmul(rsub(Jyp, Syp), uyp));
+        dt_xy = rsub(qxy, rfma(Jxp, uyp, -rmul(0.5f, rfma(Sxp, uyp, rmul(Syp, uxp)))));
+        ugr = rfma(ux, grx, rmul(uy, gry));
     }
 
     // pressure (Eq. for P, Sec. 3.3) with K = w0/(c^2 - cs2) = 2/3:
@@ -646,8 +667,8 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         if (!var)
             P_ = 0.6f * (hsum - (2.f / 3.f) * rho * (ux * ux + uy * uy) + (1.f / 3.f) * (dt_xx + dt_yy));
         else
-            P_ = 0.6f * (hsum + 0.5f * ugr - (2.f / 3.f) * ((rho * ux - Sx) * ux + (rho * uy - Sy) * uy) +
-                         (1.f / 3.f) * (dt_xx + dt_yy));
+            P_ = rmul(0.6f, rfma(1.f / 3.f, radd(dt_xx, dt_yy),
+                                 rfma(-2.f / 3.f, radd(qxx, qyy), rfma(0.5f, ugr, hsum))));
     }
 
     {
@@ -703,13 +724,19 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
                 s4 = p.s4h_eff;
                 k4 = p.k4h;
             } else {
-                s2 = __frcp_rn(3.f * (p.muB + (phi - p.phiB) * p.inv_dphi * p.dmu) * (var ? inv_rho : p.inv_rho) + 0.5f);
+                if constexpr (!var)
+                    s2 = __frcp_rn(3.f * (p.muB + (phi - p.phiB) * p.inv_dphi * p.dmu) * p.inv_rho + 0.5f);
+                else  // nu = mu(phi) / rho(phi)
+                    s2 = __frcp_rn(rfma(rmul(3.f, rfma(rmul(rsub(phi, p.phiB), p.inv_dphi), p.dmu, p.muB)), inv_rho, 0.5f));
                 k2 = 1.f - 0.5f * s2;
                 s4 = p.tie_s4h ? s2 : p.s4h;
                 k4 = 1.f - 0.5f * s4;
             }
             const float s1 = p.s1h, s3 = p.s3h, k1 = p.k1h, k3 = p.k3h;
-            const float Jx = rho * ux, Jy = rho * uy;
+            if constexpr (!var) {
+                Jx = rho * ux;
+                Jy = rho * uy;
+            }
             // equilibrium moments, Q = (rho u - S) u:
             //   (., Jx, Jy, P + Q_xx, P + Q_yy, (Q_xy + Q_yx)/2, Jx/3, Jy/3, P/3 + (Q_xx + Q_yy)/3)
             // source moments of H, m2H = d_t(rho u u - (S u + u S)/2) + cs2 (u grad rho + grad rho u):
@@ -719,31 +746,31 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
             const float m5 = ha - hb, m8 = ha + hb, m6 = h57 - h68, m7 = h57 + h68;
             const float m3 = (h[1] + h[3]) + m8, m4 = (h[2] + h[4]) + m8;
             // increments dm_k = -s_k (m_k - m_eq_k) + (1 - s_k/2) m_src_k, then h* = h + M^-1 dm
-            const float d1 = k1 * Fx - s1 * (jx - Jx);
-            const float d2 = k1 * Fy - s1 * (jy - Jy);
+            const float d1 = var ? rfma(k1, Fx, -rmul(s1, rsub(jx, Jx))) : k1 * Fx - s1 * (jx - Jx);
+            const float d2 = var ? rfma(k1, Fy, -rmul(s1, rsub(jy, Jy))) : k1 * Fy - s1 * (jy - Jy);
             float d3, d4, d5, d8;
-            float qxx = 0.f, qyy = 0.f, mxx = 0.f, myy = 0.f;
+            float mxx = 0.f, myy = 0.f;
             if constexpr (!var) {
                 d3 = k2 * dt_xx - s2 * (m3 - (P_ + Jx * ux));
                 d4 = k2 * dt_yy - s2 * (m4 - (P_ + Jy * uy));
                 d5 = k2 * dt_xy - s2 * (m5 - Jx * uy);
             } else {
-                qxx = (Jx - Sx) * ux;
-                qyy = (Jy - Sy) * uy;
-                const float qxy = Jx * uy - 0.5f * (Sx * uy + Sy * ux);
-                mxx = dt_xx + (2.f / 3.f) * ux * grx;
-                myy = dt_yy + (2.f / 3.f) * uy * gry;
-                const float mxy = dt_xy + (1.f / 3.f) * (ux * gry + uy * grx);
-                d3 = k2 * (mxx + (1.f / 3.f) * ugr) - s2 * (m3 - (P_ + qxx));
-                d4 = k2 * (myy + (1.f / 3.f) * ugr) - s2 * (m4 - (P_ + qyy));
-                d5 = k2 * mxy - s2 * (m5 - qxy);
+                mxx = rfma(2.f / 3.f, rmul(ux, grx), dt_xx);
+                myy = rfma(2.f / 3.f, rmul(uy, gry), dt_yy);
+                const float mxy = rfma(1.f / 3.f, rfma(ux, gry, rmul(uy, grx)), dt_xy);
+                d3 = rfma(k2, rfma(1.f / 3.f, ugr, mxx), -rmul(s2, rsub(m3, radd(P_, qxx))));
+                d4 = rfma(k2, rfma(1.f / 3.f, ugr, myy), -rmul(s2, rsub(m4, radd(P_, qyy))));
+                d5 = rfma(k2, mxy, -rmul(s2, rsub(m5, qxy)));
             }
-            const float d6 = (1.f / 3.f) * (k3 * Fx - s3 * (3.f * m6 - Jx));
-            const float d7 = (1.f / 3.f) * (k3 * Fy - s3 * (3.f * m7 - Jy));
+            const float d6 = var ? rmul(1.f / 3.f, rfma(k3, Fx, -rmul(s3, rfma(3.f, m6, -Jx))))
+                                 : (1.f / 3.f) * (k3 * Fx - s3 * (3.f * m6 - Jx));
+            const float d7 = var ? rmul(1.f / 3.f, rfma(k3, Fy, -rmul(s3, rfma(3.f, m7, -Jy))))
+                                 : (1.f / 3.f) * (k3 * Fy - s3 * (3.f * m7 - Jy));
             if constexpr (!var)
                 d8 = (1.f / 3.f) * (k4 * (dt_xx + dt_yy) - s4 * (3.f * m8 - (P_ + Jx * ux + Jy * uy)));
             else  // 3 x the eighth source moment (mxx + myy)/3 + u.grad rho/9
-                d8 = (1.f / 3.f) * (k4 * ((mxx + myy) + (1.f / 3.f) * ugr) - s4 * (3.f * m8 - (P_ + qxx + qyy)));
+                d8 = rmul(1.f / 3.f, rfma(k4, rfma(1.f / 3.f, ugr, radd(mxx, myy)),
+                                          -rmul(s4, rfma(3.f, m8, -radd(P_, radd(qxx, qyy))))));
             const float A = d1 - d6, B = d3 - d8, C = d2 - d7, D = d4 - d8;
             const float E = d8 + d5, F = d8 - d5, G = d6 + d7, H = d7 - d6;
             h[1] += 0.5f * (A + B);
