@@ -39,6 +39,15 @@ _FLOW_RATES = (1.0, 1.0, 1.0, 1.0, 0.0)
 
 
 def base_params(nx: int, ny: int, **kw) -> dict:
+    """Defaults of every workload.  The unit normal n = grad phi / |grad phi| is taken wherever
+    |grad phi| > n_eps = 1e-12, that is wherever grad phi is not zero, as the paper defines it.
+    In single precision that makes some workloads sensitive to rounding: in a nearly flat bulk
+    grad phi is itself of rounding size (about 1e-7 for phi of order 1) and its direction, which
+    steers the sharpening terms A n and B n, flips from step to step.  Measured with the FP64
+    oracle, a 6e-8 relative jitter of the initial fields moves phi by 1e-5 and psi by 2e-5
+    (relative L2) in 3000 steps of a 256 x 128 sheared drop with n_eps = 1e-12, by 3e-9 and 1e-8
+    with n_eps = 1e-4.  A larger threshold is no default: with n = 0 in the bulk, surfactant there
+    is no longer swept onto the interface (Sec. 2.2)."""
     p = dict(
         nx=int(nx), ny=int(ny), walls=False, eos="linear", u_top=0.0, u_bot=0.0,
         phiA=1.0, phiB=0.0, rhoA=1.0, rhoB=1.0, muA=0.1, muB=0.1,
@@ -103,25 +112,23 @@ def surface_diffusion(n=256, R=60.0, W=4.0, D=0.05, M_phi=0.05):
     return p, fields(phi, psi)
 
 
-def rising_bubble(R=60.0, W=4.0, E0=0.5, psi0=1.0, Re=35.0, Pe=10.0, Bo=10.0, M_phi=0.05, n_eps=1e-4):
+def rising_bubble(R=60.0, W=4.0, E0=0.5, psi0=1.0, Re=35.0, Pe=10.0, Bo=10.0, M_phi=0.05):
     """Single rising bubble (Sec. 4): a bubble of fluid B (phi = phiB = 0; rhoB = rhoA/10,
     muB = muA/10) of radius R at (2R, 2R) in a 4R x 8R box, walls at rest below and above, periodic
     in x, gravity -y, linear EOS, psi = psi0 sech^2 on the interface.  Lattice units with the
     paper's diffusive scaling dt = dx^2 at dx = 0.25/R: the velocity scale sqrt(2 g R) = 0.7 (in
     the paper's units) becomes 0.175/R, and mu_A, sigma0 and D follow from Re, Bo and Pe.  The
-    phase-field mobility is not given; M_phi = 0.05 as for the other workloads.  The unit normal is
-    taken only where |grad phi| > n_eps = 1e-4 (beyond about 4.6 cells from the interface centre at
-    W = 4 it is 0, where A n is below 1e-4 cA): in the nearly flat bulk the direction of grad phi is
-    set by rounding (about 1e-7 for phi of order 1 in single precision), and this gravity-driven flow
-    carries those flips into phi.  A 6e-8 relative jitter of the initial fields moves phi by 5e-5
-    (relative L2, 400 steps, R = 16) with n_eps = 1e-12, by 1-2e-5 with 1e-5, by 5e-9 with 1e-4."""
+    phase-field mobility is not given; M_phi = 0.05 as for the other workloads.  This flow is the
+    most sensitive to the normal threshold n_eps: a 6e-8 relative jitter of the initial fields
+    moves phi by 5e-5 (relative L2, 400 steps, R = 16) with the default n_eps = 1e-12, by 1-2e-5
+    with 1e-5 and by 5e-9 with 1e-4."""
     nx, ny = int(round(4 * R)), int(round(8 * R))
     U = 0.175 / R
     g = U * U / (2.0 * R)
     muA = 2.0 * R * U / Re
     sigma0 = 4.0 * g * R * R / Bo
     p = base_params(nx, ny, walls=True, rhoA=1.0, rhoB=0.1, muA=muA, muB=0.1 * muA, sigma0=sigma0,
-                    E0=E0, eos="linear", gy=-g, W=W, M_phi=M_phi, D=2.0 * R * U / Pe, n_eps=n_eps)
+                    E0=E0, eos="linear", gy=-g, W=W, M_phi=M_phi, D=2.0 * R * U / Pe)
     phi = 1.0 - drop_phi(nx, ny, R, W, xc=nx / 2.0 - 0.5, yc=2.0 * R - 0.5)  # walls at y = -1/2, ny - 1/2
     return p, fields(phi, psi0 * interface_weight(phi))
 

@@ -1,7 +1,10 @@
 """Write shear_drop_2048x1024_10000_samples.txt: the FP64 oracle's fields after 10000 steps of the
 2048 x 1024 sheared drop (Sec. 4.4 set-up: drop between walls moving at +/-U, R = 160, Re = 1,
 Ca = 0.2, Langmuir EOS E0 = 0.2, psi0 = 0.3), at seeded sample cells, plus the FP64 totals of phi
-and psi.  Calls only the oracle and the input generators.
+and psi.  Calls only the oracle and the input generators.  The unit normal is taken where
+|grad phi| > 1e-4 (N_EPS): with n wherever grad phi is not zero, the far-bulk normal of a
+single-precision run is set by rounding and 10000 steps would compare rounding histories, not
+implementations.
 
     python tests/golden/make_shear_drop_2048x1024_samples.py [threads]
 
@@ -19,6 +22,7 @@ import oracle  # noqa: E402
 from paper_2408_15654_gb300 import workloads as W  # noqa: E402
 
 STEPS = 10000
+N_EPS = 1e-4
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "shear_drop_2048x1024_10000_samples.txt")
 
 
@@ -38,6 +42,7 @@ def main():
     oracle.build()
     oracle.set_threads(threads)
     p, f = W.shear_drop_large()
+    p = dict(p, n_eps=N_EPS)
     xs, ys = sample_cells(f["phi"])
     s = oracle.Sim(p)
     s.init(**f)
@@ -51,6 +56,7 @@ def main():
                  f"after {STEPS} steps\n")
         fh.write("# written by tests/golden/make_shear_drop_2048x1024_samples.py (oracle only)\n")
         fh.write(f"# steps {STEPS}\n")
+        fh.write(f"# n_eps {N_EPS}\n")
         fh.write(f"# total_phi {s.total('phi'):.17g}\n")
         fh.write(f"# total_psi {s.total('psi'):.17g}\n")
         fh.write("# x y phi psi ux uy P\n")

