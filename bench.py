@@ -35,6 +35,8 @@ BYTES_PER_LUP_FG = 18 * 2 * 2 + 8 * 4 * 2 + 2 * 4 * 2  # f, g in 16 bits, h in F
 BYTES_PER_LUP_PRESCRIBED = {"fp32": 9 * 8 * 2 + 2 * 4 * 2, "fp16": 9 * 4 * 2 + 2 * 4 * 2}  # f, g and u only
 HALF_MODES = {"fp16": BYTES_PER_LUP_16, "bf16": BYTES_PER_LUP_16, "fp16_fg": BYTES_PER_LUP_FG,
               "bf16_fg": BYTES_PER_LUP_FG}
+# density ratio != 1: the same populations and u history plus the mass-flux history S (2 floats)
+BYTES_PER_LUP_VAR_RHO = {"fp32": BYTES_PER_LUP + 2 * 4 * 2, "fp16": BYTES_PER_LUP_16 + 2 * 4 * 2}
 METRIC = "MLUPS (3 lattices) and % HBM roofline, FP32 vs half-store; serving p50/p99"
 WORKLOAD = "sheared drop 2048x1024 (R=160, Re=1, Ca=0.2, Langmuir E0=0.2, psi0=0.3), FP32 storage"
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_2048x1024_fp32.json")
@@ -248,6 +250,30 @@ def serving_leg(torch, lbm, W, reqs, jobs, policy: str, max_jobs: int, force_fp3
             "lattice_updates": lup, "gpu_launches": st["kernel_launches"], "rounds": st["rounds"]}
 
 
+def timed_leg(torch, lbm, p, f, args, stream, world, what: str, bytes_per_lup: int):
+    """Warm-up, then exactly args.steps steps of one lattice timed with CUDA events on its stream."""
+    sim = lbm.Lattice(p, stream=stream)
+    sim.init(**f)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ms_max = barrier_max(ms, world)
+    if sim.status != lbm.LBM_OK:
+        raise RuntimeError(f"unstable state in the {what} benchmark: {lbm.lbm_last_error()}")
+    sim.close()
+    cells = p["nx"] * p["ny"]
+    ach = cells * bytes_per_lup / (ms / args.steps * 1e-3) / 1e9
+    return {"value": cells * args.steps * world / (ms_max * 1e-3) / 1e6, "unit": "MLUPS",
+            "ms_per_step": ms_max / args.steps, "achieved_gbs": ach,
+            "frac_of_measured_hbm": ach / measured_peak()[0], "algorithmic_bytes_per_lup": bytes_per_lup}
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle as it stands on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", 0))
@@ -344,27 +370,17 @@ def run_ours(args):
     prescribed = {}
     pp, pf = W.convected_drop(NX, NY, R=160.0)
     for st, bpl in BYTES_PER_LUP_PRESCRIBED.items():
-        ps = lbm.Lattice(dict(pp, storage=st), stream=stream)
-        ps.init(**pf)
-        ps.step(args.warmup)
-        torch.cuda.synchronize()
-        barrier(world)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ps.step(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        pms = barrier_max(e0.elapsed_time(e1), world)
-        if ps.status != lbm.LBM_OK:
-            raise RuntimeError(f"unstable state in the prescribed {st} benchmark: {lbm.lbm_last_error()}")
-        pach = cells * bpl / (e0.elapsed_time(e1) / args.steps * 1e-3) / 1e9
-        prescribed[st] = {"value": cells * args.steps * world / (pms * 1e-3) / 1e6, "unit": "MLUPS",
-                          "ms_per_step": pms / args.steps, "achieved_gbs": pach,
-                          "frac_of_measured_hbm": pach / measured_peak()[0], "algorithmic_bytes_per_lup": bpl}
-        ps.close()
-    if prescribed:
-        prescribed["workload"] = ("drop R=160 carried by an imposed u = (0.05, 0) on 2048x1024, periodic, "
-                                  "M_phi=1, D=2 (the convection test of Sec. 4 scaled up); f, g only")
+        prescribed[st] = timed_leg(torch, lbm, dict(pp, storage=st), pf, args, stream, world, f"prescribed {st}", bpl)
+    prescribed["workload"] = ("drop R=160 carried by an imposed u = (0.05, 0) on 2048x1024, periodic, "
+                              "M_phi=1, D=2 (the convection test of Sec. 4 scaled up); f, g only")
+
+    # density ratio 10: the rising bubble of Sec. 4 at R = 256 (1024 x 2048, the same cell count)
+    var_rho = {}
+    bp, bf = W.rising_bubble(256.0)
+    for st, bpl in BYTES_PER_LUP_VAR_RHO.items():
+        var_rho[st] = timed_leg(torch, lbm, dict(bp, storage=st), bf, args, stream, world, f"density-ratio {st}", bpl)
+    var_rho["workload"] = ("rising bubble R=256 on 1024x2048 (Sec. 4: rho and mu ratio 10, Re=35, Bo=10, Pe=10, "
+                           "E0=0.5, linear EOS, walls below and above, gravity); mass-flux history included")
 
     # many lattices at once: the 64-lattice mix, FP32 and FP16 storage
     batch = {}
@@ -423,6 +439,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_lup": BYTES_PER_LUP},
             "half_store": half,
             "prescribed_velocity": prescribed,
+            "density_ratio": var_rho,
             "batch": batch,
             "serving": serving,
             "cpu_baseline": base,
@@ -432,6 +449,7 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "gpu_launches_half_store": len(HALF_MODES) * args.steps,
             "gpu_launches_prescribed": len(BYTES_PER_LUP_PRESCRIBED) * args.steps,
+            "gpu_launches_density_ratio": len(BYTES_PER_LUP_VAR_RHO) * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
