@@ -270,23 +270,36 @@ template <> __device__ __forceinline__ __nv_bfloat16 bits_to<__nv_bfloat16>(uint
 }
 template <> __device__ __forceinline__ float bits_to<float>(uint32_t b) { return __uint_as_float(b); }
 
-// (f_i, g_i) from storage: the values (FP32), or the deviations (f_i - w_i phi_ref, g_i) (16-bit)
-// Decoding multiplies by w_i / S, which is not a binary fraction (w_i = 4/9, 1/9, 1/36): the FP32
-// constant would carry the same relative error (~1e-8) into every decoded value of link i at
-// every step, and that error would add up coherently in the totals of phi and psi.  The constant
-// is therefore split into a head and a tail (dd_hi + dd_lo = w_i / S to ~2^-48) and applied with
-// one extra fused multiply-add, so that only the final rounding remains.
+// 16-bit storage holds r_i = (f_i / w_i - phi_ref) S_f and g_i / w_i S_g.  The decode constant
+// w_i / S is not a binary fraction (w_i = 4/9, 1/9, 1/36), so the stored state is never decoded
+// and re-encoded: the step computes its moments from r (each weight class summed raw and scaled
+// once; the constant's ~1e-8 relative error then only touches the physics) and writes
+// r* = r + (S / w_i) dq_i, the increment of the collision scaled by the exact constant S / w_i.
+// A resting bulk, whose increments are below half an FP32 ulp of r, keeps its stored values
+// exactly, and the totals of phi and psi carry no coherent decode error.
 __host__ __device__ constexpr double wgt_d(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
-__host__ __device__ constexpr float dd_hi(double x) { return (float)x; }
-__host__ __device__ constexpr float dd_lo(double x) { return (float)(x - (double)(float)x); }
-template <int ST, int I> __device__ __forceinline__ float2 dec_pair(typename Traits<ST>::P v) {
+// decode constant w_i / S of link i as one (f, g) pair
+template <int ST, int I> __device__ __forceinline__ float2 kdec() {
     using T = Traits<ST>;
-    if constexpr (!T::kPair16) {
-        return v;
+    return make_float2((float)(wgt_d(I) / T::SF), (float)(wgt_d(I) / T::SG));
+}
+// c S / w_i of link i (exact in FP32: 1 / w_i is 9/4, 9 or 36 and S a power of two)
+template <int ST, int I> __device__ __forceinline__ float2 kenc(double c) {
+    using T = Traits<ST>;
+    return make_float2((float)(c * T::SF / wgt_d(I)), (float)(c * T::SG / wgt_d(I)));
+}
+// (phi, psi) of a cell from its nine stored pairs, converted to FP32 (r): FP32 storage sums the
+// values; 16-bit storage sums the raw values of each weight class and scales each class sum once
+template <int ST> __device__ __forceinline__ float2 pair_sum(const float2 (&r)[9], float2 ref) {
+    if constexpr (!Traits<ST>::kPair16) {
+        float2 s = ref;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s = add2(s, r[i]);
+        return s;
     } else {
-        constexpr double df = wgt_d(I) / T::SF, dg = wgt_d(I) / T::SG;
-        const float2 r = raw2(v);
-        return fma2(r, make_float2(dd_hi(df), dd_hi(dg)), mul2(r, make_float2(dd_lo(df), dd_lo(dg))));
+        const float2 ax = add2(add2(r[1], r[3]), add2(r[2], r[4]));
+        const float2 dg = add2(add2(r[5], r[7]), add2(r[6], r[8]));
+        return fma2(dg, kdec<ST, 5>(), fma2(ax, kdec<ST, 1>(), fma2(r[0], kdec<ST, 0>(), ref)));
     }
 }
 // 3 w_i rho c_i.u: the first-order velocity part of h_eq removed before 16-bit storage
@@ -317,10 +330,9 @@ __device__ __forceinline__ uint32_t cell_key(uint32_t cell, uint32_t seed) {
 // Random bits of conversion k of a cell: a rotation of the cell's word.  Every rounding stays
 // unbiased; conversions of one cell share bits, which correlates their errors but adds no bias.
 __device__ __forceinline__ uint32_t rbits_of(uint32_t key, int k) { return __funnelshift_l(key, key, 5 * k + 1); }
-// (f_i, g_i) deviations to stochastically rounded 16-bit storage
-template <int ST, int I> __device__ __forceinline__ typename Traits<ST>::P enc_pair_rs(float2 q, uint32_t key) {
+// a scaled (f_i, g_i) pair r* to stochastically rounded 16-bit storage
+template <int ST, int I> __device__ __forceinline__ typename Traits<ST>::P enc_pair_rs(float2 v, uint32_t key) {
     using T = Traits<ST>;
-    const float2 v = mul2(q, make_float2((float)(T::SF / wgt_d(I)), (float)(T::SG / wgt_d(I))));
     const uint32_t bits = cvt_rs2<typename T::P>(v.x, v.y, rbits_of(key, I));
     return *reinterpret_cast<const typename T::P*>(&bits);
 }
@@ -369,14 +381,27 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
 // q may hold deviations q_i - w_i r (r per lane): the odd moments are unchanged, the even ones
 // drop r times (1, 1/3, 1/3, 1/9), so they are compared with sr = s - r.
 // nS_k = -s_k and K_k = 1 - s_k/2 per lane (f, g).
+// FP32 storage: q holds the values and becomes q*.  16-bit storage: q holds the raw stored values r
+// and becomes r* = r + (S / w_i) (M^-1 dm)_i (the moments come from r, each weight class scaled by
+// its decode constant once).
+template <int ST>
 __device__ __forceinline__ void collide_pair(float2 q[9], float2 s, float2 sr, float ux, float uy, float2 vx,
                                              float2 vy, float2 nS1, float2 nS2, float2 nS3, float2 nS4, float2 K1,
                                              float2 K3) {
+    constexpr bool raw = Traits<ST>::kPair16;
     const float2 third = bc(1.f / 3.f);
     const float2 a = add2(q[5], q[7]), b = add2(q[6], q[8]), c = sub2(q[5], q[7]), d = sub2(q[6], q[8]);
-    const float2 m5 = sub2(a, b), m8 = add2(a, b), m6 = sub2(c, d), m7 = add2(c, d);
-    const float2 m1 = add2(sub2(q[1], q[3]), m6), m2 = add2(sub2(q[2], q[4]), m7);
-    const float2 m3 = add2(add2(q[1], q[3]), m8), m4 = add2(add2(q[2], q[4]), m8);
+    float2 m1, m2, m3, m4, m5, m6, m7, m8;
+    if constexpr (!raw) {
+        m5 = sub2(a, b), m8 = add2(a, b), m6 = sub2(c, d), m7 = add2(c, d);
+        m1 = add2(sub2(q[1], q[3]), m6), m2 = add2(sub2(q[2], q[4]), m7);
+        m3 = add2(add2(q[1], q[3]), m8), m4 = add2(add2(q[2], q[4]), m8);
+    } else {
+        const float2 kax = kdec<ST, 1>(), kdg = kdec<ST, 5>();
+        m5 = mul2(kdg, sub2(a, b)), m8 = mul2(kdg, add2(a, b)), m6 = mul2(kdg, sub2(c, d)), m7 = mul2(kdg, add2(c, d));
+        m1 = fma2(kax, sub2(q[1], q[3]), m6), m2 = fma2(kax, sub2(q[2], q[4]), m7);
+        m3 = fma2(kax, add2(q[1], q[3]), m8), m4 = fma2(kax, add2(q[2], q[4]), m8);
+    }
     const float2 su = mul2(s, bc(ux)), sv = mul2(s, bc(uy)), s3 = mul2(sr, third);
     const float2 d1 = fma2(nS1, sub2(m1, su), mul2(K1, vx));
     const float2 d2 = fma2(nS1, sub2(m2, sv), mul2(K1, vy));
@@ -388,16 +413,28 @@ __device__ __forceinline__ void collide_pair(float2 q[9], float2 s, float2 sr, f
     const float2 d8 = mul2(nS4, fma2(sr, bc(-1.f / 9.f), m8));
     const float2 A = sub2(d1, d6), B = sub2(d3, d8), C = sub2(d2, d7), D = sub2(d4, d8);
     const float2 E = add2(d8, d5), F = sub2(d8, d5), G = add2(d6, d7), H = sub2(d7, d6);
-    const float2 half = bc(0.5f), quarter = bc(0.25f);
-    q[0] = add2(q[0], sub2(sub2(d8, d3), d4));
-    q[1] = fma2(half, add2(A, B), q[1]);
-    q[3] = fma2(half, sub2(B, A), q[3]);
-    q[2] = fma2(half, add2(C, D), q[2]);
-    q[4] = fma2(half, sub2(D, C), q[4]);
-    q[5] = fma2(quarter, add2(E, G), q[5]);
-    q[7] = fma2(quarter, sub2(E, G), q[7]);
-    q[6] = fma2(quarter, add2(F, H), q[6]);
-    q[8] = fma2(quarter, sub2(F, H), q[8]);
+    if constexpr (!raw) {
+        const float2 half = bc(0.5f), quarter = bc(0.25f);
+        q[0] = add2(q[0], sub2(sub2(d8, d3), d4));
+        q[1] = fma2(half, add2(A, B), q[1]);
+        q[3] = fma2(half, sub2(B, A), q[3]);
+        q[2] = fma2(half, add2(C, D), q[2]);
+        q[4] = fma2(half, sub2(D, C), q[4]);
+        q[5] = fma2(quarter, add2(E, G), q[5]);
+        q[7] = fma2(quarter, sub2(E, G), q[7]);
+        q[6] = fma2(quarter, add2(F, H), q[6]);
+        q[8] = fma2(quarter, sub2(F, H), q[8]);
+    } else {
+        q[0] = fma2(kenc<ST, 0>(1.0), sub2(sub2(d8, d3), d4), q[0]);
+        q[1] = fma2(kenc<ST, 1>(0.5), add2(A, B), q[1]);
+        q[3] = fma2(kenc<ST, 3>(0.5), sub2(B, A), q[3]);
+        q[2] = fma2(kenc<ST, 2>(0.5), add2(C, D), q[2]);
+        q[4] = fma2(kenc<ST, 4>(0.5), sub2(D, C), q[4]);
+        q[5] = fma2(kenc<ST, 5>(0.25), add2(E, G), q[5]);
+        q[7] = fma2(kenc<ST, 7>(0.25), sub2(E, G), q[7]);
+        q[6] = fma2(kenc<ST, 6>(0.25), add2(F, H), q[6]);
+        q[8] = fma2(kenc<ST, 8>(0.25), sub2(F, H), q[8]);
+    }
 }
 
 template <int ST, int I>
@@ -412,9 +449,10 @@ __device__ __forceinline__ float load_h(const unsigned char* sm, const float2* H
         // the slot was stored with the first-order velocity part of the cell that stored it:
         // the source cell x - c_i, or across a wall the own cell (whose opposite slot it is)
         const float2 us = bb ? make_float2(-uown.x, -uown.y) : Hist[(ty + 1 - cy(I)) * BW + tx + 4 - cx(I)];
-        constexpr double dh = wgt_d(I) / T::SH;
-        const float r = raw1(v);
-        return fmaf(r, dd_hi(dh), fmaf(r, dd_lo(dh), h_vel<I>(us, p)));
+        // one FP32 decode constant: h has no conserved zeroth moment, and the collision relaxes the
+        // constant's ~1e-8 relative error away every step
+        constexpr float dh = (float)(wgt_d(I) / T::SH);
+        return fmaf(raw1(v), dh, h_vel<I>(us, p));
     }
 }
 
@@ -475,19 +513,9 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         int row = ty + 1;
         if (WALLS && y >= p.ny) row = p.ny - y0;
         const P* base = FG + row * BW + tx + 4;
-        q[0] = dec_pair<ST, 0>(base[0 * SLOT - cx(0)]);
-        q[1] = dec_pair<ST, 1>(base[1 * SLOT - cx(1)]);
-        q[2] = dec_pair<ST, 2>(base[2 * SLOT - cx(2)]);
-        q[3] = dec_pair<ST, 3>(base[3 * SLOT - cx(3)]);
-        q[4] = dec_pair<ST, 4>(base[4 * SLOT - cx(4)]);
-        q[5] = dec_pair<ST, 5>(base[5 * SLOT - cx(5)]);
-        q[6] = dec_pair<ST, 6>(base[6 * SLOT - cx(6)]);
-        q[7] = dec_pair<ST, 7>(base[7 * SLOT - cx(7)]);
-        q[8] = dec_pair<ST, 8>(base[8 * SLOT - cx(8)]);
-        float2 s = ref;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s = add2(s, q[i]);
-        PP[eo] = s;
+        for (int i = 0; i < 9; ++i) q[i] = raw2(base[i * SLOT - cx(i)]);  // the values, or the raw 16-bit deviations
+        PP[eo] = pair_sum<ST>(q, ref);
     }
     if (t < NRING) {
         int ex, ey;
@@ -502,17 +530,10 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
             else if (gy >= p.ny) row = p.ny - y0;
         }
         const P* base = FG + row * BW + ex + 3;
-        float2 s = ref;
-        s = add2(s, dec_pair<ST, 0>(base[0 * SLOT - cx(0)]));
-        s = add2(s, dec_pair<ST, 1>(base[1 * SLOT - cx(1)]));
-        s = add2(s, dec_pair<ST, 2>(base[2 * SLOT - cx(2)]));
-        s = add2(s, dec_pair<ST, 3>(base[3 * SLOT - cx(3)]));
-        s = add2(s, dec_pair<ST, 4>(base[4 * SLOT - cx(4)]));
-        s = add2(s, dec_pair<ST, 5>(base[5 * SLOT - cx(5)]));
-        s = add2(s, dec_pair<ST, 6>(base[6 * SLOT - cx(6)]));
-        s = add2(s, dec_pair<ST, 7>(base[7 * SLOT - cx(7)]));
-        s = add2(s, dec_pair<ST, 8>(base[8 * SLOT - cx(8)]));
-        PP[ey * EX + ex] = s;
+        float2 r[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) r[i] = raw2(base[i * SLOT - cx(i)]);
+        PP[ey * EX + ex] = pair_sum<ST>(r, ref);
     }
     if (__syncthreads_or(abort)) {
         // a staging copy did not arrive in time: report it, wait (bounded) for it, store nothing
@@ -617,17 +638,10 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     float uxp = ux, uyp = uy;
     if (!io.first) {
         const P* base = FG + (ty + 1) * BW + tx + 4;
-        float2 s = ref;
-        s = add2(s, dec_pair<ST, 0>(base[0 * SLOT + cy(0) * BW]));
-        s = add2(s, dec_pair<ST, 1>(base[1 * SLOT + cy(1) * BW]));
-        s = add2(s, dec_pair<ST, 2>(base[2 * SLOT + cy(2) * BW]));
-        s = add2(s, dec_pair<ST, 3>(base[3 * SLOT + cy(3) * BW]));
-        s = add2(s, dec_pair<ST, 4>(base[4 * SLOT + cy(4) * BW]));
-        s = add2(s, dec_pair<ST, 5>(base[5 * SLOT + cy(5) * BW]));
-        s = add2(s, dec_pair<ST, 6>(base[6 * SLOT + cy(6) * BW]));
-        s = add2(s, dec_pair<ST, 7>(base[7 * SLOT + cy(7) * BW]));
-        s = add2(s, dec_pair<ST, 8>(base[8 * SLOT + cy(8) * BW]));
-        pprev = s;
+        float2 r[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) r[i] = raw2(base[i * SLOT + cy(i) * BW]);
+        pprev = pair_sum<ST>(r, ref);
         uxp = uown.x;
         uyp = uown.y;
     }
@@ -697,7 +711,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         {
             const float2 vx = fma2(make_float2(Aterm, Bterm), bc(nx_ * (1.f / 3.f)), dtX);
             const float2 vy = fma2(make_float2(Aterm, Bterm), bc(ny_ * (1.f / 3.f)), dtY);
-            collide_pair(q, pp, sub2(pp, ref), ux, uy, vx, vy, make_float2(p.nS1[0], p.nS1[1]),
+            collide_pair<ST>(q, pp, sub2(pp, ref), ux, uy, vx, vy, make_float2(p.nS1[0], p.nS1[1]),
                          make_float2(p.nS2[0], p.nS2[1]), make_float2(p.nS3[0], p.nS3[1]),
                          make_float2(p.nS4[0], p.nS4[1]), make_float2(p.K1[0], p.K1[1]), make_float2(p.K3[0], p.K3[1]));
             if constexpr (!T::kPair16) {
