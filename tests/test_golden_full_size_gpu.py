@@ -1,0 +1,99 @@
+"""The precision configuration at full size: the 2048 x 1024 sheared drop (Sec. 4.4 set-up) after
+10 000 steps in every storage mode, against the FP64 oracle on seeded sample cells and on the FP64
+totals of phi and psi.  The expected values are tests/golden/shear_drop_2048x1024_10000_samples.txt,
+written by tests/golden/make_shear_drop_2048x1024_samples.py from the oracle alone."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2408_15654_gb300 import lbm
+from paper_2408_15654_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIXTURE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "shear_drop_2048x1024_10000_samples.txt")
+OUT = os.environ.get("LBM_RECORD_DIR")  # measured errors are written there as JSON, if it is set
+_records = {}
+
+# stated relative-L2 bounds over the sample cells (u against the norm of the sampled velocity; P
+# after removing the sample mean, against its range) and on the totals
+BOUND = {
+    "fp32": {"phi": 1e-5, "psi": 1e-5, "u": 1e-5, "P": 1e-3, "total": 1e-6},
+    "fp16": {"phi": 3e-3, "psi": 5e-3, "u": 5e-4, "P": 5e-2, "total": 1e-3},
+    "bf16": {"phi": 2e-2, "psi": 3e-2, "u": 2e-3, "P": 2e-1, "total": 5e-3},
+}
+BOUND["fp16_fg"] = BOUND["fp16"]
+BOUND["bf16_fg"] = BOUND["bf16"]
+
+
+def load_fixture():
+    head, rows = {}, []
+    with open(FIXTURE) as fh:
+        for line in fh:
+            if line.startswith("#"):
+                parts = line[1:].split()
+                if len(parts) == 2:
+                    try:
+                        head[parts[0]] = float(parts[1])
+                    except ValueError:
+                        pass
+            elif line.strip():
+                rows.append([float(v) for v in line.split()])
+    a = np.array(rows)
+    return {"steps": int(head["steps"]), "n_eps": head["n_eps"], "total_phi": head["total_phi"],
+            "total_psi": head["total_psi"], "x": a[:, 0].astype(int), "y": a[:, 1].astype(int),
+            "phi": a[:, 2], "psi": a[:, 3], "ux": a[:, 4], "uy": a[:, 5], "P": a[:, 6]}
+
+
+@pytest.fixture(scope="module")
+def fx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lbm.load()
+    assert os.path.exists(FIXTURE), "the golden file is part of the repository"
+    return load_fixture()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _record(name, errs):
+    _records[name] = errs
+    if not OUT:
+        return
+    try:
+        os.makedirs(OUT, exist_ok=True)
+        with open(os.path.join(OUT, "golden_full_size_errors.json"), "w") as fh:
+            json.dump(_records, fh, indent=1)
+    except OSError:
+        pass
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16", "fp16_fg", "bf16_fg"])
+def test_full_size_shear_drop_after_10000_steps(fx, storage):
+    p, f = W.shear_drop_large()
+    p = dict(p, n_eps=fx["n_eps"], storage=storage)
+    g = lbm.Lattice(p)
+    g.init(**f)
+    g.step(fx["steps"])
+    assert g.status == 0
+    m = g.moments()
+    xs, ys = fx["x"], fx["y"]
+    e = {k: rel_l2(m[k][ys, xs], fx[k]) for k in ("phi", "psi")}
+    du = np.hypot(m["ux"][ys, xs] - fx["ux"], m["uy"][ys, xs] - fx["uy"])
+    e["u"] = float(np.linalg.norm(du) / np.linalg.norm(np.hypot(fx["ux"], fx["uy"])))
+    pg, po = m["P"][ys, xs], fx["P"]
+    e["P"] = float(np.abs((pg - pg.mean()) - (po - po.mean())).max() / np.ptp(po))
+    e["total_phi"] = abs(g.total("phi") - fx["total_phi"]) / fx["total_phi"]
+    e["total_psi"] = abs(g.total("psi") - fx["total_psi"]) / fx["total_psi"]
+    g.close()
+    print(storage, {k: f"{v:.2e}" for k, v in e.items()})
+    _record(storage, e)
+    b = BOUND[storage]
+    assert e["phi"] <= b["phi"] and e["psi"] <= b["psi"] and e["u"] <= b["u"], e
+    assert e["P"] <= b["P"], e
+    assert e["total_phi"] <= b["total"] and e["total_psi"] <= b["total"], e
