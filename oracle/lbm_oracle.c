@@ -37,6 +37,8 @@
  *
  * Precision: FP64, round to nearest, compiled without FMA contraction or fast-math.
  *
+ * Direct check (tests/test_bruteforce_8x8.py): an independent NumPy statement of the step in
+ * distribution space equals every population to 1e-13 after 1 and 10 steps on 8 x 8 grids.
  * Pins (tests/test_oracle_pins.py): the printed M; D2Q9 isotropy; the Appendix A conditions on
  * Lambda, g_eq and G (and the same for f_eq, F); the moments of h_eq and H; recovery of u and P
  * from an equilibrium state; stencils exact on quadratics; the Marangoni integral across a flat
