@@ -168,10 +168,22 @@ def cpu_baseline(budget_s: float = 12.0):
     t0 = time.perf_counter()
     s.step(n)
     dt = time.perf_counter() - t0
+    # the same oracle on one core, a few steps of the same run
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    s.step(1)
+    t1c = time.perf_counter() - t0
+    n1 = max(1, min(20, int(budget_s / 2 / max(t1c, 1e-6))))
+    t0 = time.perf_counter()
+    s.step(n1)
+    dt1 = time.perf_counter() - t0
+    oracle.set_threads(cores)
     s.close()
     return {"value": NX * NY * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"{n} FP64 oracle steps of the 2048x1024 sheared drop after 1 untimed step, "
-                      f"OpenMP over rows ({cores} threads)"}
+                      f"OpenMP over rows ({cores} threads)",
+            "single_core": {"value": NX * NY * n1 / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
+                            "sample": f"{n1} further steps of the same run on one thread, after 1 untimed step"}}
 
 
 def batch_leg(torch, lbm, W, storage: str, steps: int, alone_steps: int = 0):
