@@ -626,9 +626,13 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     }
 
     // velocity: rho u = sum c_i h_i + F/2 (Sec. 3.3), or the imposed velocity (kept in the history)
-    const float h13 = h[1] - h[3], h24 = h[2] - h[4], h57 = h[5] - h[7], h68 = h[6] - h[8];
-    const float jx = h13 + (h57 - h68);
-    const float jy = h24 + (h57 + h68);
+    // the links paired as (1, 2), (3, 4), (5, 6), (7, 8) for packed FP32x2 arithmetic
+    float2 X = make_float2(h[1], h[2]), Y = make_float2(h[3], h[4]), U = make_float2(h[5], h[6]),
+           V = make_float2(h[7], h[8]);
+    const float2 dXY = sub2(X, Y), dUV = sub2(U, V);  // (h1 - h3, h2 - h4), (h5 - h7, h6 - h8)
+    const float h57 = dUV.x, h68 = dUV.y;
+    const float jx = dXY.x + (h57 - h68);
+    const float jy = dXY.y + (h57 + h68);
     const float inv_rho = var ? __frcp_rn(rho_v) : p.inv_rho;
     const float ux = FLOW ? (jx + 0.5f * Fx) * inv_rho : uown.x;
     const float uy = FLOW ? (jy + 0.5f * Fy) * inv_rho : uown.y;
@@ -675,7 +679,8 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
 
     // pressure (Eq. for P, Sec. 3.3) with K = w0/(c^2 - cs2) = 2/3:
     //   P = 3/5 [sum_{i>0} h_i + u.grad rho / 2 - (2/3) (rho u - S).u + (1/3) d_t(rho u.u - S.u)]
-    const float hsum = ((h[1] + h[2]) + (h[3] + h[4])) + ((h[5] + h[6]) + (h[7] + h[8]));
+    const float2 sXY = add2(X, Y), sUV = add2(U, V);  // (h1 + h3, h2 + h4), (h5 + h7, h6 + h8)
+    const float hsum = (sXY.x + sXY.y) + (sUV.x + sUV.y);
     float P_ = 0.f;
     if (FLOW) {
         if (!var)
@@ -756,71 +761,70 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
             // source moments of H, m2H = d_t(rho u u - (S u + u S)/2) + cs2 (u grad rho + grad rho u):
             //   (., Fx, Fy, m2H_xx + u.grad rho/3, m2H_yy + u.grad rho/3, m2H_xy, Fx/3, Fy/3,
             //    (m2H_xx + m2H_yy)/3 + u.grad rho/9)
-            const float ha = h[5] + h[7], hb = h[6] + h[8];
-            const float m5 = ha - hb, m8 = ha + hb, m6 = h57 - h68, m7 = h57 + h68;
-            const float m3 = (h[1] + h[3]) + m8, m4 = (h[2] + h[4]) + m8;
-            // increments dm_k = -s_k (m_k - m_eq_k) + (1 - s_k/2) m_src_k, then h* = h + M^-1 dm
-            const float d1 = var ? rfma(k1, Fx, -rmul(s1, rsub(jx, Jx))) : k1 * Fx - s1 * (jx - Jx);
-            const float d2 = var ? rfma(k1, Fy, -rmul(s1, rsub(jy, Jy))) : k1 * Fy - s1 * (jy - Jy);
-            float d3, d4, d5, d8;
-            float mxx = 0.f, myy = 0.f;
+            const float m5 = sUV.x - sUV.y, m8 = sUV.x + sUV.y;
+            const float2 m67 = make_float2(h57 - h68, h57 + h68);  // (m6, m7)
+            const float2 m34 = add2(sXY, bc(m8));                   // (m3, m4)
+            const float2 Fv = make_float2(Fx, Fy), Jv = make_float2(Jx, Jy), uv = make_float2(ux, uy);
+            // increments dm_k = -s_k (m_k - m_eq_k) + (1 - s_k/2) m_src_k, then h* = h + M^-1 dm; the
+            // x and y moments of each order as one pair
+            float2 d12, d34, d67;
+            float d5, d8;
             if constexpr (!var) {
-                d3 = k2 * dt_xx - s2 * (m3 - (P_ + Jx * ux));
-                d4 = k2 * dt_yy - s2 * (m4 - (P_ + Jy * uy));
+                d12 = fma2(bc(k1), Fv, mul2(bc(-s1), sub2(make_float2(jx, jy), Jv)));
+                d34 = fma2(bc(k2), make_float2(dt_xx, dt_yy), mul2(bc(-s2), sub2(m34, fma2(Jv, uv, bc(P_)))));
                 d5 = k2 * dt_xy - s2 * (m5 - Jx * uy);
-            } else {
-                mxx = rfma(2.f / 3.f, rmul(ux, grx), dt_xx);
-                myy = rfma(2.f / 3.f, rmul(uy, gry), dt_yy);
-                const float mxy = rfma(1.f / 3.f, rfma(ux, gry, rmul(uy, grx)), dt_xy);
-                d3 = rfma(k2, rfma(1.f / 3.f, ugr, mxx), -rmul(s2, rsub(m3, radd(P_, qxx))));
-                d4 = rfma(k2, rfma(1.f / 3.f, ugr, myy), -rmul(s2, rsub(m4, radd(P_, qyy))));
-                d5 = rfma(k2, mxy, -rmul(s2, rsub(m5, qxy)));
-            }
-            const float d6 = var ? rmul(1.f / 3.f, rfma(k3, Fx, -rmul(s3, rfma(3.f, m6, -Jx))))
-                                 : (1.f / 3.f) * (k3 * Fx - s3 * (3.f * m6 - Jx));
-            const float d7 = var ? rmul(1.f / 3.f, rfma(k3, Fy, -rmul(s3, rfma(3.f, m7, -Jy))))
-                                 : (1.f / 3.f) * (k3 * Fy - s3 * (3.f * m7 - Jy));
-            if constexpr (!var)
+                d67 = mul2(bc(1.f / 3.f), fma2(bc(k3), Fv, mul2(bc(-s3), fma2(bc(3.f), m67, make_float2(-Jx, -Jy)))));
                 d8 = (1.f / 3.f) * (k4 * (dt_xx + dt_yy) - s4 * (3.f * m8 - (P_ + Jx * ux + Jy * uy)));
-            else  // 3 x the eighth source moment (mxx + myy)/3 + u.grad rho/9
+            } else {
+                d12 = make_float2(rfma(k1, Fx, -rmul(s1, rsub(jx, Jx))), rfma(k1, Fy, -rmul(s1, rsub(jy, Jy))));
+                const float mxx = rfma(2.f / 3.f, rmul(ux, grx), dt_xx);
+                const float myy = rfma(2.f / 3.f, rmul(uy, gry), dt_yy);
+                const float mxy = rfma(1.f / 3.f, rfma(ux, gry, rmul(uy, grx)), dt_xy);
+                d34 = make_float2(rfma(k2, rfma(1.f / 3.f, ugr, mxx), -rmul(s2, rsub(m34.x, radd(P_, qxx)))),
+                                  rfma(k2, rfma(1.f / 3.f, ugr, myy), -rmul(s2, rsub(m34.y, radd(P_, qyy)))));
+                d5 = rfma(k2, mxy, -rmul(s2, rsub(m5, qxy)));
+                d67 = make_float2(rmul(1.f / 3.f, rfma(k3, Fx, -rmul(s3, rfma(3.f, m67.x, -Jx)))),
+                                  rmul(1.f / 3.f, rfma(k3, Fy, -rmul(s3, rfma(3.f, m67.y, -Jy)))));
+                // 3 x the eighth source moment (mxx + myy)/3 + u.grad rho/9
                 d8 = rmul(1.f / 3.f, rfma(k4, rfma(1.f / 3.f, ugr, radd(mxx, myy)),
                                           -rmul(s4, rfma(3.f, m8, -radd(P_, radd(qxx, qyy))))));
-            const float A = d1 - d6, B = d3 - d8, C = d2 - d7, D = d4 - d8;
-            const float E = d8 + d5, F = d8 - d5, G = d6 + d7, H = d7 - d6;
-            h[1] += 0.5f * (A + B);
-            h[3] += 0.5f * (B - A);
-            h[2] += 0.5f * (C + D);
-            h[4] += 0.5f * (D - C);
-            h[5] += 0.25f * (E + G);
-            h[7] += 0.25f * (E - G);
-            h[6] += 0.25f * (F + H);
-            h[8] += 0.25f * (F - H);
+            }
+            // (A, C) = (d1 - d6, d2 - d7), (B, D) = (d3 - d8, d4 - d8), (E, F) = (d8 + d5, d8 - d5),
+            // (G, H) = (d6 + d7, d7 - d6)
+            const float2 AC = sub2(d12, d67), BD = sub2(d34, bc(d8));
+            const float2 EF = make_float2(d8 + d5, d8 - d5), GH = make_float2(d67.x + d67.y, d67.y - d67.x);
+            X = fma2(bc(0.5f), add2(AC, BD), X);     // h1 += (A + B)/2, h2 += (C + D)/2
+            Y = fma2(bc(0.5f), sub2(BD, AC), Y);     // h3 += (B - A)/2, h4 += (D - C)/2
+            U = fma2(bc(0.25f), add2(EF, GH), U);    // h5 += (E + G)/4, h6 += (F + H)/4
+            V = fma2(bc(0.25f), sub2(EF, GH), V);    // h7 += (E - G)/4, h8 += (F - H)/4
             if (WALLS) {
                 // moving-wall term for the links that leave through a wall, folded in before storing:
                 // h_ibar(x_b, t+1) = h*_i(x_b, t) - 2 w_i rho c_i.u_w / cs2
                 if (y == 0) {
-                    h[7] -= 6.f * wgt(7) * rho * (-1.f) * p.u_bot;
-                    h[8] -= 6.f * wgt(8) * rho * (1.f) * p.u_bot;
+                    V.x -= 6.f * wgt(7) * rho * (-1.f) * p.u_bot;
+                    V.y -= 6.f * wgt(8) * rho * (1.f) * p.u_bot;
                 }
                 if (y == p.ny - 1) {
-                    h[5] -= 6.f * wgt(5) * rho * (1.f) * p.u_top;
-                    h[6] -= 6.f * wgt(6) * rho * (-1.f) * p.u_top;
+                    U.x -= 6.f * wgt(5) * rho * (1.f) * p.u_top;
+                    U.y -= 6.f * wgt(6) * rho * (-1.f) * p.u_top;
                 }
             }
             if constexpr (!T::kH16) {
-    #pragma unroll
-                for (int i = 1; i < 9; ++i) outh[i - 1] = h[i];
+                outh[0] = X.x, outh[1] = X.y, outh[2] = Y.x, outh[3] = Y.y;
+                outh[4] = U.x, outh[5] = U.y, outh[6] = V.x, outh[7] = V.y;
             } else {
                 // every slot is stored relative to this cell's new u (what the next step reads back):
                 // raw = (h_i / w_i - 3 rho c_i.u) S_h, two links per stochastic conversion
                 const float vx = p.kh3 * T::SH * ux, vy = p.kh3 * T::SH * uy;
                 constexpr float e1 = (float)(T::SH / wgt_d(1)), e5 = (float)(T::SH / wgt_d(5));  // exact
-                const uint32_t b12 = cvt_rs2<typename T::P>(fmaf(h[1], e1, -vx), fmaf(h[2], e1, -vy), rbits_of(key, 9));
-                const uint32_t b34 = cvt_rs2<typename T::P>(fmaf(h[3], e1, vx), fmaf(h[4], e1, vy), rbits_of(key, 10));
-                const uint32_t b56 =
-                    cvt_rs2<typename T::P>(fmaf(h[5], e5, -(vx + vy)), fmaf(h[6], e5, vx - vy), rbits_of(key, 11));
-                const uint32_t b78 =
-                    cvt_rs2<typename T::P>(fmaf(h[7], e5, vx + vy), fmaf(h[8], e5, vy - vx), rbits_of(key, 12));
+                const float2 r12 = fma2(X, bc(e1), make_float2(-vx, -vy));
+                const float2 r34 = fma2(Y, bc(e1), make_float2(vx, vy));
+                const float2 r56 = fma2(U, bc(e5), make_float2(-(vx + vy), vx - vy));
+                const float2 r78 = fma2(V, bc(e5), make_float2(vx + vy, vy - vx));
+                const uint32_t b12 = cvt_rs2<typename T::P>(r12.x, r12.y, rbits_of(key, 9));
+                const uint32_t b34 = cvt_rs2<typename T::P>(r34.x, r34.y, rbits_of(key, 10));
+                const uint32_t b56 = cvt_rs2<typename T::P>(r56.x, r56.y, rbits_of(key, 11));
+                const uint32_t b78 = cvt_rs2<typename T::P>(r78.x, r78.y, rbits_of(key, 12));
                 outh[0] = bits_to<Hv>(b12 & 0xFFFFu);
                 outh[1] = bits_to<Hv>(b12 >> 16);
                 outh[2] = bits_to<Hv>(b34 & 0xFFFFu);

@@ -180,9 +180,12 @@ def test_autotune_keeps_results_exact(torch):
 
 
 def test_batch_member_against_oracle(torch):
-    """A member of a mixed batch after 200 steps against the FP64 oracle (FP32 parity bound)."""
+    """A member of a mixed batch after 200 steps against the FP64 oracle (FP32 parity bound).  The
+    unit normal is taken only where |grad phi| > 1e-4: the perturbed members compress the flat bulk,
+    where grad phi is of rounding size and its direction is set by rounding (with the default
+    threshold, member 1 differs by 4.3e-5 in psi; with this one by 1.4e-7)."""
     stream = torch.cuda.Stream()
-    cases = mixed_cases()
+    cases = [(dict(p, n_eps=1e-4), f) for p, f in mixed_cases()]
     lats = make(torch, cases, stream)
     b = lbm.Batch(lats, stream)
     b.set_schedule("row_interleaved", 8)
