@@ -289,6 +289,48 @@ def timed_leg(torch, lbm, p, f, args, stream, world, what: str, bytes_per_lup: i
             "frac_of_measured_hbm": ach / measured_peak()[0], "algorithmic_bytes_per_lup": bytes_per_lup}
 
 
+GOLDEN = os.path.join(ROOT, "tests", "golden", "shear_drop_2048x1024_10000_samples.txt")
+
+
+def precision_leg(torch, lbm, W, stream):
+    """The precision configuration's errors: every storage mode after the oracle's 10 000 steps of
+    the 2048 x 1024 sheared drop, against the oracle's FP64 values at its seeded sample cells (the
+    golden file written by the oracle alone); relative L2 over the samples, u against the sampled
+    speed.  Not part of any timed region."""
+    if not os.path.exists(GOLDEN):
+        return None
+    head, rows = {}, []
+    with open(GOLDEN) as fh:
+        for line in fh:
+            if line.startswith("#"):
+                parts = line[1:].split()
+                if len(parts) == 2:
+                    try:
+                        head[parts[0]] = float(parts[1])
+                    except ValueError:
+                        pass
+            elif line.strip():
+                rows.append([float(v) for v in line.split()])
+    import numpy as np
+    a = np.array(rows)
+    xs, ys = a[:, 0].astype(int), a[:, 1].astype(int)
+    steps = int(head["steps"])
+    out = {"steps": steps, "sample_cells": len(xs), "n_eps": head["n_eps"]}
+    p, f = W.shear_drop_large(NX, NY)
+    for st in ("fp32",) + tuple(HALF_MODES):
+        sim = lbm.Lattice(dict(p, storage=st, n_eps=head["n_eps"]), stream=stream)
+        sim.init(**f)
+        sim.step(steps)
+        m = sim.moments()
+        rel = lambda g, o: float(np.linalg.norm(g - o) / np.linalg.norm(o))  # noqa: E731
+        du = np.hypot(m["ux"][ys, xs] - a[:, 4], m["uy"][ys, xs] - a[:, 5])
+        out[st] = {"phi": rel(m["phi"][ys, xs], a[:, 2]), "psi": rel(m["psi"][ys, xs], a[:, 3]),
+                   "u": float(np.linalg.norm(du) / np.linalg.norm(np.hypot(a[:, 4], a[:, 5]))),
+                   "total_phi": abs(sim.total("phi") - head["total_phi"]) / head["total_phi"]}
+        sim.close()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle as it stands on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", 0))
@@ -397,6 +439,9 @@ def run_ours(args):
     var_rho["workload"] = ("rising bubble R=256 on 1024x2048 (Sec. 4: rho and mu ratio 10, Re=35, Bo=10, Pe=10, "
                            "E0=0.5, linear EOS, walls below and above, gravity); mass-flux history included")
 
+    # errors of every storage mode against the oracle after 10 000 steps (untimed)
+    precision = precision_leg(torch, lbm, W, stream) if (rank == 0 and not args.no_precision) else None
+
     # many lattices at once: the 64-lattice mix, FP32 and FP16 storage
     batch = {}
     if args.batch_steps > 0:
@@ -453,6 +498,7 @@ def run_ours(args):
                          "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "algorithmic_bytes_per_lup": BYTES_PER_LUP},
             "half_store": half,
+            "precision_vs_oracle": precision,
             "prescribed_velocity": prescribed,
             "density_ratio": var_rho,
             "batch": batch,
@@ -481,6 +527,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the untimed storage-error leg")
     ap.add_argument("--batch-steps", type=int, default=1000, help="steps of the 64-lattice batch legs (0: skip)")
     ap.add_argument("--serving-requests", type=int, default=24,
                     help="requests of the seeded serving stream to replay (at most 200; 0: skip)")
