@@ -1,7 +1,7 @@
 // Host implementation of the C ABI declared in include/lbm.h.
 //
 // The library owns no device memory: the caller passes one workspace, carved here into
-//   [pops A | pops B | u history A | u history B | status word | reduction partials]
+//   [pops A | pops B | u history A | u history B | (S history A | S history B) | status word | reduction partials]
 // every part 256-byte aligned.  Between steps the population buffer that is not current is dead
 // (the next step overwrites all of it), so host transfers stage through it.
 #include <cmath>

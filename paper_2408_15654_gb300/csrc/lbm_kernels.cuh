@@ -27,7 +27,8 @@
 // in a steady flow a cell rounds nearly the same values every step, and round-to-nearest would
 // then add the same error every step.  All arithmetic stays in FP32; f and g are collided as the
 // deviations f_i - w_i phi_ref that the storage holds (the reference enters only the even
-// moments, through phi - phi_ref).
+// moments, through phi - phi_ref), and the stored pair values are updated in place by the
+// scaled increment of the collision rather than decoded and re-encoded (see kdec / kenc).
 //
 // Velocity order (the columns of the printed moment matrix M, Sec. 4):
 //   0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
