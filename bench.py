@@ -128,7 +128,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(loaded)}
 
 
-def dist_setup(n_gpus: int):
+def dist_setup(n_gpus: int, backend: str = "nccl"):
+    """Rank, world size and local rank from the launcher's environment; one process per GPU joins
+    a process group (NCCL on the GPUs; gloo runs the same host logic on CPU).  Replicas exchange
+    nothing on the data path: the group carries only barriers and the max of the timings."""
     import torch
     rank, world, local = 0, 1, 0
     if n_gpus > 1 or "WORLD_SIZE" in os.environ:
@@ -137,19 +140,30 @@ def dist_setup(n_gpus: int):
         world = int(os.environ.get("WORLD_SIZE", 1))
         local = int(os.environ.get("LOCAL_RANK", 0))
         if world > 1:
-            torch.cuda.set_device(local)
-            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            if backend == "nccl":
+                torch.cuda.set_device(local)
+                dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            else:
+                dist.init_process_group(backend)
     return rank, world, local
 
 
 def barrier_max(value: float, world: int) -> float:
+    """The maximum of value over the ranks (the slowest rank's time)."""
     if world <= 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_mlups(cells_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput of weak-scaled replicas: the updates of all ranks over the slowest
+    rank's time."""
+    return cells_per_rank * steps * world / (ms_max * 1e-3) / 1e6
 
 
 def barrier(world: int):
@@ -404,7 +418,7 @@ def run_ours(args):
     st = sim.status
     if st != lbm.LBM_OK:
         raise RuntimeError(f"unstable state during the benchmark: {lbm.lbm_last_error()}")
-    value = cells * args.steps * world / (ms_max * 1e-3) / 1e6
+    value = aggregate_mlups(cells, args.steps, world, ms_max)
 
     # the same workload with 16-bit population storage (FP32 arithmetic)
     half = {}
