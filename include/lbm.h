@@ -213,10 +213,12 @@ int lbm_destroy(lbm_handle* h);
 /* Step kernel of a handle.  Both variants compute the same step bit for bit; they differ in how
  * the work is laid out on the GPU:
  *   LBM_KERNEL_TILE       one CTA per 32 x 8 tile, launched as a grid of all tiles;
- *   LBM_KERNEL_PIPELINED  persistent CTAs (as many as fit on all SMs, at most one per tile),
- *                         each staging its next tile with TMA while it computes the current one;
- *   LBM_KERNEL_AUTO       (lbm_set_kernel only) the library's choice, currently TILE for every
- *                         storage mode (the faster or equal one on GB300 at 2048 x 1024).
+ *   LBM_KERNEL_PIPELINED  persistent, warp-specialised CTAs (as many as fit on all SMs, at most
+ *                         one per tile): a copy warp claims tiles and stages each with TMA into
+ *                         one of two buffers while eight compute warps work on the other;
+ *   LBM_KERNEL_AUTO       (lbm_set_kernel only) the library's choice: TILE for FP32 storage,
+ *                         PIPELINED for the 16-bit modes (the faster ones on GB300 at
+ *                         2048 x 1024).
  * A new handle uses the library's choice.  LBM_EINVAL if the pipelined kernel does not fit. */
 #define LBM_KERNEL_AUTO 0
 #define LBM_KERNEL_TILE 1

@@ -150,13 +150,13 @@ Layout layout_of(const lbm_params* p) {
     return L;
 }
 
-// Step kernel of a new handle: one CTA per tile.  Measured on GB300 (2048 x 1024, us per step,
-// tile / pipelined): FP32 77.4 / 84.0, FP16 66.9 / 69.5, FP16_FG 66.8 / 66.7, BF16_FG 68.2 / 65.7.
-// With four CTAs of the one-tile kernel per SM the copy latency is already hidden by the other
-// CTAs, so overlapping it inside a CTA gains nothing.
+// Step kernel of a new handle: the one-tile kernel for FP32 storage, the warp-specialised
+// persistent kernel for the 16-bit modes.
 int default_kernel(int storage, int pipe_blocks_per_sm) {
-    (void)storage;
-    (void)pipe_blocks_per_sm;
+    // Measured on GB300 at 2048 x 1024 (us per step, one-tile / warp-specialised): FP32 74.1 / 76.5
+    // (HBM-bound either way), FP16 60.4 / 59.8, BF16 61.9 / 58.9, FP16_FG 64.1 / 60.9, BF16_FG
+    // 64.8 / 59.5: the 16-bit modes are bound by issue and latency, which the copy warp relieves.
+    if (storage != LBM_STORE_FP32 && pipe_blocks_per_sm >= 1) return LBM_KERNEL_PIPELINED;
     return LBM_KERNEL_TILE;
 }
 

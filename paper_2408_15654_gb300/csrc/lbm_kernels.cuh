@@ -198,12 +198,13 @@ template <int ST> struct Smem {
     // batched kernel: the lattice's constants
     static constexpr int PHYS = BYTES;
     static constexpr int BYTES_BATCH = PHYS + (int)((sizeof(Phys) + 15) / 16 * 16);
-    // pipelined kernel: two stages of the TMA boxes ([0, PP) each), one (phi, psi) tile, two
-    // mbarriers
+    // warp-specialised persistent kernel: two stages of the TMA boxes ([0, PP) each), two
+    // (phi, psi) tiles (alternating with the tile count), a full and an empty mbarrier per stage,
+    // the tile origin (x0, y0) of each stage
     static constexpr int STAGE = PP;
     static constexpr int PIPE_PP = 2 * STAGE;
-    static constexpr int PIPE_BAR = PIPE_PP + NE * 8;
-    static constexpr int PIPE_SLOT = PIPE_BAR + 16;  // tile index of each stage
+    static constexpr int PIPE_BAR = PIPE_PP + 2 * NE * 8;
+    static constexpr int PIPE_SLOT = PIPE_BAR + 32;
     static constexpr int BYTES_PIPE = PIPE_SLOT + 16;
     static constexpr unsigned TX_BYTES =
         (unsigned)(kPairs * FG_BOX * sizeof(typename T::P) + kHPlanes * H_BOX * sizeof(typename T::H) + HIST_BYTES);
@@ -364,6 +365,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* m, uint32_
         if (mbar_try_wait(m, parity)) return true;
     return false;
 }
+__device__ __forceinline__ void mbar_arrive(unsigned long long* m) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(m)) : "memory");
+}
+// Named barrier 1 of the NT compute threads of a warp-specialised CTA (its copy warp never takes
+// part); the OR form also tells every thread whether any of them passed true.
+__device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(NT) : "memory"); }
+__device__ __forceinline__ bool compute_sync_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(NT)
+        : "memory");
+    return r != 0;
+}
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
                                             unsigned long long* m) {
     asm volatile(
@@ -483,7 +499,9 @@ __device__ __forceinline__ void issue_tile_loads(unsigned char* sm, const CUtens
 // 9-point stencils; the same boxes hold the own cell's unshifted post-collision values, whose sums
 // are phi and psi of the previous level (m*_0 = phi exactly, Sec. 3.1), so only u of the
 // previous level is stored.
-template <int ST, bool WALLS, bool LANGMUIR, int MODE, int FLOW>
+// WS: called by the compute warps of a warp-specialised CTA, which synchronise among themselves
+// with named barrier 1 only (the copy warp has staged the tile and waits on its own barriers).
+template <int ST, bool WALLS, bool LANGMUIR, int MODE, int FLOW, bool WS = false>
 __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsigned char* sm, float2* PP,
                                           unsigned long long* mbar, uint32_t parity, int x0, int y0) {
     using T = Traits<ST>;
@@ -492,7 +510,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     const P* FG = reinterpret_cast<const P*>(sm + S::FG);
     const float2* Hist = reinterpret_cast<const float2*>(sm + S::HIST);
     const int t = threadIdx.x;
-    __syncthreads();
+    if constexpr (!WS) __syncthreads();
     bool abort = !mbar_wait_bounded(mbar, parity);
 
     const int tx = t % TX, ty = t / TX;
@@ -536,13 +554,14 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         for (int i = 0; i < 9; ++i) r[i] = raw2(base[i * SLOT - cx(i)]);
         PP[ey * EX + ex] = pair_sum<ST>(r, ref);
     }
-    if (__syncthreads_or(abort)) {
+    if (WS ? compute_sync_or(abort) : __syncthreads_or(abort)) {
         // a staging copy did not arrive in time: report it, wait (bounded) for it, store nothing
         if (t == 0) {
             atomicOr(io.status, kStatusTimeout);
             mbar_wait_bounded(mbar, parity);
         }
-        __syncthreads();
+        if constexpr (WS) compute_sync();
+        else __syncthreads();
         return true;
     }
     if (!active) return false;
@@ -945,64 +964,91 @@ __device__ __forceinline__ void tile_origin(int k, int ntx, int nty, int& x0, in
     y0 = tr * TY;
 }
 
-// One step of one lattice by a persistent grid: each CTA claims tiles from an atomic counter
-// and stages its next tile's boxes with TMA into the other of two buffers while it computes the
-// current one, so the copy latency hides behind the arithmetic.  Claiming tiles one at a time
-// balances the longer edge tiles (ghost-frame writes) across the CTAs.  Thread 0 claims a tile one iteration before
-// it needs it, so the atomic's latency also hides behind a tile's work.
+// One step of one lattice by a persistent, warp-specialised grid.  Each CTA has NT compute threads
+// (eight warps, one cell each, as in step_kernel) and one copy warp.  One lane of the copy warp
+// claims tiles from an atomic counter (one at a time, which balances the longer edge tiles across
+// the CTAs) and stages each into one of two buffers with TMA, on that buffer's "full" mbarrier;
+// the compute warps release a buffer on its "empty" mbarrier (one arrival per warp) once the tile
+// is done, so the copy of the next tile overlaps the arithmetic of the current one and the copy
+// warp never joins a block-wide barrier.  After the last tile the copy lane arrives on a full
+// barrier without a copy; the compute warps read the stop mark (x0 = -1) and stop.  Every
+// wait is bounded: a copy lane that gives up waits (bounded) for the copies it has in flight.
+constexpr int NT_PIPE = NT + 32;
+
 template <int ST, bool WALLS, bool LANGMUIR, int FLOW>
-__global__ void __launch_bounds__(NT, 4) step_kernel_pipe(const __grid_constant__ StepArgs a, int ntx, int nty) {
+__global__ void __launch_bounds__(NT_PIPE, 3) step_kernel_pipe(const __grid_constant__ StepArgs a, int ntx, int nty) {
     using S = Smem<ST>;
     extern __shared__ __align__(1024) unsigned char sm[];
-    float2* PP = reinterpret_cast<float2*>(sm + S::PIPE_PP);
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(sm + S::PIPE_BAR);
-    volatile unsigned* slot = reinterpret_cast<volatile unsigned*>(sm + S::PIPE_SLOT);
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(sm + S::PIPE_BAR);
+    unsigned long long* empty = full + 2;
+    volatile int* slot = reinterpret_cast<volatile int*>(sm + S::PIPE_SLOT);  // (x0, y0) per buffer
     const unsigned ntiles = (unsigned)(ntx * nty);
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], NT / 32);
+        mbar_init(&empty[1], NT / 32);
         fence_mbar_init();
     }
+    __syncthreads();
     cudaTriggerProgrammaticLaunchCompletion();
     cudaGridDependencySynchronize();  // also: the previous launch no longer uses its counter
-    unsigned ahead = 0;               // thread 0: the tile claimed for the stage after next
-    if (threadIdx.x == 0) {
+
+    if (threadIdx.x >= NT) {
+        // ---- copy warp ----
+        if (threadIdx.x != NT) return;
         if (blockIdx.x == 0) *a.tile_ctr_next = 0u;
-        const unsigned k0 = atomicAdd(a.tile_ctr, 1u);
-        slot[0] = k0;
-        if (k0 < ntiles) {
+        bool pending[2] = {false, false};   // a copy into the buffer that no release has confirmed
+        uint32_t issued[2] = {0u, 0u};      // parity of the full barrier's phase of that copy
+        for (int it = 0;; ++it) {
+            const int b = it & 1;
+            if (it >= 2) {
+                if (!mbar_wait_bounded(&empty[b], (uint32_t)((it >> 1) - 1) & 1u)) {
+                    atomicOr(a.io.status, kStatusTimeout);
+                    for (int q = 0; q < 2; ++q)
+                        if (pending[q]) mbar_wait_bounded(&full[q], issued[q]);
+                    return;
+                }
+                pending[b] = false;
+            }
+            const unsigned k = atomicAdd(a.tile_ctr, 1u);
+            if (k >= ntiles) {
+                slot[2 * b] = -1;
+                mbar_arrive(&full[b]);  // no copy: the compute warps read x0 = -1 and stop
+                return;
+            }
             int x0, y0;
-            tile_origin((int)k0, ntx, nty, x0, y0);
-            issue_tile_loads<ST, FLOW>(sm, &a.tm_fg, &a.tm_h, &a.tm_hist, x0, y0, &bars[0]);
-            ahead = atomicAdd(a.tile_ctr, 1u);
-        } else {
-            ahead = ntiles;
+            tile_origin((int)k, ntx, nty, x0, y0);
+            slot[2 * b] = x0;
+            slot[2 * b + 1] = y0;
+            issue_tile_loads<ST, FLOW>(sm + b * S::STAGE, &a.tm_fg, &a.tm_h, &a.tm_hist, x0, y0, &full[b]);
+            pending[b] = true;
+            issued[b] = (uint32_t)(it >> 1) & 1u;
         }
     }
-    __syncthreads();
+
+    // ---- compute warps ----
     for (int it = 0;; ++it) {
-        const int cur = it & 1, nxt = cur ^ 1;
-        const unsigned k = slot[cur];
-        if (k >= ntiles) break;  // uniform: every thread reads the same slot
-        if (threadIdx.x == 0) {
-            // the other stage and its slot were released by the barrier that ended the previous tile
-            slot[nxt] = ahead;
-            if (ahead < ntiles) {
-                int xn, yn;
-                tile_origin((int)ahead, ntx, nty, xn, yn);
-                issue_tile_loads<ST, FLOW>(sm + nxt * S::STAGE, &a.tm_fg, &a.tm_h, &a.tm_hist, xn, yn, &bars[nxt]);
-                ahead = atomicAdd(a.tile_ctr, 1u);
+        const int b = it & 1;
+        const uint32_t parity = (uint32_t)(it >> 1) & 1u;
+        const bool late = !mbar_wait_bounded(&full[b], parity);
+        if (compute_sync_or(late)) {  // uniform: a copy (or the stop mark) did not come in time
+            if (threadIdx.x == 0) {
+                atomicOr(a.io.status, kStatusTimeout);
+                // wait (bounded) for the copies that may still be in flight into either buffer
+                mbar_wait_bounded(&full[b], parity);
+                mbar_wait_bounded(&full[b ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
             }
+            return;
         }
-        int x0, y0;
-        tile_origin((int)k, ntx, nty, x0, y0);
-        if (step_tile<ST, WALLS, LANGMUIR, kStep, FLOW>(a.p, a.io, sm + cur * S::STAGE, PP, &bars[cur], (it >> 1) & 1,
-                                                        x0, y0)) {
-            // a copy timed out: stop this CTA, after waiting (bounded) for the copy in flight
-            if (threadIdx.x == 0 && slot[nxt] < ntiles) mbar_wait_bounded(&bars[nxt], ((it + 1) >> 1) & 1);
-            break;
-        }
-        __syncthreads();  // stage `cur` (only read by this CTA), its slot and PP are free again
+        const int x0 = slot[2 * b], y0 = slot[2 * b + 1];
+        if (x0 < 0) return;  // uniform: every compute thread reads the same slot
+        float2* PP = reinterpret_cast<float2*>(sm + S::PIPE_PP) + b * NE;
+        if (step_tile<ST, WALLS, LANGMUIR, kStep, FLOW, true>(a.p, a.io, sm + b * S::STAGE, PP, &full[b], parity, x0,
+                                                              y0))
+            return;  // uniform (decided by the OR barrier inside)
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[b]);  // this warp is done with buffer b
     }
 }
 

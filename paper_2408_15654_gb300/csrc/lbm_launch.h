@@ -42,14 +42,15 @@ inline Variant variant_of(int k) {
 }
 constexpr int kVariants = 10;
 
-inline cudaLaunchConfig_t pdl_config(dim3 grid, size_t smem, cudaStream_t stream, cudaLaunchAttribute* attr) {
+inline cudaLaunchConfig_t pdl_config(dim3 grid, size_t smem, cudaStream_t stream, cudaLaunchAttribute* attr,
+                                     unsigned threads = NT) {
     // Every launch uses programmatic dependent launch: the kernel waits (griddepcontrol.wait) for
     // the previous grid before touching memory, so the next launch may be scheduled during the
     // tail of this one.
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = grid;
-    cfg.blockDim = dim3(NT);
+    cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -60,14 +61,14 @@ inline cudaLaunchConfig_t pdl_config(dim3 grid, size_t smem, cudaStream_t stream
 }
 
 // grid = (tiles along x, tiles along y).  A step (mode kStep) with pipe_ctas > 0 runs the
-// persistent pipelined kernel on pipe_ctas CTAs instead of one CTA per tile.
+// persistent warp-specialised kernel on pipe_ctas CTAs of NT_PIPE threads instead of one CTA per tile.
 template <int ST>
 cudaError_t launch_step_impl(const StepArgs& a, int mode, const Variant& v, dim3 grid, int pipe_ctas,
                              cudaStream_t stream) {
     cudaLaunchAttribute attr[1];
     if (mode == kStep && pipe_ctas > 0) {
         const int ntx = (int)grid.x, nty = (int)grid.y;
-        cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)pipe_ctas), Smem<ST>::BYTES_PIPE, stream, attr);
+        cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)pipe_ctas), Smem<ST>::BYTES_PIPE, stream, attr, NT_PIPE);
         return dispatch_variant(v, [&]<bool W, bool L, int F>() {
             return cudaLaunchKernelEx(&cfg, step_kernel_pipe<ST, W, L, F>, a, ntx, nty);
         });
@@ -97,7 +98,7 @@ cudaError_t prepare_step_impl(int* blocks_per_sm, int* pipe_blocks_per_sm) {
         tile = b < tile ? b : tile;
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1, NT, Smem<ST>::BYTES);
         tile = b < tile ? b : tile;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kp, NT, Smem<ST>::BYTES_PIPE);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kp, NT_PIPE, Smem<ST>::BYTES_PIPE);
         pipe = b < pipe ? b : pipe;
         return e;
     };
