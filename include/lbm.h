@@ -167,6 +167,14 @@ int lbm_get_moments(lbm_handle* h, unsigned mask, double* const out[5], int mem)
  * Synchronous. */
 int lbm_reduce(lbm_handle* h, int what, double* out);
 
+/* Failure-detection self-test.  Launches one warp on cuda_stream that waits, with the bounded
+ * wait every step kernel uses for its copies, on an mbarrier that nothing completes.  The wait
+ * gives up after at most about one second and records a timeout in d_word (a device pointer to 4
+ * bytes owned by the caller), without faulting: the context stays usable.  Synchronous.
+ * Returns LBM_ETIMEOUT when the timeout was recorded (the expected outcome), LBM_ECUDA if the
+ * launch failed or no timeout was recorded, LBM_EINVAL for a NULL d_word. */
+int lbm_selftest_wait(unsigned* d_word, void* cuda_stream);
+
 /* The sum of lbm_reduce for callers that cannot allocate device memory.  (This entry point has no
  * counterpart in the paper; it exists for the library's users.)  Some callers may not call
  * cudaMalloc: a plugin inside a host application whose memory manager owns all device memory, code

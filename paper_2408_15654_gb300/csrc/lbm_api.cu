@@ -338,6 +338,20 @@ int noalloc_scratch(double** out) {
 
 extern "C" {
 
+int lbm_selftest_wait(unsigned* d_word, void* cuda_stream) {
+    g_err.clear();
+    if (!d_word) return fail(LBM_EINVAL, "NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    LBM_CUDA(cudaMemsetAsync(d_word, 0xFF, sizeof(unsigned), st));
+    lbm::selftest_wait_kernel<<<1, 32, 0, st>>>(d_word);
+    LBM_CUDA(cudaGetLastError());
+    unsigned w = 0;
+    LBM_CUDA(cudaMemcpyAsync(&w, d_word, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    LBM_CUDA(cudaStreamSynchronize(st));
+    if (w == lbm::kStatusTimeout) return fail(LBM_ETIMEOUT, "the bounded wait gave up, as it should");
+    return fail(LBM_ECUDA, "the self-test wait did not report a timeout (word %u)", w);
+}
+
 int lbm_reduce_noalloc(const void* d_pops, int nx, int ny, int what, void* cuda_stream, double* out) {
     g_err.clear();
     if (!d_pops || !out) return fail(LBM_EINVAL, "d_pops and out are required");

@@ -1275,6 +1275,21 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partial_kernel(const vo
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
+// Failure-detection self-test: one warp waits, with the bounded wait of the step kernels, on an
+// mbarrier whose phase nothing completes; the wait gives up and the status word records it.  It
+// exercises the timeout path without a copy in flight, so nothing faults and the context stays
+// usable.
+static __global__ void selftest_wait_kernel(unsigned* __restrict__ status) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);  // one arrival expected; none comes
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool done = mbar_wait_bounded(&bar, 0u);
+    if (threadIdx.x == 0) *status = done ? 0u : kStatusTimeout;
+}
+
 static __global__ void __launch_bounds__(kReduceThreads) reduce_final_kernel(const double* __restrict__ partials, int n,
                                                                       double* __restrict__ out) {
     __shared__ double smem[32];

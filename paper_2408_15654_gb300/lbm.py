@@ -39,7 +39,7 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_init_fields", "lbm_step", "
            "lbm_batch_create", "lbm_batch_set_members", "lbm_batch_set_schedule", "lbm_batch_step",
            "lbm_batch_autotune", "lbm_batch_launches", "lbm_batch_destroy", "lbm_server_workspace_bytes",
            "lbm_server_create", "lbm_server_submit", "lbm_server_poll", "lbm_server_get_stats",
-           "lbm_server_destroy")
+           "lbm_server_destroy", "lbm_selftest_wait")
 
 
 class lbm_params(C.Structure):
@@ -121,6 +121,7 @@ def load(path: str | None = None):
         "lbm_server_poll": [vp, C.POINTER(lbm_job_result), C.c_int, C.c_double, C.POINTER(C.c_int)],
         "lbm_server_get_stats": [vp, C.POINTER(lbm_server_stats)],
         "lbm_server_destroy": [vp],
+        "lbm_selftest_wait": [vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -205,6 +206,11 @@ def lbm_reduce_noalloc(d_pops: int, nx: int, ny: int, what: int, stream_ptr: int
     _check(load().lbm_reduce_noalloc(C.c_void_p(d_pops), int(nx), int(ny), int(what), C.c_void_p(stream_ptr),
                                      C.byref(v)))
     return v.value
+
+
+def lbm_selftest_wait(d_word: int, stream_ptr: int) -> int:
+    """The failure-detection self-test (a bounded wait that must give up); returns the status code."""
+    return load().lbm_selftest_wait(C.c_void_p(d_word), C.c_void_p(stream_ptr))
 
 
 def lbm_status(h: int) -> int:
