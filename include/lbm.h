@@ -262,8 +262,8 @@ typedef struct lbm_batch lbm_batch;
 int lbm_batch_tiles(lbm_handle* const* members, int n, int64_t* tiles);
 
 /* Device workspace of a batch of up to max_members lattices with up to max_tiles tiles in total:
- * one descriptor per member (TMA maps, constants, buffer pointers, step count) and the tile
- * list, each 256-byte aligned. */
+ * one descriptor per member (TMA maps, constants, buffer pointers, step count), the tile list and
+ * the two tile counters of the warp-specialised kernel, each 256-byte aligned. */
 int lbm_batch_workspace_bytes(int max_members, int64_t max_tiles, size_t* bytes);
 
 /* Create an empty batch enqueuing its work on cuda_stream.  CUDA graphs (lbm_batch_set_schedule)
@@ -288,6 +288,17 @@ int lbm_batch_step(lbm_batch* b, int64_t n);
  * advances by 4 * (16 + trial_steps rounded up to a multiple of 16) + 1 + trial_steps steps
  * (without graphs, on the legacy default stream: 4 * (1 + trial_steps)).  Synchronous. */
 int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* schedule, int* graph_steps);
+
+/* Kernel of the batch's launches; both give the same results bit for bit:
+ *   LBM_KERNEL_TILE       one CTA per tile of the tile list;
+ *   LBM_KERNEL_PIPELINED  persistent, warp-specialised CTAs: a copy warp claims tiles from a
+ *                         counter in the workspace and stages each tile's boxes and its lattice's
+ *                         constants while eight compute warps work on the previous tile;
+ *   LBM_KERNEL_AUTO       the default: PIPELINED for the groups of FP32 members, TILE for
+ *                         16-bit groups (the faster ones on GB300 with a 64-lattice mix).
+ * PIPELINED applies only if it fits (else TILE).  lbm_batch_get_kernel reports the setting. */
+int lbm_batch_set_kernel(lbm_batch* b, int variant);
+int lbm_batch_get_kernel(const lbm_batch* b, int* variant);
 
 /* Kernels this batch has launched so far (a graph replay counts its kernels). */
 int lbm_batch_launches(const lbm_batch* b, int64_t* launches);

@@ -111,8 +111,9 @@ __host__ __device__ constexpr bool h_is_16bit(int st) { return st == kFP16 || st
 // the x coordinate of every box a multiple of 16 bytes (boxes start 4 or 8 cells left of a tile).
 constexpr int kGX = 8, kGY = 2;
 
-// Physical constants in FP32, precomputed on the host from lbm_params.
-struct Phys {
+// Physical constants in FP32, precomputed on the host from lbm_params.  16-byte aligned and sized
+// so that the batched kernel can stage a lattice's copy with one bulk copy.
+struct alignas(16) Phys {
     int nx, ny, pitch, pad0;
     long long plane;          // cells per plane ((ny + 2 kGY) * pitch)
     long long org;            // index of cell (0, 0): kGY * pitch + kGX
@@ -206,6 +207,12 @@ template <int ST> struct Smem {
     static constexpr int PIPE_BAR = PIPE_PP + 2 * NE * 8;
     static constexpr int PIPE_SLOT = PIPE_BAR + 32;
     static constexpr int BYTES_PIPE = PIPE_SLOT + 16;
+    // warp-specialised batch kernel: the same buffers and barriers, a 4-word slot per buffer
+    // (x0, y0, lattice, current population buffer) and per buffer the lattice's constants
+    static constexpr int PHYS_BYTES = (int)sizeof(Phys);
+    static constexpr int BWS_SLOT = PIPE_BAR + 32;
+    static constexpr int BWS_PHYS = BWS_SLOT + 32;
+    static constexpr int BYTES_BWS = BWS_PHYS + 2 * PHYS_BYTES;
     static constexpr unsigned TX_BYTES =
         (unsigned)(kPairs * FG_BOX * sizeof(typename T::P) + kHPlanes * H_BOX * sizeof(typename T::H) + HIST_BYTES);
     static constexpr unsigned TX_BYTES_NOH = (unsigned)(kPairs * FG_BOX * sizeof(typename T::P) + HIST_BYTES);
@@ -364,6 +371,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* m, uint32_
     for (unsigned it = 0; it < kWaitLimit; ++it)
         if (mbar_try_wait(m, parity)) return true;
     return false;
+}
+// Raise the transaction count of the current phase without arriving (for a copy issued before the
+// arrival that completes the phase's expectations).
+__device__ __forceinline__ void mbar_expect_tx_only(unsigned long long* m, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+// Untiled bulk copy global -> shared on an mbarrier (both addresses 16-byte aligned, size a
+// multiple of 16 bytes).
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* m) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(m))
+        : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(unsigned long long* m) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(m)) : "memory");
@@ -1074,7 +1094,18 @@ struct BatchArgs {
     const InstDesc* __restrict__ descs;
     const uint2* __restrict__ tiles;
     int s;
+    // warp-specialised kernel only (ws_ctas > 0): the tile count, the persistent grid, the member
+    // count, this launch's tile counter (zero at its start) and the next launch's (zeroed by this one)
+    int ntiles, ws_ctas, ndescs;
+    unsigned* ctr;
+    unsigned* ctr_next;
 };
+
+// A bounded wait of the batched warp-specialised kernel gave up: flag every member (the stalled
+// tile's lattice is not known to every thread that sees the timeout).
+__device__ __forceinline__ void flag_batch_timeout(const BatchArgs& b) {
+    for (int k = 0; k < b.ndescs; ++k) atomicOr(b.descs[k].status, kStatusTimeout);
+}
 
 template <int ST, bool WALLS, bool LANGMUIR, int FLOW>
 __global__ void __launch_bounds__(NT, 4) batch_step_kernel(const __grid_constant__ BatchArgs b) {
@@ -1109,6 +1140,119 @@ __global__ void __launch_bounds__(NT, 4) batch_step_kernel(const __grid_constant
     io.seed = step_seed(d.steps + b.s);
     io.first = d.first && b.s == 0;
     step_tile<ST, WALLS, LANGMUIR, kStep, FLOW>(*sp, io, sm, reinterpret_cast<float2*>(sm + S::PP), mbar, 0, x0, y0);
+}
+
+// One step of many lattices by a persistent, warp-specialised grid (the design of step_kernel_pipe).
+// The copy lane claims entries of the tile list from this launch's counter; for each it reads the
+// lattice's current buffer, stages the lattice's constants (one bulk copy) and the tile's boxes
+// (TMA) into a buffer on its full barrier.  It works one tile ahead: the claim, list entry and
+// descriptor read of the next tile are in flight while it waits for a buffer, so these dependent
+// loads overlap the arithmetic instead of delaying every tile.
+template <int ST, bool WALLS, bool LANGMUIR, int FLOW>
+__global__ void __launch_bounds__(NT_PIPE, 3) batch_step_kernel_ws(const __grid_constant__ BatchArgs b) {
+    using S = Smem<ST>;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(sm + S::PIPE_BAR);
+    unsigned long long* empty = full + 2;
+    volatile int* slot = reinterpret_cast<volatile int*>(sm + S::BWS_SLOT);  // x0, y0, lattice, cur per buffer
+    const unsigned ntiles = (unsigned)b.ntiles;
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], NT / 32);
+        mbar_init(&empty[1], NT / 32);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    cudaTriggerProgrammaticLaunchCompletion();
+    cudaGridDependencySynchronize();  // descriptors and populations of the previous launch
+
+    if (threadIdx.x >= NT) {
+        // ---- copy warp ----
+        if (threadIdx.x != NT) return;
+        if (blockIdx.x == 0) *b.ctr_next = 0u;
+        bool pending[2] = {false, false};
+        uint32_t issued[2] = {0u, 0u};
+        // the tile of the current iteration, claimed and read one iteration ahead
+        unsigned k = atomicAdd(b.ctr, 1u);
+        uint2 te = make_uint2(0u, 0u);
+        int cur = 0;
+        if (k < ntiles) {
+            te = b.tiles[k];
+            cur = (b.descs[te.x].cur + b.s) & 1;
+        }
+        for (int it = 0;; ++it) {
+            const int q = it & 1;
+            const unsigned kn = k < ntiles ? atomicAdd(b.ctr, 1u) : ntiles;  // the next claim, early
+            if (it >= 2) {
+                if (!mbar_wait_bounded(&empty[q], (uint32_t)((it >> 1) - 1) & 1u)) {
+                    flag_batch_timeout(b);
+                    for (int r = 0; r < 2; ++r)
+                        if (pending[r]) mbar_wait_bounded(&full[r], issued[r]);
+                    return;
+                }
+                pending[q] = false;
+            }
+            if (k >= ntiles) {
+                slot[4 * q] = -1;
+                mbar_arrive(&full[q]);  // no copy: the compute warps read x0 = -1 and stop
+                return;
+            }
+            const InstDesc* d = &b.descs[te.x];
+            const int x0 = (int)(te.y & 0xFFFFu) * TX, y0 = (int)(te.y >> 16) * TY;
+            slot[4 * q] = x0;
+            slot[4 * q + 1] = y0;
+            slot[4 * q + 2] = (int)te.x;
+            slot[4 * q + 3] = cur;
+            mbar_expect_tx_only(&full[q], (uint32_t)S::PHYS_BYTES);
+            bulk_copy_g2s(sm + S::BWS_PHYS + q * S::PHYS_BYTES, &d->p, (uint32_t)S::PHYS_BYTES, &full[q]);
+            issue_tile_loads<ST, FLOW>(sm + q * S::STAGE, &d->tm_fg[cur], &d->tm_h[cur], &d->tm_hist[cur], x0, y0, &full[q]);
+            pending[q] = true;
+            issued[q] = (uint32_t)(it >> 1) & 1u;
+            // read the next tile's list entry and buffer now; they arrive while this lane waits
+            k = kn;
+            if (k < ntiles) {
+                te = b.tiles[k];
+                cur = (b.descs[te.x].cur + b.s) & 1;
+            }
+        }
+    }
+
+    // ---- compute warps ----
+    for (int it = 0;; ++it) {
+        const int q = it & 1;
+        const uint32_t parity = (uint32_t)(it >> 1) & 1u;
+        const bool late = !mbar_wait_bounded(&full[q], parity);
+        if (compute_sync_or(late)) {
+            if (threadIdx.x == 0) {
+                flag_batch_timeout(b);
+                mbar_wait_bounded(&full[q], parity);
+                mbar_wait_bounded(&full[q ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
+            }
+            return;
+        }
+        const int x0 = slot[4 * q], y0 = slot[4 * q + 1];
+        if (x0 < 0) return;  // uniform: every compute thread reads the same slot
+        const int lat = slot[4 * q + 2], cur = slot[4 * q + 3];
+        const InstDesc& d = b.descs[lat];
+        TileIO io;
+        io.src = d.pops[cur];
+        io.dst = d.pops[cur ^ 1];
+        io.hist_src = d.hist[cur];
+        io.hist_dst = d.hist[cur ^ 1];
+        io.shist_src = d.shist[cur];
+        io.shist_dst = d.shist[cur ^ 1];
+        io.status = d.status;
+        io.out[0] = io.out[1] = io.out[2] = io.out[3] = io.out[4] = nullptr;
+        io.seed = step_seed(d.steps + b.s);
+        io.first = d.first && b.s == 0;
+        const Phys& p = *reinterpret_cast<const Phys*>(sm + S::BWS_PHYS + q * S::PHYS_BYTES);
+        float2* PP = reinterpret_cast<float2*>(sm + S::PIPE_PP) + q * NE;
+        if (step_tile<ST, WALLS, LANGMUIR, kStep, FLOW, true>(p, io, sm + q * S::STAGE, PP, &full[q], parity, x0, y0))
+            return;
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[q]);
+    }
 }
 
 // After a sequence of n launches: advance every descriptor by n steps.

@@ -109,25 +109,43 @@ cudaError_t prepare_step_impl(int* blocks_per_sm, int* pipe_blocks_per_sm) {
     return e;
 }
 
-// One launch of the many-lattice kernel over `ntiles` tiles (all lattices of one variant).
+// One launch of the many-lattice kernel over `ntiles` tiles (all lattices of one variant): one CTA
+// per tile, or (b.ws_ctas > 0) the persistent warp-specialised kernel on b.ws_ctas CTAs.
 template <int ST>
 cudaError_t launch_batch_impl(const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t stream) {
     cudaLaunchAttribute attr[1];
+    if (b.ws_ctas > 0) {
+        cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)b.ws_ctas), Smem<ST>::BYTES_BWS, stream, attr, NT_PIPE);
+        return dispatch_variant(v, [&]<bool W, bool L, int F>() {
+            return cudaLaunchKernelEx(&cfg, batch_step_kernel_ws<ST, W, L, F>, b);
+        });
+    }
     cudaLaunchConfig_t cfg = pdl_config(dim3(ntiles), Smem<ST>::BYTES_BATCH, stream, attr);
     return dispatch_variant(v, [&]<bool W, bool L, int F>() {
         return cudaLaunchKernelEx(&cfg, batch_step_kernel<ST, W, L, F>, b);
     });
 }
 
+// Opt both batch kernels of storage mode ST into their shared memory; resident CTAs per SM of the
+// warp-specialised one (the minimum over the variants).
 template <int ST>
-cudaError_t prepare_batch_impl() {
+cudaError_t prepare_batch_impl(int* ws_blocks_per_sm) {
     cudaError_t e = cudaSuccess;
+    int ws = 1 << 30;
     for (int k = 0; k < kVariants && e == cudaSuccess; ++k) {
         e = dispatch_variant(variant_of(k), [&]<bool W, bool L, int F>() {
-            return cudaFuncSetAttribute(batch_step_kernel<ST, W, L, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        Smem<ST>::BYTES_BATCH);
+            cudaError_t r = cudaFuncSetAttribute(batch_step_kernel<ST, W, L, F>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES_BATCH);
+            auto kw = batch_step_kernel_ws<ST, W, L, F>;
+            if (r == cudaSuccess)
+                r = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES_BWS);
+            int bl = 0;
+            if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, kw, NT_PIPE, Smem<ST>::BYTES_BWS);
+            ws = bl < ws ? bl : ws;
+            return r;
         });
     }
+    *ws_blocks_per_sm = ws;
     return e;
 }
 
@@ -135,14 +153,14 @@ cudaError_t prepare_batch_impl() {
 cudaError_t launch_step(int st, const StepArgs& a, int mode, const Variant& v, dim3 grid, int pipe, cudaStream_t s);
 cudaError_t prepare_step(int st, int* blocks_per_sm, int* pipe_blocks_per_sm);
 cudaError_t launch_batch(int st, const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t s);
-cudaError_t prepare_batch(int st);
+cudaError_t prepare_batch(int st, int* ws_blocks_per_sm);
 
 #define LBM_DECLARE_STORAGE(name)                                                                                  \
     cudaError_t launch_step_##name(const StepArgs& a, int mode, const Variant& v, dim3 grid, int pipe,              \
                                    cudaStream_t s);                                                                \
     cudaError_t prepare_step_##name(int* blocks_per_sm, int* pipe_blocks_per_sm);                                   \
     cudaError_t launch_batch_##name(const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t s);         \
-    cudaError_t prepare_batch_##name();
+    cudaError_t prepare_batch_##name(int* ws_blocks_per_sm);
 LBM_DECLARE_STORAGE(fp32)
 LBM_DECLARE_STORAGE(fp16)
 LBM_DECLARE_STORAGE(bf16)
@@ -162,6 +180,6 @@ LBM_DECLARE_STORAGE(bf16fg)
     cudaError_t launch_batch_##name(const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t s) {        \
         return launch_batch_impl<ST>(b, v, ntiles, s);                                                            \
     }                                                                                                              \
-    cudaError_t prepare_batch_##name() { return prepare_batch_impl<ST>(); }
+    cudaError_t prepare_batch_##name(int* ws_blocks_per_sm) { return prepare_batch_impl<ST>(ws_blocks_per_sm); }
 
 }  // namespace lbm

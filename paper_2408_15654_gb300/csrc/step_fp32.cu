@@ -36,13 +36,13 @@ cudaError_t launch_batch(int st, const BatchArgs& b, const Variant& v, unsigned 
     }
 }
 
-cudaError_t prepare_batch(int st) {
+cudaError_t prepare_batch(int st, int* ws_blocks_per_sm) {
     switch (st) {
-        case kFP16: return prepare_batch_fp16();
-        case kBF16: return prepare_batch_bf16();
-        case kFP16FG: return prepare_batch_fp16fg();
-        case kBF16FG: return prepare_batch_bf16fg();
-        default: return prepare_batch_fp32();
+        case kFP16: return prepare_batch_fp16(ws_blocks_per_sm);
+        case kBF16: return prepare_batch_bf16(ws_blocks_per_sm);
+        case kFP16FG: return prepare_batch_fp16fg(ws_blocks_per_sm);
+        case kBF16FG: return prepare_batch_bf16fg(ws_blocks_per_sm);
+        default: return prepare_batch_fp32(ws_blocks_per_sm);
     }
 }
 

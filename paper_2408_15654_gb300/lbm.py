@@ -39,7 +39,7 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_init_fields", "lbm_step", "
            "lbm_batch_create", "lbm_batch_set_members", "lbm_batch_set_schedule", "lbm_batch_step",
            "lbm_batch_autotune", "lbm_batch_launches", "lbm_batch_destroy", "lbm_server_workspace_bytes",
            "lbm_server_create", "lbm_server_submit", "lbm_server_poll", "lbm_server_get_stats",
-           "lbm_server_destroy", "lbm_selftest_wait")
+           "lbm_server_destroy", "lbm_selftest_wait", "lbm_batch_set_kernel", "lbm_batch_get_kernel")
 
 
 class lbm_params(C.Structure):
@@ -122,6 +122,8 @@ def load(path: str | None = None):
         "lbm_server_get_stats": [vp, C.POINTER(lbm_server_stats)],
         "lbm_server_destroy": [vp],
         "lbm_selftest_wait": [vp, vp],
+        "lbm_batch_set_kernel": [vp, C.c_int],
+        "lbm_batch_get_kernel": [vp, C.POINTER(C.c_int)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -354,6 +356,16 @@ def lbm_batch_autotune(b: int, trial_steps: int):
     return s.value, k.value
 
 
+def lbm_batch_set_kernel(b: int, variant: int):
+    _check(load().lbm_batch_set_kernel(C.c_void_p(b), int(variant)))
+
+
+def lbm_batch_get_kernel(b: int) -> int:
+    v = C.c_int()
+    _check(load().lbm_batch_get_kernel(C.c_void_p(b), C.byref(v)))
+    return v.value
+
+
 def lbm_batch_launches(b: int) -> int:
     v = C.c_int64()
     _check(load().lbm_batch_launches(C.c_void_p(b), C.byref(v)))
@@ -402,6 +414,14 @@ class Batch:
     @property
     def launches(self) -> int:
         return lbm_batch_launches(self.handle)
+
+    @property
+    def kernel(self) -> str:
+        return {v: k for k, v in KERNELS.items()}[lbm_batch_get_kernel(self.handle)]
+
+    @kernel.setter
+    def kernel(self, name: str):
+        lbm_batch_set_kernel(self.handle, KERNELS[name])
 
     def close(self):
         if getattr(self, "handle", None):

@@ -59,13 +59,19 @@ def alone_states(torch, cases, steps, stream):
 
 @pytest.mark.parametrize("schedule", lbm.SCHEDULES)
 @pytest.mark.parametrize("graph_steps", [0, 4])
-def test_batch_bitwise_equals_alone(torch, schedule, graph_steps):
+@pytest.mark.parametrize("kernel", ["auto", "tile", "pipelined"])
+def test_batch_bitwise_equals_alone(torch, schedule, graph_steps, kernel):
+    """Every schedule, with and without graphs, with each batch kernel; 5 + 8 steps run as graph
+    replays and plain launches mixed, which also exercises the alternating tile counters of the
+    warp-specialised kernel across replays."""
     stream = torch.cuda.Stream()
     cases = mixed_cases()
     steps = 13  # three 4-step graphs and a remainder
     ref = alone_states(torch, cases, steps, stream)
     lats = make(torch, cases, stream)
     b = lbm.Batch(lats, stream)
+    b.kernel = kernel
+    assert b.kernel == kernel
     b.set_schedule(schedule, graph_steps)
     b.step(5)
     b.step(steps - 5)
