@@ -987,7 +987,8 @@ __device__ __forceinline__ void tile_origin(int k, int ntx, int nty, int& x0, in
 // One step of one lattice by a persistent, warp-specialised grid.  Each CTA has NT compute threads
 // (eight warps, one cell each, as in step_kernel) and one copy warp.  One lane of the copy warp
 // claims tiles from an atomic counter (one at a time, which balances the longer edge tiles across
-// the CTAs) and stages each into one of two buffers with TMA, on that buffer's "full" mbarrier;
+// the CTAs; each claim one iteration ahead, so its latency overlaps the wait for a buffer) and
+// stages each into one of two buffers with TMA, on that buffer's "full" mbarrier;
 // the compute warps release a buffer on its "empty" mbarrier (one arrival per warp) once the tile
 // is done, so the copy of the next tile overlaps the arithmetic of the current one and the copy
 // warp never joins a block-wide barrier.  After the last tile the copy lane arrives on a full
@@ -1020,8 +1021,10 @@ __global__ void __launch_bounds__(NT_PIPE, 3) step_kernel_pipe(const __grid_cons
         if (blockIdx.x == 0) *a.tile_ctr_next = 0u;
         bool pending[2] = {false, false};   // a copy into the buffer that no release has confirmed
         uint32_t issued[2] = {0u, 0u};      // parity of the full barrier's phase of that copy
+        unsigned k = atomicAdd(a.tile_ctr, 1u);  // claimed one iteration ahead of its use
         for (int it = 0;; ++it) {
             const int b = it & 1;
+            const unsigned kn = k < ntiles ? atomicAdd(a.tile_ctr, 1u) : ntiles;  // the next claim, early
             if (it >= 2) {
                 if (!mbar_wait_bounded(&empty[b], (uint32_t)((it >> 1) - 1) & 1u)) {
                     atomicOr(a.io.status, kStatusTimeout);
@@ -1031,7 +1034,6 @@ __global__ void __launch_bounds__(NT_PIPE, 3) step_kernel_pipe(const __grid_cons
                 }
                 pending[b] = false;
             }
-            const unsigned k = atomicAdd(a.tile_ctr, 1u);
             if (k >= ntiles) {
                 slot[2 * b] = -1;
                 mbar_arrive(&full[b]);  // no copy: the compute warps read x0 = -1 and stop
@@ -1044,6 +1046,7 @@ __global__ void __launch_bounds__(NT_PIPE, 3) step_kernel_pipe(const __grid_cons
             issue_tile_loads<ST, FLOW>(sm + b * S::STAGE, &a.tm_fg, &a.tm_h, &a.tm_hist, x0, y0, &full[b]);
             pending[b] = true;
             issued[b] = (uint32_t)(it >> 1) & 1u;
+            k = kn;
         }
     }
 
