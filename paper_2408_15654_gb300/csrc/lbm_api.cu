@@ -59,8 +59,9 @@ int get_encoder(EncodeTiledFn* fn) {
 }
 
 // 3-D tensor map {nx, ny, planes} of elements of es bytes (8: float pairs, 4: floats or
-// 16-bit pairs, 2: 16-bit values); pitch and plane stride counted in elements.  The maps of the
-// step cover whole planes including the ghost frame (nx = pitch, ny = rows of a plane).
+// 16-bit pairs, 2: 16-bit values); pitch and plane stride counted in elements.  The step's load
+// maps cover whole planes including the ghost frame (nx = pitch, ny = rows of a plane); its store
+// maps end at the grid's last column and row.
 int encode_map(CUtensorMap* tm, void* base, int es, int nx, int ny, int planes, int pitch, size_t plane,
                unsigned bw, unsigned bh, unsigned bp) {
     EncodeTiledFn enc;
@@ -239,6 +240,7 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
     a.tm_fg = h->tm_fg[h->cur];
     a.tm_h = h->tm_h[h->cur];
     a.tm_hist = h->tm_hist[h->cur];
+    a.tm_st_fg = h->tm_st_fg[h->cur ^ 1];
     a.p = h->phys;
     a.io.first = h->first;
     a.io.src = h->pops[h->cur];
@@ -433,6 +435,11 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
         char* hbase = static_cast<char*>(h->pops[b]) + (size_t)lbm::kPairs * L.plane * es_pair;
         if (!rc && p->velocity == LBM_VELOCITY_SOLVED)  // no h planes with a prescribed velocity
             rc = encode_map(&h->tm_h[b], hbase, es_h, L.pitch, p->ny + 2 * lbm::kGY, lbm::kHPlanes, L.pitch, L.plane, hbw, lbm::TY, 1);
+        // the persistent kernel's row stores of the pairs with FP32 h (tiles wholly inside the
+        // grid in x, rows inside it); the extents end at the last grid column and row
+        if (!rc && pair16 && !h16)
+            rc = encode_map(&h->tm_st_fg[b], h->pops[b], es_pair, lbm::kGX + p->nx, lbm::kGY + p->ny, lbm::kPairs, L.pitch,
+                            L.plane, lbm::TX, 1, lbm::kPairs);
     }
     for (int b = 0; b < 2 && !rc; ++b)
         rc = h16 ? encode_map(&h->tm_hist[b], h->hist[b], 8, L.pitch, p->ny + 2 * lbm::kGY, 1, L.pitch, L.plane, lbm::BW, lbm::BH, 1)

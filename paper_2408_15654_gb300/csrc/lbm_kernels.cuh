@@ -206,7 +206,15 @@ template <int ST> struct Smem {
     static constexpr int PIPE_PP = 2 * STAGE;
     static constexpr int PIPE_BAR = PIPE_PP + 2 * NE * 8;
     static constexpr int PIPE_SLOT = PIPE_BAR + 32;
-    static constexpr int BYTES_PIPE = PIPE_SLOT + 16;
+    // 16-bit pairs with FP32 h (FP16_FG, BF16_FG): per compute warp a staging row of its cells'
+    // post-collision pairs, [plane][TX] as the bulk tensor store reads it; h goes out with plain
+    // stores (staging it too would cost the third CTA per SM).  The all-16-bit modes keep plain
+    // stores: with the pairs and h staged their step issued more instructions, not fewer.
+    static constexpr bool kTS = T::kPair16 && !T::kH16;
+    static constexpr int STG_W = kPairs * TX * (int)sizeof(typename T::P);
+    static constexpr int PIPE_STG = round128(PIPE_SLOT + 16);
+    static constexpr int BYTES_PIPE = kTS ? PIPE_STG + TY * STG_W : PIPE_SLOT + 16;
+    static_assert(STG_W % 128 == 0, "staging rows keep 128-byte alignment");
     // warp-specialised batch kernel: the same buffers and barriers, a 4-word slot per buffer
     // (x0, y0, lattice, current population buffer) and per buffer the lattice's constants
     static constexpr int PHYS_BYTES = (int)sizeof(Phys);
@@ -223,6 +231,7 @@ struct StepArgs {
     CUtensorMap tm_fg;            // {nx, ny, 9} pairs, box {BW, BH, 1}
     CUtensorMap tm_h;             // {nx, ny, 8} h values, box {H_BW, TY, 1}
     CUtensorMap tm_hist;          // {nx, ny, 1} float2, box {TX, TY, 1} or {BW, BH, 1}
+    CUtensorMap tm_st_fg;         // destination pairs {kGX + nx, kGY + ny, 9}, box {TX, 1, 9} (16-bit pairs, FP32 h)
     Phys p;
     TileIO io;
     unsigned* tile_ctr;           // pipelined kernel: tile counter of this launch (zero at start)
@@ -408,6 +417,21 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
         "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(m))
         : "memory");
 }
+// Bulk tensor store shared -> global of one box (source 128-byte aligned); the writes that fall
+// outside the tensor map's extents are dropped.  The issuing thread tracks it in its bulk group.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, const void* src, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// The issuing thread's bulk stores have read their shared-memory source (it may be rewritten).
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// The issuing thread's bulk stores are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// Generic-proxy writes to shared memory made visible to a later bulk copy (async proxy).
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 // Moment-space MRT collision of the (f, g) pair, applied as an increment so that FP32 rounding
 // stays at the scale of the departure from equilibrium (in a uniform bulk nothing changes):
@@ -521,9 +545,10 @@ __device__ __forceinline__ void issue_tile_loads(unsigned char* sm, const CUtens
 // previous level is stored.
 // WS: called by the compute warps of a warp-specialised CTA, which synchronise among themselves
 // with named barrier 1 only (the copy warp has staged the tile and waits on its own barriers).
-template <int ST, bool WALLS, bool LANGMUIR, int MODE, int FLOW, bool WS = false>
+template <int ST, bool WALLS, bool LANGMUIR, int MODE, int FLOW, bool WS = false, bool TS = false>
 __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsigned char* sm, float2* PP,
-                                          unsigned long long* mbar, uint32_t parity, int x0, int y0) {
+                                          unsigned long long* mbar, uint32_t parity, int x0, int y0,
+                                          unsigned char* stg = nullptr) {
     using T = Traits<ST>;
     using S = Smem<ST>;
     using P = typename T::P;
@@ -891,7 +916,19 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         const bool xl = x <= 1, xr = x >= p.nx - 2;
         const bool yl = !WALLS && y <= 1, yr = !WALLS && y >= p.ny - 2;
         const long long DX = p.nx, DY = (long long)p.ny * p.pitch;
-        put((long long)cell);
+        if constexpr (TS) {
+            // the own cell into the warp's staging row (the warp is the tile row, tx the lane); the
+            // caller writes the row out (store_staged_row)
+            P* sp = reinterpret_cast<P*>(stg) + tx;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) sp[i * TX] = outp[i];
+            if constexpr (FLOW) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) dh[i * pl + cell] = outh[i];
+            }
+        } else {
+            put((long long)cell);
+        }
         if (xl | xr | yl | yr) {
             if (xl) put(cell + DX);
             if (xr) put(cell - DX);
@@ -996,6 +1033,33 @@ __device__ __forceinline__ void tile_origin(int k, int ntx, int nty, int& x0, in
 // wait is bounded: a copy lane that gives up waits (bounded) for the copies it has in flight.
 constexpr int NT_PIPE = NT + 32;
 
+// Writes the staged own pairs of tile row y0 + warp (see Smem::kTS).  A tile that lies wholly
+// inside the grid in x goes out as one bulk tensor store, issued by lane 0 and tracked in its bulk
+// group.  The ragged last tile column ends next
+// to the ghost columns that hold the periodic images of x = 0, 1, which plain stores write in the
+// same step; its lanes copy their own cells with plain stores, so no bulk store depends on
+// clipping at the map's extent.
+template <int ST>
+__device__ __forceinline__ void store_staged_row(const StepArgs& a, const unsigned char* stg, int x0, int y0,
+                                                 int warp, int lane) {
+    using P = typename Traits<ST>::P;
+    const int y = y0 + warp;
+    if (x0 + TX <= a.p.nx) {
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0 && y < a.p.ny) {
+            tma_store_3d(&a.tm_st_fg, stg, kGX + x0, kGY + y, 0);
+            bulk_commit();
+        }
+    } else if (x0 + lane < a.p.nx && y < a.p.ny) {
+        const long long pl = a.p.plane, cell = a.p.org + (long long)y * a.p.pitch + x0 + lane;
+        P* dfg = static_cast<P*>(a.io.dst);
+        const P* sp = reinterpret_cast<const P*>(stg) + lane;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dfg[i * pl + cell] = sp[i * TX];
+    }
+}
+
 template <int ST, bool WALLS, bool LANGMUIR, int FLOW>
 __global__ void __launch_bounds__(NT_PIPE, 3) step_kernel_pipe(const __grid_constant__ StepArgs a, int ntx, int nty) {
     using S = Smem<ST>;
@@ -1051,9 +1115,14 @@ __global__ void __launch_bounds__(NT_PIPE, 3) step_kernel_pipe(const __grid_cons
     }
 
     // ---- compute warps ----
+    const int warp = (int)threadIdx.x / 32, lane = (int)threadIdx.x % 32;
+    unsigned char* stg = sm + S::PIPE_STG + warp * S::STG_W;  // this warp's staging row (see Smem::kTS)
     for (int it = 0;; ++it) {
         const int b = it & 1;
         const uint32_t parity = (uint32_t)(it >> 1) & 1u;
+        // the previous tile's bulk stores have read the staging row before the barrier below, so
+        // the warp may rewrite it after the barrier
+        if (S::kTS && lane == 0) bulk_wait_read();
         const bool late = !mbar_wait_bounded(&full[b], parity);
         if (compute_sync_or(late)) {  // uniform: a copy (or the stop mark) did not come in time
             if (threadIdx.x == 0) {
@@ -1062,17 +1131,20 @@ __global__ void __launch_bounds__(NT_PIPE, 3) step_kernel_pipe(const __grid_cons
                 mbar_wait_bounded(&full[b], parity);
                 mbar_wait_bounded(&full[b ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
             }
-            return;
+            break;
         }
         const int x0 = slot[2 * b], y0 = slot[2 * b + 1];
-        if (x0 < 0) return;  // uniform: every compute thread reads the same slot
+        if (x0 < 0) break;  // uniform: every compute thread reads the same slot
         float2* PP = reinterpret_cast<float2*>(sm + S::PIPE_PP) + b * NE;
-        if (step_tile<ST, WALLS, LANGMUIR, kStep, FLOW, true>(a.p, a.io, sm + b * S::STAGE, PP, &full[b], parity, x0,
-                                                              y0))
-            return;  // uniform (decided by the OR barrier inside)
+        if (step_tile<ST, WALLS, LANGMUIR, kStep, FLOW, true, S::kTS>(a.p, a.io, sm + b * S::STAGE, PP, &full[b],
+                                                                      parity, x0, y0, stg))
+            break;  // uniform (decided by the OR barrier inside)
+        if constexpr (S::kTS) store_staged_row<ST>(a, stg, x0, y0, warp, lane);
         __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[b]);  // this warp is done with buffer b
+        if (lane == 0) mbar_arrive(&empty[b]);  // this warp is done with buffer b
     }
+    // the bulk stores are complete before the CTA's shared memory goes away
+    if (S::kTS && lane == 0) bulk_wait_all();
 }
 
 // ---- many lattices in one launch ----

@@ -1,5 +1,7 @@
-"""The two step kernels (one CTA per tile; persistent CTAs with a double-buffered TMA pipeline)
-compute the same step bit for bit, in every storage mode, on ragged and full-size grids."""
+"""The two step kernels (one CTA per tile; persistent CTAs with a double-buffered TMA pipeline,
+whose 16-bit variants write the own cells with bulk tensor stores) compute the same step bit for
+bit, in every storage mode and flow variant, on ragged and full-size grids; the comparison covers
+the whole state, ghost frame included."""
 import pytest
 
 from paper_2408_15654_gb300 import lbm
@@ -26,6 +28,11 @@ def cases():
     yield "walls_45x19_perturbed", p, W.perturbed(p, f, seed=2)
     p, f = W.shear_drop(20, 6, R=2.5)
     yield "below_one_tile", p, f
+    p, f = W.rising_bubble(7.0)
+    yield "density_ratio_walls_28x56_perturbed", p, W.perturbed(p, f, seed=3)
+    yield "density_ratio_periodic_28x56_perturbed", dict(p, walls=False), W.perturbed(p, f, seed=4)
+    p, f = W.convected_drop(70, 45, R=10)
+    yield "prescribed_70x45", p, f
 
 
 def run(torch, p, f, kernel, steps):
