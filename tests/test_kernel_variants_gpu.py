@@ -28,11 +28,19 @@ def cases():
     yield "walls_45x19_perturbed", p, W.perturbed(p, f, seed=2)
     p, f = W.shear_drop(20, 6, R=2.5)
     yield "below_one_tile", p, f
+    # widths that are multiples of the tile width: every tile column is whole, so the FP16_FG and
+    # BF16_FG persistent kernel writes every row with bulk tensor stores
+    p, f = W.stationary_drop(64, 37, R=10)
+    yield "periodic_64x37_perturbed", p, W.perturbed(p, f, seed=5)
     p, f = W.rising_bubble(7.0)
     yield "density_ratio_walls_28x56_perturbed", p, W.perturbed(p, f, seed=3)
-    yield "density_ratio_periodic_28x56_perturbed", dict(p, walls=False), W.perturbed(p, f, seed=4)
+    p, f = W.rising_bubble(8.0)
+    yield "density_ratio_walls_32x64_perturbed", p, W.perturbed(p, f, seed=6)
+    yield "density_ratio_periodic_32x64_perturbed", dict(p, walls=False), W.perturbed(p, f, seed=4)
     p, f = W.convected_drop(70, 45, R=10)
     yield "prescribed_70x45", p, f
+    p, f = W.convected_drop(64, 45, R=10)
+    yield "prescribed_64x45", p, f
 
 
 def run(torch, p, f, kernel, steps):

@@ -204,7 +204,7 @@ def test_device_memory_fields_match_host_path():
     a.step(20)
     ha = a.moments()
     b = lbm.Lattice(p)
-    dev = {k: torch.from_numpy(v).cuda() for k, v in f.items()}
+    dev = {k: torch.from_numpy(np.array(v, dtype=np.float64)).cuda() for k, v in f.items()}
     lbm.lbm_init_fields(b.handle, *[dev[k] for k in lbm.FIELDS], mem=lbm.LBM_MEM_DEVICE)
     b.step(20)
     outs = [torch.zeros((40, 64), dtype=torch.float64, device="cuda") for _ in range(5)]
