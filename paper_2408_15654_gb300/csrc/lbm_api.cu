@@ -153,11 +153,13 @@ Layout layout_of(const lbm_params* p) {
 
 // Step kernel of a new handle: the one-tile kernel for FP32 storage, the warp-specialised
 // persistent kernel for the 16-bit modes.
-int default_kernel(int storage, int pipe_blocks_per_sm) {
-    // Measured on GB300 at 2048 x 1024 (us per step, one-tile / warp-specialised): FP32 74.1 / 76.5
-    // (HBM-bound either way), FP16 60.4 / 59.8, BF16 61.9 / 58.9, FP16_FG 64.1 / 60.9, BF16_FG
-    // 64.8 / 59.5: the 16-bit modes are bound by issue and latency, which the copy warp relieves.
-    if (storage != LBM_STORE_FP32 && pipe_blocks_per_sm >= 1) return LBM_KERNEL_PIPELINED;
+int default_kernel(int storage, bool var_rho, int pipe_blocks_per_sm) {
+    // Measured on GB300 (us per step, one-tile / warp-specialised), sheared drop 2048 x 1024: FP32
+    // 74.1 / 74.7 (HBM-bound either way), FP16 60.4 / 60.3, BF16 61.9 / 59.1, FP16_FG 64.1 / 58.3,
+    // BF16_FG 64.8 / 57.9; rising bubble 1024 x 2048 (density ratio 10): FP32 84.8 / 83.5, FP16
+    // 70.2 / 64.9.  The 16-bit modes, and the density-ratio step with its larger cell update, are
+    // bound by issue and latency, which the copy warp relieves.
+    if ((storage != LBM_STORE_FP32 || var_rho) && pipe_blocks_per_sm >= 1) return LBM_KERNEL_PIPELINED;
     return LBM_KERNEL_TILE;
 }
 
@@ -453,7 +455,7 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
     {
         const long long ntiles = (long long)h->tiles_x * h->tiles_y, slots = (long long)bps_pipe * sms;
         h->pipe_ctas = (int)(ntiles < slots ? ntiles : slots);
-        h->kernel = default_kernel(p->storage, bps_pipe);
+        h->kernel = default_kernel(p->storage, h->phys.var_rho != 0, bps_pipe);
     }
     cudaError_t e = cudaMemsetAsync(h->ws, 0, L.total, h->stream);
     if (e != cudaSuccess) {
@@ -661,7 +663,7 @@ int lbm_set_kernel(lbm_handle* h, int variant) {
         int bps = 0, bps_pipe = 0;
         int rc = prepare_kernels(h->prm.storage, &bps, &bps_pipe);
         if (rc) return rc;
-        h->kernel = default_kernel(h->prm.storage, bps_pipe);
+        h->kernel = default_kernel(h->prm.storage, h->phys.var_rho != 0, bps_pipe);
         return LBM_OK;
     }
     if (variant != LBM_KERNEL_TILE && variant != LBM_KERNEL_PIPELINED) return fail(LBM_EINVAL, "bad kernel variant");

@@ -89,3 +89,9 @@ def test_default_kernel_per_storage(torch):
     # the one-tile kernel for FP32 (bandwidth-bound), the warp-specialised one for 16-bit storage
     assert got == {"fp32": "tile", "fp16": "pipelined", "bf16": "pipelined", "fp16_fg": "pipelined",
                    "bf16_fg": "pipelined"}
+    # a density ratio != 1 takes the warp-specialised kernel in every storage mode
+    p, f = W.rising_bubble(8.0)
+    for st in ("fp32", "fp16", "bf16_fg"):
+        g = lbm.Lattice(dict(p, storage=st))
+        assert g.kernel == "pipelined", st
+        g.close()
