@@ -429,14 +429,18 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
     if (!rc && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, attr.device) != cudaSuccess)
         rc = fail(LBM_ECUDA, "cudaDeviceGetAttribute failed");
     const bool pair16 = lbm::pair_is_16bit(p->storage), h16 = lbm::h_is_16bit(p->storage);
-    const int es_pair = pair16 ? 4 : 8, es_h = h16 ? 2 : 4;
+    const int es_pair = pair16 ? 4 : 8;
+    // h boxes: FP32 h one plane per link; 16-bit h one plane per pair of links (4-byte elements,
+    // TY + 1 rows to cover both links' source rows)
     const unsigned hbw = h16 ? lbm::Traits<lbm::kFP16>::H_BW : lbm::Traits<lbm::kFP32>::H_BW;
+    const unsigned hbh = h16 ? lbm::TY + 1 : lbm::TY;
+    const int h_planes = h16 ? lbm::kHPlanes / 2 : lbm::kHPlanes, es_hbox = 4;
     for (int b = 0; b < 2 && !rc; ++b) {
         rc = encode_map(&h->tm_fg[b], h->pops[b], es_pair, L.pitch, p->ny + 2 * lbm::kGY, lbm::kPairs, L.pitch, L.plane, lbm::BW,
                         lbm::BH, 1);
         char* hbase = static_cast<char*>(h->pops[b]) + (size_t)lbm::kPairs * L.plane * es_pair;
         if (!rc && p->velocity == LBM_VELOCITY_SOLVED)  // no h planes with a prescribed velocity
-            rc = encode_map(&h->tm_h[b], hbase, es_h, L.pitch, p->ny + 2 * lbm::kGY, lbm::kHPlanes, L.pitch, L.plane, hbw, lbm::TY, 1);
+            rc = encode_map(&h->tm_h[b], hbase, es_hbox, L.pitch, p->ny + 2 * lbm::kGY, h_planes, L.pitch, L.plane, hbw, hbh, 1);
         // the persistent kernel's row stores of the pairs with FP32 h (tiles wholly inside the
         // grid in x, rows inside it); the extents end at the last grid column and row
         if (!rc && pair16 && !h16)

@@ -3,7 +3,8 @@
 // Data layout in HBM (one population buffer; each plane ny + 4 rows x `pitch` cells, the grid
 // inside a ghost frame, see kGX / kGY):
 //   9 pair planes  (f_i, g_i), i = 0..8      phase field (Sec. 3.1) and surfactant (Sec. 3.2)
-//   8 planes       h_1..h_8                  flow (Sec. 3.3; absent with a prescribed velocity)
+//   8 planes       h_1..h_8                  flow (Sec. 3.3; absent with a prescribed velocity);
+//                                            16-bit h: 4 planes of pairs (h_1, h_2) .. (h_7, h_8)
 // f_i and g_i stream along the same link, so they travel and collide together: one access per
 // pair, and Blackwell's packed FP32x2 arithmetic runs both collisions at once.  h_0 is never
 // stored: column 0 of M^-1 is e_0 and rows 1..8 of M do not see h_0, so h_0 feeds only itself
@@ -68,14 +69,14 @@ template <> struct Traits<kFP16> {
     using P = __half2;
     using H = __half;
     static constexpr bool kPair16 = true, kH16 = true;
-    static constexpr int H_X0 = 8, H_BW = 48;
+    static constexpr int H_X0 = 4, H_BW = 40;  // in (h_i, h_i+1) pairs
     static constexpr float SF = 1.f, SG = 256.f, SH = 4096.f;  // keep the deviations normal in FP16
 };
 template <> struct Traits<kBF16> {
     using P = __nv_bfloat162;
     using H = __nv_bfloat16;
     static constexpr bool kPair16 = true, kH16 = true;
-    static constexpr int H_X0 = 8, H_BW = 48;
+    static constexpr int H_X0 = 4, H_BW = 40;  // in (h_i, h_i+1) pairs
     static constexpr float SF = 1.f, SG = 1.f, SH = 1.f;        // BF16 has the FP32 exponent range
 };
 template <> struct Traits<kFP16FG> {
@@ -110,6 +111,20 @@ __host__ __device__ constexpr bool h_is_16bit(int st) { return st == kFP16 || st
 // tile reads is then at its plain position, and the TMA boxes need no patching.  kGX = 8 keeps
 // the x coordinate of every box a multiple of 16 bytes (boxes start 4 or 8 cells left of a tile).
 constexpr int kGX = 8, kGY = 2;
+
+// Index, in h values, of link i's slot at cell k of a buffer's h planes (plane stride `plane`
+// cells).  16-bit h is stored as pairs (h_2j+1, h_2j+2) in plane j, link 2j+1 in the low half, so
+// that a cell's eight values leave in four 32-bit stores.
+template <int ST>
+__host__ __device__ __forceinline__ long long h_index(int i, long long k, long long plane) {
+    if constexpr (Traits<ST>::kH16) return (((long long)((i - 1) >> 1) * plane + k) << 1) + ((i - 1) & 1);
+    else return (long long)(i - 1) * plane + k;
+}
+// First row of h box j relative to the tile's first row: the lower source row of its links.
+template <int ST>
+__host__ __device__ constexpr int h_row0(int j) {
+    return Traits<ST>::kH16 ? -(cy(2 * j + 1) > cy(2 * j + 2) ? cy(2 * j + 1) : cy(2 * j + 2)) : -cy(j + 1);
+}
 
 // Physical constants in FP32, precomputed on the host from lbm_params.  16-byte aligned and sized
 // so that the batched kernel can stage a lattice's copy with one bulk copy.
@@ -186,13 +201,18 @@ template <int ST> struct Smem {
     using T = Traits<ST>;
     static constexpr bool kHalo = T::kH16;  // the 16-bit h decode needs the source cell's u
     static constexpr int FG_SLOT = round128(FG_BOX * (int)sizeof(typename T::P));
-    static constexpr int H_BOX = T::H_BW * TY;
-    static constexpr int H_SLOT = round128(H_BOX * (int)sizeof(typename T::H));
+    // h boxes: one per plane (FP32 h), or one per plane of 16-bit pairs (h_2k+1, h_2k+2), which
+    // spans the rows of both links (TY + 1)
+    static constexpr int H_SLOTS = T::kH16 ? kHPlanes / 2 : kHPlanes;
+    static constexpr int H_ES = T::kH16 ? 4 : (int)sizeof(typename T::H);
+    static constexpr int H_BH = T::kH16 ? TY + 1 : TY;
+    static constexpr int H_BOX = T::H_BW * H_BH;
+    static constexpr int H_SLOT = round128(H_BOX * H_ES);
     static constexpr int HIST_W = kHalo ? BW : TX, HIST_H = kHalo ? BH : TY;
     static constexpr int HIST_BYTES = HIST_W * HIST_H * 8;
     static constexpr int FG = 0;
     static constexpr int H = FG + kPairs * FG_SLOT;
-    static constexpr int HIST = H + kHPlanes * H_SLOT;
+    static constexpr int HIST = H + H_SLOTS * H_SLOT;
     static constexpr int PP = HIST + round128(HIST_BYTES);
     static constexpr int BAR = PP + NE * 8;
     static constexpr int BYTES = BAR + 16;
@@ -222,14 +242,14 @@ template <int ST> struct Smem {
     static constexpr int BWS_PHYS = BWS_SLOT + 32;
     static constexpr int BYTES_BWS = BWS_PHYS + 2 * PHYS_BYTES;
     static constexpr unsigned TX_BYTES =
-        (unsigned)(kPairs * FG_BOX * sizeof(typename T::P) + kHPlanes * H_BOX * sizeof(typename T::H) + HIST_BYTES);
+        (unsigned)(kPairs * FG_BOX * sizeof(typename T::P) + H_SLOTS * H_BOX * H_ES + HIST_BYTES);
     static constexpr unsigned TX_BYTES_NOH = (unsigned)(kPairs * FG_BOX * sizeof(typename T::P) + HIST_BYTES);
 };
 
 
 struct StepArgs {
     CUtensorMap tm_fg;            // {nx, ny, 9} pairs, box {BW, BH, 1}
-    CUtensorMap tm_h;             // {nx, ny, 8} h values, box {H_BW, TY, 1}
+    CUtensorMap tm_h;             // {nx, ny, 8} FP32 h, box {H_BW, TY, 1}; or {nx, ny, 4} 16-bit h pairs, box {H_BW, TY + 1, 1}
     CUtensorMap tm_hist;          // {nx, ny, 1} float2, box {TX, TY, 1} or {BW, BH, 1}
     CUtensorMap tm_st_fg;         // destination pairs {kGX + nx, kGY + ny, 9}, box {TX, 1, 9} (16-bit pairs, FP32 h)
     Phys p;
@@ -503,7 +523,11 @@ __device__ __forceinline__ float load_h(const unsigned char* sm, const float2* H
                                         bool bb, float2 uown) {
     using T = Traits<ST>;
     using S = Smem<ST>;
-    const typename T::H v = reinterpret_cast<const typename T::H*>(sm + S::H + (I - 1) * S::H_SLOT)[ty * T::H_BW + tx + T::H_X0 - cx(I)];
+    constexpr int j = T::kH16 ? (I - 1) / 2 : I - 1;     // the box (plane) holding link I
+    constexpr int dr = -cy(I) - h_row0<ST>(j);           // the source row's offset inside it
+    const int e = (ty + dr) * T::H_BW + tx + T::H_X0 - cx(I);
+    const typename T::H* box = reinterpret_cast<const typename T::H*>(sm + S::H + j * S::H_SLOT);
+    const typename T::H v = T::kH16 ? box[2 * e + ((I - 1) & 1)] : box[e];
     if constexpr (!T::kH16) {
         return v;
     } else {
@@ -529,8 +553,8 @@ __device__ __forceinline__ void issue_tile_loads(unsigned char* sm, const CUtens
         tma_load_3d(sm + S::FG + i * S::FG_SLOT, tm_fg, x0 - 4 + kGX, y0 - 1 - cy(i) + kGY, i, mbar);
     if constexpr (FLOW) {
 #pragma unroll
-        for (int i = 1; i < 9; ++i)
-            tma_load_3d(sm + S::H + (i - 1) * S::H_SLOT, tm_h, x0 - T::H_X0 + kGX, y0 - cy(i) + kGY, i - 1, mbar);
+        for (int j = 0; j < S::H_SLOTS; ++j)
+            tma_load_3d(sm + S::H + j * S::H_SLOT, tm_h, x0 - T::H_X0 + kGX, y0 + h_row0<ST>(j) + kGY, j, mbar);
     }
     if constexpr (S::kHalo) tma_load_3d(sm + S::HIST, tm_hist, x0 - 4 + kGX, y0 - 1 + kGY, 0, mbar);
     else tma_load_3d(sm + S::HIST, tm_hist, x0 + kGX, y0 + kGY, 0, mbar);
@@ -776,7 +800,8 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         uint32_t key = 0;
         if constexpr (T::kPair16) key = cell_key((uint32_t)cell, io.seed);
         P outp[9];  // the stored (f_i, g_i)
-        Hv outh[8]; // the stored h_1..h_8
+        Hv outh[8]; // the stored h_1..h_8 (FP32 h)
+        uint32_t outw[4];  // 16-bit h: the stored pairs (h_1, h_2), (h_3, h_4), (h_5, h_6), (h_7, h_8)
         // ---- f (Sec. 3.1) and g (Sec. 3.2) together; sources cs2 V = d_t(s u) + cs2 (A or B) n ----
         {
             const float2 vx = fma2(make_float2(Aterm, Bterm), bc(nx_ * (1.f / 3.f)), dtX);
@@ -886,18 +911,10 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
                 const float2 r34 = fma2(Y, bc(e1), make_float2(vx, vy));
                 const float2 r56 = fma2(U, bc(e5), make_float2(-(vx + vy), vx - vy));
                 const float2 r78 = fma2(V, bc(e5), make_float2(vx + vy, vy - vx));
-                const uint32_t b12 = cvt_rs2<typename T::P>(r12.x, r12.y, rbits_of(key, 9));
-                const uint32_t b34 = cvt_rs2<typename T::P>(r34.x, r34.y, rbits_of(key, 10));
-                const uint32_t b56 = cvt_rs2<typename T::P>(r56.x, r56.y, rbits_of(key, 11));
-                const uint32_t b78 = cvt_rs2<typename T::P>(r78.x, r78.y, rbits_of(key, 12));
-                outh[0] = bits_to<Hv>(b12 & 0xFFFFu);
-                outh[1] = bits_to<Hv>(b12 >> 16);
-                outh[2] = bits_to<Hv>(b34 & 0xFFFFu);
-                outh[3] = bits_to<Hv>(b34 >> 16);
-                outh[4] = bits_to<Hv>(b56 & 0xFFFFu);
-                outh[5] = bits_to<Hv>(b56 >> 16);
-                outh[6] = bits_to<Hv>(b78 & 0xFFFFu);
-                outh[7] = bits_to<Hv>(b78 >> 16);
+                outw[0] = cvt_rs2<typename T::P>(r12.x, r12.y, rbits_of(key, 9));
+                outw[1] = cvt_rs2<typename T::P>(r34.x, r34.y, rbits_of(key, 10));
+                outw[2] = cvt_rs2<typename T::P>(r56.x, r56.y, rbits_of(key, 11));
+                outw[3] = cvt_rs2<typename T::P>(r78.x, r78.y, rbits_of(key, 12));
             }
         }
         // ---- stores: the own cell, its periodic images in the ghost frame, and at a wall the
@@ -908,7 +925,11 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         auto put = [&](long long c) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) dfg[i * pl + c] = outp[i];
-            if constexpr (FLOW) {
+            if constexpr (FLOW && T::kH16) {
+                uint32_t* dw = reinterpret_cast<uint32_t*>(dh);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dw[j * pl + c] = outw[j];
+            } else if constexpr (FLOW) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) dh[i * pl + c] = outh[i];
             }
@@ -950,7 +971,12 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
                 const int nx = p.nx;
                 auto one = [&](long long d) {
                     dfg[i * pl + d] = outp[io_];
-                    if constexpr (FLOW) dh[(i - 1) * pl + d] = outh[io_ - 1];
+                    if constexpr (FLOW && T::kH16) {
+                        const uint32_t w = outw[(io_ - 1) >> 1];
+                        dh[h_index<ST>(i, d, pl)] = bits_to<Hv>(((io_ - 1) & 1) ? (w >> 16) : (w & 0xFFFFu));
+                    } else if constexpr (FLOW) {
+                        dh[(i - 1) * pl + d] = outh[io_ - 1];
+                    }
                 };
                 one(c);
                 if (col <= 1) one(c + nx);
@@ -1151,7 +1177,7 @@ __global__ void __launch_bounds__(NT_PIPE, 3) step_kernel_pipe(const __grid_cons
 // Per-lattice descriptor, in device memory, written by the host between launches and advanced by
 // batch_advance_kernel.  Buffer `cur` holds the current state; `steps` steps were taken since
 // initialisation.
-struct alignas(64) InstDesc {
+struct alignas(128) InstDesc {
     CUtensorMap tm_fg[2], tm_h[2], tm_hist[2];
     Phys p;
     void* pops[2];
@@ -1414,7 +1440,7 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
         auto at = [&](int c, int r) {
             const long long k = p.org + (long long)r * p.pitch + c;
             fg[(long long)i * p.plane + k] = vfg;
-            if (i > 0 && a.flow) hp[(long long)(i - 1) * p.plane + k] = vh;
+            if (i > 0 && a.flow) hp[h_index<ST>(i, k, p.plane)] = vh;
         };
         auto row = [&](int c, int r) {
             at(c, r);
