@@ -943,7 +943,11 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
             P* sp = reinterpret_cast<P*>(stg) + tx;
 #pragma unroll
             for (int i = 0; i < 9; ++i) sp[i * TX] = outp[i];
-            if constexpr (FLOW) {
+            if constexpr (FLOW && T::kH16) {
+                uint32_t* dw = reinterpret_cast<uint32_t*>(dh);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dw[j * pl + cell] = outw[j];
+            } else if constexpr (FLOW) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) dh[i * pl + cell] = outh[i];
             }
