@@ -154,7 +154,8 @@ Layout layout_of(const lbm_params* p) {
 // Step kernel of a new handle: the one-tile kernel for FP32 storage, the warp-specialised
 // persistent kernel for the 16-bit modes.
 int default_kernel(int storage, bool var_rho, int pipe_blocks_per_sm) {
-    // Measured on GB300 (us per step, one-tile / warp-specialised), sheared drop 2048 x 1024: FP32
+    // Measured on GB300 (us per step, one-tile / warp-specialised, with the 16-bit h then stored
+    // per link), sheared drop 2048 x 1024: FP32
     // 74.1 / 74.7 (HBM-bound either way), FP16 60.4 / 60.3, BF16 61.9 / 59.1, FP16_FG 64.1 / 58.3,
     // BF16_FG 64.8 / 57.9; rising bubble 1024 x 2048 (density ratio 10): FP32 84.8 / 83.5, FP16
     // 70.2 / 64.9.  The 16-bit modes, and the density-ratio step with its larger cell update, are
