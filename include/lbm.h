@@ -294,8 +294,8 @@ int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* schedule, int* graph_
  *   LBM_KERNEL_PIPELINED  persistent, warp-specialised CTAs: a copy warp claims tiles from a
  *                         counter in the workspace and stages each tile's boxes and its lattice's
  *                         constants while eight compute warps work on the previous tile;
- *   LBM_KERNEL_AUTO       the default: PIPELINED for the groups of FP32 members, TILE for
- *                         16-bit groups (the faster ones on GB300 with a 64-lattice mix).
+ *   LBM_KERNEL_AUTO       the default: PIPELINED for every group (the faster one on GB300
+ *                         with a 64-lattice mix in every storage mode).
  * PIPELINED applies only if it fits (else TILE).  lbm_batch_get_kernel reports the setting. */
 int lbm_batch_set_kernel(lbm_batch* b, int variant);
 int lbm_batch_get_kernel(const lbm_batch* b, int* variant);

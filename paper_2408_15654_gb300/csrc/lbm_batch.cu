@@ -63,7 +63,7 @@ struct lbm_batch {
     // launches (each zeroes the other); the parity of the next launch; that parity after a replay
     // of the graph (which starts by zeroing both)
     int kernel;            // LBM_KERNEL_AUTO, LBM_KERNEL_TILE or LBM_KERNEL_PIPELINED
-    int ws_blocks;         // resident warp-specialised CTAs per SM over the members' storage modes
+    int ws_blocks[5];      // resident warp-specialised CTAs per SM of each members' storage mode (0: none)
     int sms;
     unsigned* d_ctr;
     int ctr_parity;
@@ -173,12 +173,12 @@ int upload_descs(lbm_batch* b) {
     return LBM_OK;
 }
 
-// Kernel of a group: the warp-specialised one if chosen, or under AUTO for FP32 storage, where it
-// hides the dependent loads that start every tile (64-lattice mix on GB300: 26.3 GLUPS against
-// 24.5 for one CTA per tile; FP16 30.3 against 30.6, so 16-bit groups keep one CTA per tile).
+// Kernel of a group: the warp-specialised one unless TILE is chosen or it does not fit.  It hides
+// the dependent loads that start every tile; 64-lattice mix on GB300, GLUPS warp-specialised /
+// one CTA per tile: FP32 26.3 / 24.5, FP16 31.8 / 31.3, BF16 33.1 / 31.4, FP16_FG 31.4 / 30.0.
 bool group_ws(const lbm_batch* b, const Group& g) {
-    if (b->ws_blocks <= 0 || b->kernel == LBM_KERNEL_TILE) return false;
-    return b->kernel == LBM_KERNEL_PIPELINED || g.st == lbm::kFP32;
+    if (b->ws_blocks[g.st] <= 0 || b->kernel == LBM_KERNEL_TILE) return false;
+    return true;
 }
 
 // Launch s of a sequence: every group once.
@@ -191,7 +191,7 @@ int launch_one(lbm_batch* b, int s) {
         a.s = s;
         a.ntiles = (int)g.count;
         a.ndescs = (int)b->members.size();
-        a.ws_ctas = ws ? (int)std::min<int64_t>(g.count, (int64_t)b->ws_blocks * b->sms) : 0;
+        a.ws_ctas = ws ? (int)std::min<int64_t>(g.count, (int64_t)b->ws_blocks[g.st] * b->sms) : 0;
         a.ctr = b->d_ctr + b->ctr_parity;
         a.ctr_next = b->d_ctr + (b->ctr_parity ^ 1);
         cudaError_t e = lbm::launch_batch(g.st, a, lbm::Variant{g.walls, g.lang, g.flow, g.var_rho}, (unsigned)g.count, b->stream);
@@ -296,7 +296,7 @@ int lbm_batch_create(int max_members, int64_t max_tiles, void* d_workspace, size
     b->d_ctr = reinterpret_cast<unsigned*>(ws + align_up((size_t)max_members * sizeof(lbm::InstDesc)) +
                                            align_up((size_t)max_tiles * sizeof(uint2)));
     b->kernel = LBM_KERNEL_AUTO;
-    b->ws_blocks = 0;
+    for (int& w : b->ws_blocks) w = 0;
     b->sms = 0;
     b->ctr_parity = 0;
     b->graph_end_parity = 0;
@@ -334,14 +334,14 @@ int lbm_batch_set_members(lbm_batch* b, lbm_handle* const* members, int n) {
     int64_t t = 0;
     lbm_batch_tiles(members, n, &t);
     if (t > b->max_tiles) return fail(LBM_EINVAL, "the members have %lld tiles > max_tiles", (long long)t);
-    int ws = 1 << 30;
+    int ws[5] = {0, 0, 0, 0, 0};
     for (int k = 0; k < n; ++k) {
-        int wk = 0;
-        cudaError_t e = lbm::prepare_batch(members[k]->prm.storage, &wk);
+        const int st = members[k]->prm.storage;
+        if (ws[st] > 0) continue;
+        cudaError_t e = lbm::prepare_batch(st, &ws[st]);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "kernel setup: %s", cudaGetErrorString(e));
-        ws = wk < ws ? wk : ws;
     }
-    b->ws_blocks = n > 0 ? ws : 0;
+    for (int st = 0; st < 5; ++st) b->ws_blocks[st] = ws[st];
     b->members.assign(members, members + n);
     return build_tiles(b);
 }
