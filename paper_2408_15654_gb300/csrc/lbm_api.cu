@@ -431,11 +431,11 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
         rc = fail(LBM_ECUDA, "cudaDeviceGetAttribute failed");
     const bool pair16 = lbm::pair_is_16bit(p->storage), h16 = lbm::h_is_16bit(p->storage);
     const int es_pair = pair16 ? 4 : 8;
-    // h boxes: FP32 h one plane per link; 16-bit h one plane per pair of links (4-byte elements,
-    // TY + 1 rows to cover both links' source rows)
+    // h boxes: one plane per pair of links (elements of two values: 4 bytes for 16-bit h, 8 for
+    // FP32 h), TY + 1 rows to cover both links' source rows
     const unsigned hbw = h16 ? lbm::Traits<lbm::kFP16>::H_BW : lbm::Traits<lbm::kFP32>::H_BW;
-    const unsigned hbh = h16 ? lbm::TY + 1 : lbm::TY;
-    const int h_planes = h16 ? lbm::kHPlanes / 2 : lbm::kHPlanes, es_hbox = 4;
+    const unsigned hbh = lbm::TY + 1;
+    const int h_planes = lbm::kHPlanes / 2, es_hbox = h16 ? 4 : 8;
     for (int b = 0; b < 2 && !rc; ++b) {
         rc = encode_map(&h->tm_fg[b], h->pops[b], es_pair, L.pitch, p->ny + 2 * lbm::kGY, lbm::kPairs, L.pitch, L.plane, lbm::BW,
                         lbm::BH, 1);

@@ -3,8 +3,7 @@
 // Data layout in HBM (one population buffer; each plane ny + 4 rows x `pitch` cells, the grid
 // inside a ghost frame, see kGX / kGY):
 //   9 pair planes  (f_i, g_i), i = 0..8      phase field (Sec. 3.1) and surfactant (Sec. 3.2)
-//   8 planes       h_1..h_8                  flow (Sec. 3.3; absent with a prescribed velocity);
-//                                            16-bit h: 4 planes of pairs (h_1, h_2) .. (h_7, h_8)
+//   4 pair planes  (h_1, h_2) .. (h_7, h_8)   flow (Sec. 3.3; absent with a prescribed velocity)
 // f_i and g_i stream along the same link, so they travel and collide together: one access per
 // pair, and Blackwell's packed FP32x2 arithmetic runs both collisions at once.  h_0 is never
 // stored: column 0 of M^-1 is e_0 and rows 1..8 of M do not see h_0, so h_0 feeds only itself
@@ -55,14 +54,15 @@ constexpr int kHPlanes = 8;     // h_1..h_8 planes
 
 enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2, kFP16FG = 3, kBF16FG = 4 };
 
-// Storage traits: element types, compile-time scales, and the x origin / width of the h boxes
-// (TMA x coordinates must be multiples of 16 bytes: 4 cells of 4 bytes, 8 cells of 2 bytes).
+// Storage traits: element types, compile-time scales, and the x origin / width of the h boxes in
+// (h_i, h_i+1) pairs (TMA x coordinates must be multiples of 16 bytes: 2 pairs of 8 bytes, 4 of
+// 4 bytes; box columns x0 - H_X0 + kGX onwards).
 template <int ST> struct Traits;
 template <> struct Traits<kFP32> {
     using P = float2;
     using H = float;
     static constexpr bool kPair16 = false, kH16 = false;
-    static constexpr int H_X0 = 4, H_BW = 40;
+    static constexpr int H_X0 = 2, H_BW = 36;  // in (h_i, h_i+1) pairs
     static constexpr float SF = 1.f, SG = 1.f, SH = 1.f;
 };
 template <> struct Traits<kFP16> {
@@ -83,14 +83,14 @@ template <> struct Traits<kFP16FG> {
     using P = __half2;
     using H = float;
     static constexpr bool kPair16 = true, kH16 = false;
-    static constexpr int H_X0 = 4, H_BW = 40;
+    static constexpr int H_X0 = 2, H_BW = 36;  // in (h_i, h_i+1) pairs
     static constexpr float SF = 1.f, SG = 256.f, SH = 1.f;
 };
 template <> struct Traits<kBF16FG> {
     using P = __nv_bfloat162;
     using H = float;
     static constexpr bool kPair16 = true, kH16 = false;
-    static constexpr int H_X0 = 4, H_BW = 40;
+    static constexpr int H_X0 = 2, H_BW = 36;  // in (h_i, h_i+1) pairs
     static constexpr float SF = 1.f, SG = 1.f, SH = 1.f;
 };
 
@@ -113,17 +113,15 @@ __host__ __device__ constexpr bool h_is_16bit(int st) { return st == kFP16 || st
 constexpr int kGX = 8, kGY = 2;
 
 // Index, in h values, of link i's slot at cell k of a buffer's h planes (plane stride `plane`
-// cells).  16-bit h is stored as pairs (h_2j+1, h_2j+2) in plane j, link 2j+1 in the low half, so
-// that a cell's eight values leave in four 32-bit stores.
-template <int ST>
+// cells).  h is stored as pairs (h_2j+1, h_2j+2) in plane j, link 2j+1 first, so that a cell's
+// eight values leave in four stores (32-bit for 16-bit h, 64-bit for FP32 h) and the flow
+// collision's FP32x2 pairs go out as they are.
 __host__ __device__ __forceinline__ long long h_index(int i, long long k, long long plane) {
-    if constexpr (Traits<ST>::kH16) return (((long long)((i - 1) >> 1) * plane + k) << 1) + ((i - 1) & 1);
-    else return (long long)(i - 1) * plane + k;
+    return (((long long)((i - 1) >> 1) * plane + k) << 1) + ((i - 1) & 1);
 }
 // First row of h box j relative to the tile's first row: the lower source row of its links.
-template <int ST>
 __host__ __device__ constexpr int h_row0(int j) {
-    return Traits<ST>::kH16 ? -(cy(2 * j + 1) > cy(2 * j + 2) ? cy(2 * j + 1) : cy(2 * j + 2)) : -cy(j + 1);
+    return -(cy(2 * j + 1) > cy(2 * j + 2) ? cy(2 * j + 1) : cy(2 * j + 2));
 }
 
 // Physical constants in FP32, precomputed on the host from lbm_params.  16-byte aligned and sized
@@ -201,11 +199,10 @@ template <int ST> struct Smem {
     using T = Traits<ST>;
     static constexpr bool kHalo = T::kH16;  // the 16-bit h decode needs the source cell's u
     static constexpr int FG_SLOT = round128(FG_BOX * (int)sizeof(typename T::P));
-    // h boxes: one per plane (FP32 h), or one per plane of 16-bit pairs (h_2k+1, h_2k+2), which
-    // spans the rows of both links (TY + 1)
-    static constexpr int H_SLOTS = T::kH16 ? kHPlanes / 2 : kHPlanes;
-    static constexpr int H_ES = T::kH16 ? 4 : (int)sizeof(typename T::H);
-    static constexpr int H_BH = T::kH16 ? TY + 1 : TY;
+    // h boxes: one per plane of pairs (h_2j+1, h_2j+2), spanning the rows of both links (TY + 1)
+    static constexpr int H_SLOTS = kHPlanes / 2;
+    static constexpr int H_ES = 2 * (int)sizeof(typename T::H);
+    static constexpr int H_BH = TY + 1;
     static constexpr int H_BOX = T::H_BW * H_BH;
     static constexpr int H_SLOT = round128(H_BOX * H_ES);
     static constexpr int HIST_W = kHalo ? BW : TX, HIST_H = kHalo ? BH : TY;
@@ -249,7 +246,7 @@ template <int ST> struct Smem {
 
 struct StepArgs {
     CUtensorMap tm_fg;            // {nx, ny, 9} pairs, box {BW, BH, 1}
-    CUtensorMap tm_h;             // {nx, ny, 8} FP32 h, box {H_BW, TY, 1}; or {nx, ny, 4} 16-bit h pairs, box {H_BW, TY + 1, 1}
+    CUtensorMap tm_h;             // {nx, ny, 4} h pairs, box {H_BW, TY + 1, 1}
     CUtensorMap tm_hist;          // {nx, ny, 1} float2, box {TX, TY, 1} or {BW, BH, 1}
     CUtensorMap tm_st_fg;         // destination pairs {kGX + nx, kGY + ny, 9}, box {TX, 1, 9} (16-bit pairs, FP32 h)
     Phys p;
@@ -523,11 +520,11 @@ __device__ __forceinline__ float load_h(const unsigned char* sm, const float2* H
                                         bool bb, float2 uown) {
     using T = Traits<ST>;
     using S = Smem<ST>;
-    constexpr int j = T::kH16 ? (I - 1) / 2 : I - 1;     // the box (plane) holding link I
-    constexpr int dr = -cy(I) - h_row0<ST>(j);           // the source row's offset inside it
+    constexpr int j = (I - 1) / 2;                  // the box (pair plane) holding link I
+    constexpr int dr = -cy(I) - h_row0(j);          // the source row's offset inside it
     const int e = (ty + dr) * T::H_BW + tx + T::H_X0 - cx(I);
     const typename T::H* box = reinterpret_cast<const typename T::H*>(sm + S::H + j * S::H_SLOT);
-    const typename T::H v = T::kH16 ? box[2 * e + ((I - 1) & 1)] : box[e];
+    const typename T::H v = box[2 * e + ((I - 1) & 1)];
     if constexpr (!T::kH16) {
         return v;
     } else {
@@ -554,7 +551,7 @@ __device__ __forceinline__ void issue_tile_loads(unsigned char* sm, const CUtens
     if constexpr (FLOW) {
 #pragma unroll
         for (int j = 0; j < S::H_SLOTS; ++j)
-            tma_load_3d(sm + S::H + j * S::H_SLOT, tm_h, x0 - T::H_X0 + kGX, y0 + h_row0<ST>(j) + kGY, j, mbar);
+            tma_load_3d(sm + S::H + j * S::H_SLOT, tm_h, x0 - T::H_X0 + kGX, y0 + h_row0(j) + kGY, j, mbar);
     }
     if constexpr (S::kHalo) tma_load_3d(sm + S::HIST, tm_hist, x0 - 4 + kGX, y0 - 1 + kGY, 0, mbar);
     else tma_load_3d(sm + S::HIST, tm_hist, x0 + kGX, y0 + kGY, 0, mbar);
@@ -800,7 +797,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         uint32_t key = 0;
         if constexpr (T::kPair16) key = cell_key((uint32_t)cell, io.seed);
         P outp[9];  // the stored (f_i, g_i)
-        Hv outh[8]; // the stored h_1..h_8 (FP32 h)
+        float2 outhp[4];   // FP32 h: the stored pairs (h_1, h_2), (h_3, h_4), (h_5, h_6), (h_7, h_8)
         uint32_t outw[4];  // 16-bit h: the stored pairs (h_1, h_2), (h_3, h_4), (h_5, h_6), (h_7, h_8)
         // ---- f (Sec. 3.1) and g (Sec. 3.2) together; sources cs2 V = d_t(s u) + cs2 (A or B) n ----
         {
@@ -900,8 +897,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
                 }
             }
             if constexpr (!T::kH16) {
-                outh[0] = X.x, outh[1] = X.y, outh[2] = Y.x, outh[3] = Y.y;
-                outh[4] = U.x, outh[5] = U.y, outh[6] = V.x, outh[7] = V.y;
+                outhp[0] = X, outhp[1] = Y, outhp[2] = U, outhp[3] = V;
             } else {
                 // every slot is stored relative to this cell's new u (what the next step reads back):
                 // raw = (h_i / w_i - 3 rho c_i.u) S_h, two links per stochastic conversion
@@ -930,8 +926,9 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
 #pragma unroll
                 for (int j = 0; j < 4; ++j) dw[j * pl + c] = outw[j];
             } else if constexpr (FLOW) {
+                float2* dp = reinterpret_cast<float2*>(dh);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) dh[i * pl + c] = outh[i];
+                for (int j = 0; j < 4; ++j) dp[j * pl + c] = outhp[j];
             }
         };
         const bool xl = x <= 1, xr = x >= p.nx - 2;
@@ -948,8 +945,9 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
 #pragma unroll
                 for (int j = 0; j < 4; ++j) dw[j * pl + cell] = outw[j];
             } else if constexpr (FLOW) {
+                float2* dp = reinterpret_cast<float2*>(dh);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) dh[i * pl + cell] = outh[i];
+                for (int j = 0; j < 4; ++j) dp[j * pl + cell] = outhp[j];
             }
         } else {
             put((long long)cell);
@@ -977,9 +975,10 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
                     dfg[i * pl + d] = outp[io_];
                     if constexpr (FLOW && T::kH16) {
                         const uint32_t w = outw[(io_ - 1) >> 1];
-                        dh[h_index<ST>(i, d, pl)] = bits_to<Hv>(((io_ - 1) & 1) ? (w >> 16) : (w & 0xFFFFu));
+                        dh[h_index(i, d, pl)] = bits_to<Hv>(((io_ - 1) & 1) ? (w >> 16) : (w & 0xFFFFu));
                     } else if constexpr (FLOW) {
-                        dh[(i - 1) * pl + d] = outh[io_ - 1];
+                        const float2 w = outhp[(io_ - 1) >> 1];
+                        dh[h_index(i, d, pl)] = ((io_ - 1) & 1) ? w.y : w.x;
                     }
                 };
                 one(c);
@@ -1444,7 +1443,7 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
         auto at = [&](int c, int r) {
             const long long k = p.org + (long long)r * p.pitch + c;
             fg[(long long)i * p.plane + k] = vfg;
-            if (i > 0 && a.flow) hp[h_index<ST>(i, k, p.plane)] = vh;
+            if (i > 0 && a.flow) hp[h_index(i, k, p.plane)] = vh;
         };
         auto row = [&](int c, int r) {
             at(c, r);
