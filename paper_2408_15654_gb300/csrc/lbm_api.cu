@@ -600,7 +600,9 @@ struct StateHeader {
     int32_t nx, ny, pitch, first;
     int64_t steps;
 };
-static const uint64_t kStateMagic = 0x4c424d3253544154ull;  // "LBM2STAT"
+// Names the population layout of the blob ("LBM3STAT": h stored in link pairs); blobs written with
+// another layout are refused by lbm_set_state.
+static const uint64_t kStateMagic = 0x4c424d3353544154ull;  // "LBM3STAT"
 
 int lbm_state_bytes(const lbm_handle* h, size_t* bytes) {
     g_err.clear();
