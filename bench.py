@@ -492,7 +492,7 @@ def run_ours(args):
     traffic = profiled_traffic()
 
     # end to end through the C ABI with pinned host buffers: upload the fields, K steps, read back
-    host_in = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for k, v in f.items()}
+    host_in = {k: torch.from_numpy(np.array(v, dtype=np.float64)).pin_memory().numpy() for k, v in f.items()}
     host_out = [torch.empty((NY, NX), dtype=torch.float64).pin_memory().numpy() for _ in range(5)]
     torch.cuda.synchronize()
     barrier(world)
