@@ -1060,6 +1060,8 @@ __device__ __forceinline__ void tile_origin(int k, int ntx, int nty, int& x0, in
 // warp never joins a block-wide barrier.  After the last tile the copy lane arrives on a full
 // barrier without a copy; the compute warps read the stop mark (x0 = -1) and stop.  Every
 // wait is bounded: a copy lane that gives up waits (bounded) for the copies it has in flight.
+// Three CTAs per SM with 16-bit storage; two with FP32, whose two stages fill the shared memory of
+// two, so its bound lets the compiler use up to 112 registers (rising bubble, FP32: 81.6 -> 80.6 us).
 constexpr int NT_PIPE = NT + 32;
 
 // Writes the staged own pairs of tile row y0 + warp (see Smem::kTS).  A tile that lies wholly
@@ -1090,7 +1092,7 @@ __device__ __forceinline__ void store_staged_row(const StepArgs& a, const unsign
 }
 
 template <int ST, bool WALLS, bool LANGMUIR, int FLOW>
-__global__ void __launch_bounds__(NT_PIPE, 3) step_kernel_pipe(const __grid_constant__ StepArgs a, int ntx, int nty) {
+__global__ void __launch_bounds__(NT_PIPE, ST == kFP32 ? 2 : 3) step_kernel_pipe(const __grid_constant__ StepArgs a, int ntx, int nty) {
     using S = Smem<ST>;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned long long* full = reinterpret_cast<unsigned long long*>(sm + S::PIPE_BAR);
@@ -1251,9 +1253,12 @@ __global__ void __launch_bounds__(NT, 4) batch_step_kernel(const __grid_constant
 // lattice's current buffer, stages the lattice's constants (one bulk copy) and the tile's boxes
 // (TMA) into a buffer on its full barrier.  It works one tile ahead: the claim, list entry and
 // descriptor read of the next tile are in flight while it waits for a buffer, so these dependent
-// loads overlap the arithmetic instead of delaying every tile.
+// loads overlap the arithmetic instead of delaying every tile.  Two CTAs per SM (the FP32 buffers
+// fill the shared memory of two anyway): at that bound the compiler keeps the cell update in
+// registers, where at three it spilled 28-96 B (64-lattice mix: FP32 27.2 -> 28.7 GLUPS, FP16
+// 31.7 -> 34.7, FP16_FG 32.2 -> 34.9).
 template <int ST, bool WALLS, bool LANGMUIR, int FLOW>
-__global__ void __launch_bounds__(NT_PIPE, 3) batch_step_kernel_ws(const __grid_constant__ BatchArgs b) {
+__global__ void __launch_bounds__(NT_PIPE, 2) batch_step_kernel_ws(const __grid_constant__ BatchArgs b) {
     using S = Smem<ST>;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned long long* full = reinterpret_cast<unsigned long long*>(sm + S::PIPE_BAR);
