@@ -111,8 +111,9 @@ typedef struct lbm_handle lbm_handle;
  * rounded up to a multiple of 256, with pitch = nx + 10 rounded up to a multiple of 32 and
  * B = 104 (FP32 storage), 52 (FP16, BF16) or 68 (FP16_FG, BF16_FG); with
  * LBM_VELOCITY_PRESCRIBED, 72 (FP32) or 36 (16-bit).  A buffer holds 9 planes of (f_i, g_i)
- * pairs followed by 8 planes h_1..h_8 (h_0 never influences the step; no h planes with a
- * prescribed velocity), each plane ny + 4 rows of pitch cells: cell (x, y) is at row y + 2,
+ * pairs followed by 4 planes of (h_1, h_2), (h_3, h_4), (h_5, h_6), (h_7, h_8) pairs (h_0 never
+ * influences the step; no h planes with a prescribed velocity), each plane ny + 4 rows of pitch
+ * cells: cell (x, y) is at row y + 2,
  * column x + 8, inside a ghost frame of copies (periodic images; bounce-back values in the rows
  * next to walls) that the library maintains.  After lbm_init_fields and k steps the current
  * state is buffer k mod 2 (buffer 0 at offset 0).
