@@ -220,14 +220,15 @@ int lbm_steps_taken(const lbm_handle* h, int64_t* steps);
 int lbm_destroy(lbm_handle* h);
 
 /* Step kernel of a handle.  Both variants compute the same step bit for bit; they differ in how
- * the work is laid out on the GPU:
- *   LBM_KERNEL_TILE       one CTA per 32 x 8 tile, launched as a grid of all tiles;
+ * the work is laid out on the GPU (FP32 storage: one cell per thread, tiles of 32 x 8 cells;
+ * 16-bit storage: two horizontally adjacent cells per thread, tiles of 32 x 8 cells):
+ *   LBM_KERNEL_TILE       one CTA per tile, launched as a grid of all tiles;
  *   LBM_KERNEL_PIPELINED  persistent, warp-specialised CTAs (as many as fit on all SMs, at most
  *                         one per tile): a copy warp claims tiles and stages each with TMA into
- *                         one of two buffers while eight compute warps work on the other;
- *   LBM_KERNEL_AUTO       (lbm_set_kernel only) the library's choice: TILE for FP32 storage at
- *                         uniform density, PIPELINED for the 16-bit modes and for a density
- *                         ratio != 1 (the faster ones on GB300 at 2048 x 1024 cells).
+ *                         one of two buffers while the compute warps work on the other;
+ *   LBM_KERNEL_AUTO       (lbm_set_kernel only) the library's choice: TILE at uniform density,
+ *                         PIPELINED for a density ratio != 1 (the faster ones on GB300 at
+ *                         2048 x 1024 cells).
  * A new handle uses the library's choice.  LBM_EINVAL if the pipelined kernel does not fit. */
 #define LBM_KERNEL_AUTO 0
 #define LBM_KERNEL_TILE 1
@@ -294,7 +295,7 @@ int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* schedule, int* graph_
  *   LBM_KERNEL_TILE       one CTA per tile of the tile list;
  *   LBM_KERNEL_PIPELINED  persistent, warp-specialised CTAs: a copy warp claims tiles from a
  *                         counter in the workspace and stages each tile's boxes and its lattice's
- *                         constants while eight compute warps work on the previous tile;
+ *                         constants while the compute warps work on the previous tile;
  *   LBM_KERNEL_AUTO       the default: PIPELINED for every group (the faster one on GB300
  *                         with a 64-lattice mix in every storage mode).
  * PIPELINED applies only if it fits (else TILE).  lbm_batch_get_kernel reports the setting. */

@@ -151,16 +151,17 @@ Layout layout_of(const lbm_params* p) {
     return L;
 }
 
-// Step kernel of a new handle: the one-tile kernel for FP32 storage, the warp-specialised
-// persistent kernel for the 16-bit modes.
+// Step kernel of a new handle: the warp-specialised persistent kernel with a density ratio != 1,
+// else the one-tile kernel.
 int default_kernel(int storage, bool var_rho, int pipe_blocks_per_sm) {
-    // Measured on GB300 (us per step, one-tile / warp-specialised, with the 16-bit h then stored
-    // per link), sheared drop 2048 x 1024: FP32
-    // 74.1 / 74.7 (HBM-bound either way), FP16 60.4 / 60.3, BF16 61.9 / 59.1, FP16_FG 64.1 / 58.3,
-    // BF16_FG 64.8 / 57.9; rising bubble 1024 x 2048 (density ratio 10): FP32 84.8 / 83.5, FP16
-    // 70.2 / 64.9.  The 16-bit modes, and the density-ratio step with its larger cell update, are
-    // bound by issue and latency, which the copy warp relieves.
-    if ((storage != LBM_STORE_FP32 || var_rho) && pipe_blocks_per_sm >= 1) return LBM_KERNEL_PIPELINED;
+    // Measured on GB300 (us per step, one-tile / warp-specialised), sheared drop 2048 x 1024: FP32
+    // 72.8 / 73.6 (HBM-bound either way); two cells per thread in 32 x 8 tiles: FP16 53.5 / 64.2,
+    // BF16 54.2 / 64.7, FP16_FG 54.9 / 57.7, BF16_FG 55.4 / 58.6 (six 128-thread CTAs per SM hide
+    // the copy latency that the copy warp hid for the one-cell kernels); rising bubble 1024 x 2048
+    // (density ratio 10): FP32 83.9 / 80.1, FP16 64.9 / 64.6, whose larger cell update leaves room
+    // for fewer CTAs per SM, so the copy warp pays.
+    (void)storage;
+    if (var_rho && pipe_blocks_per_sm >= 1) return LBM_KERNEL_PIPELINED;
     return LBM_KERNEL_TILE;
 }
 
@@ -243,7 +244,6 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
     a.tm_fg = h->tm_fg[h->cur];
     a.tm_h = h->tm_h[h->cur];
     a.tm_hist = h->tm_hist[h->cur];
-    a.tm_st_fg = h->tm_st_fg[h->cur ^ 1];
     a.p = h->phys;
     a.io.first = h->first;
     a.io.src = h->pops[h->cur];
@@ -430,33 +430,31 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
     if (!rc && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, attr.device) != cudaSuccess)
         rc = fail(LBM_ECUDA, "cudaDeviceGetAttribute failed");
     const bool pair16 = lbm::pair_is_16bit(p->storage), h16 = lbm::h_is_16bit(p->storage);
+    const lbm::TileDims td = lbm::tile_dims(p->storage);
     const int es_pair = pair16 ? 4 : 8;
     // h boxes: one plane per pair of links (elements of two values: 4 bytes for 16-bit h, 8 for
     // FP32 h), TY + 1 rows to cover both links' source rows
-    const unsigned hbw = h16 ? lbm::Traits<lbm::kFP16>::H_BW : lbm::Traits<lbm::kFP32>::H_BW;
-    const unsigned hbh = lbm::TY + 1;
+    const unsigned hbw = (unsigned)td.hbw;
+    const unsigned hbh = (unsigned)td.ty + 1;
     const int h_planes = lbm::kHPlanes / 2, es_hbox = h16 ? 4 : 8;
     for (int b = 0; b < 2 && !rc; ++b) {
-        rc = encode_map(&h->tm_fg[b], h->pops[b], es_pair, L.pitch, p->ny + 2 * lbm::kGY, lbm::kPairs, L.pitch, L.plane, lbm::BW,
-                        lbm::BH, 1);
+        rc = encode_map(&h->tm_fg[b], h->pops[b], es_pair, L.pitch, p->ny + 2 * lbm::kGY, lbm::kPairs, L.pitch, L.plane,
+                        (unsigned)td.bw, (unsigned)td.bh, 1);
         char* hbase = static_cast<char*>(h->pops[b]) + (size_t)lbm::kPairs * L.plane * es_pair;
         if (!rc && p->velocity == LBM_VELOCITY_SOLVED)  // no h planes with a prescribed velocity
             rc = encode_map(&h->tm_h[b], hbase, es_hbox, L.pitch, p->ny + 2 * lbm::kGY, h_planes, L.pitch, L.plane, hbw, hbh, 1);
-        // the persistent kernel's row stores of the pairs with FP32 h (tiles wholly inside the
-        // grid in x, rows inside it); the extents end at the last grid column and row
-        if (!rc && pair16 && !h16)
-            rc = encode_map(&h->tm_st_fg[b], h->pops[b], es_pair, lbm::kGX + p->nx, lbm::kGY + p->ny, lbm::kPairs, L.pitch,
-                            L.plane, lbm::TX, 1, lbm::kPairs);
     }
     for (int b = 0; b < 2 && !rc; ++b)
-        rc = h16 ? encode_map(&h->tm_hist[b], h->hist[b], 8, L.pitch, p->ny + 2 * lbm::kGY, 1, L.pitch, L.plane, lbm::BW, lbm::BH, 1)
-                  : encode_map(&h->tm_hist[b], h->hist[b], 8, L.pitch, p->ny + 2 * lbm::kGY, 1, L.pitch, L.plane, lbm::TX, lbm::TY, 1);
+        rc = h16 ? encode_map(&h->tm_hist[b], h->hist[b], 8, L.pitch, p->ny + 2 * lbm::kGY, 1, L.pitch, L.plane,
+                              (unsigned)td.bw, (unsigned)td.bh, 1)
+                 : encode_map(&h->tm_hist[b], h->hist[b], 8, L.pitch, p->ny + 2 * lbm::kGY, 1, L.pitch, L.plane,
+                              (unsigned)td.tx, (unsigned)td.ty, 1);
     if (rc) {
         delete h;
         return rc;
     }
-    h->tiles_x = (p->nx + lbm::TX - 1) / lbm::TX;
-    h->tiles_y = (p->ny + lbm::TY - 1) / lbm::TY;
+    h->tiles_x = (p->nx + td.tx - 1) / td.tx;
+    h->tiles_y = (p->ny + td.ty - 1) / td.ty;
     {
         const long long ntiles = (long long)h->tiles_x * h->tiles_y, slots = (long long)bps_pipe * sms;
         h->pipe_ctas = (int)(ntiles < slots ? ntiles : slots);

@@ -47,8 +47,7 @@ struct lbm_handle {
     CUtensorMap tm_fg[2];    // TMA descriptors of the (f, g) pair planes of each buffer
     CUtensorMap tm_h[2];     // TMA descriptors of the h planes of each buffer
     CUtensorMap tm_hist[2];  // TMA descriptors of the u history buffers
-    CUtensorMap tm_st_fg[2]; // bulk-store descriptors of the own cells' pairs (16-bit pairs, FP32 h)
-    int tiles_x, tiles_y;    // step-kernel grid: one TX x TY tile per CTA
+    int tiles_x, tiles_y;    // step-kernel grid: one tile per CTA (lbm::tile_dims of the storage mode)
     int kernel;              // LBM_KERNEL_TILE or LBM_KERNEL_PIPELINED
     int pipe_ctas;           // CTAs of the pipelined kernel (0: it does not fit)
     int cur;          // buffer holding the current state

@@ -10,6 +10,17 @@
 
 namespace lbm {
 
+// Tile geometry of storage mode st, for the host: tile width and height in cells, the pair box
+// (BW x BH) that TMA stages per plane, and the width of the h boxes in (h_i, h_i+1) pairs.
+struct TileDims {
+    int tx, ty, bw, bh, hbw;
+};
+inline TileDims tile_dims(int st) {
+    const int hx0 = h_is_16bit(st) ? Traits<kFP16>::H_X0 : Traits<kFP32>::H_X0;
+    if (cpt_of(st) == 1) return TileDims{Geo<1>::TX, Geo<1>::TY, Geo<1>::BW, Geo<1>::BH, Geo<1>::TX + 2 * hx0};
+    return TileDims{Geo<2>::TX, Geo<2>::TY, Geo<2>::BW, Geo<2>::BH, Geo<2>::TX + 2 * hx0};
+}
+
 // Runtime flags of a launch, mapped to the kernel variant.
 struct Variant {
     bool walls, langmuir, flow, var_rho;
@@ -43,7 +54,7 @@ inline Variant variant_of(int k) {
 constexpr int kVariants = 10;
 
 inline cudaLaunchConfig_t pdl_config(dim3 grid, size_t smem, cudaStream_t stream, cudaLaunchAttribute* attr,
-                                     unsigned threads = NT) {
+                                     unsigned threads) {
     // Every launch uses programmatic dependent launch: the kernel waits (griddepcontrol.wait) for
     // the previous grid before touching memory, so the next launch may be scheduled during the
     // tail of this one.
@@ -61,19 +72,19 @@ inline cudaLaunchConfig_t pdl_config(dim3 grid, size_t smem, cudaStream_t stream
 }
 
 // grid = (tiles along x, tiles along y).  A step (mode kStep) with pipe_ctas > 0 runs the
-// persistent warp-specialised kernel on pipe_ctas CTAs of NT_PIPE threads instead of one CTA per tile.
+// persistent warp-specialised kernel on pipe_ctas CTAs of nt_pipe<ST>() threads instead of one CTA per tile.
 template <int ST>
 cudaError_t launch_step_impl(const StepArgs& a, int mode, const Variant& v, dim3 grid, int pipe_ctas,
                              cudaStream_t stream) {
     cudaLaunchAttribute attr[1];
     if (mode == kStep && pipe_ctas > 0) {
         const int ntx = (int)grid.x, nty = (int)grid.y;
-        cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)pipe_ctas), Smem<ST>::BYTES_PIPE, stream, attr, NT_PIPE);
+        cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)pipe_ctas), Smem<ST>::BYTES_PIPE, stream, attr, nt_pipe<ST>());
         return dispatch_variant(v, [&]<bool W, bool L, int F>() {
-            return cudaLaunchKernelEx(&cfg, step_kernel_pipe<ST, W, L, F>, a, ntx, nty);
+            return cudaLaunchKernelEx(&cfg, pipe_kernel<ST, W, L, F>(), a, ntx, nty);
         });
     }
-    cudaLaunchConfig_t cfg = pdl_config(grid, Smem<ST>::BYTES, stream, attr);
+    cudaLaunchConfig_t cfg = pdl_config(grid, Smem<ST>::BYTES, stream, attr, GeoOf<ST>::NT);
     return dispatch_variant(v, [&]<bool W, bool L, int F>() {
         if (mode == kStep) return cudaLaunchKernelEx(&cfg, step_kernel<ST, W, L, kStep, F>, a);
         return cudaLaunchKernelEx(&cfg, step_kernel<ST, W, L, kMoments, F>, a);
@@ -89,16 +100,16 @@ cudaError_t prepare_step_impl(int* blocks_per_sm, int* pipe_blocks_per_sm) {
         int b = 0;
         auto k0 = step_kernel<ST, W, L, kStep, F>;
         auto k1 = step_kernel<ST, W, L, kMoments, F>;
-        auto kp = step_kernel_pipe<ST, W, L, F>;
+        auto kp = pipe_kernel<ST, W, L, F>();
         cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES_PIPE);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k0, NT, Smem<ST>::BYTES);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k0, GeoOf<ST>::NT, Smem<ST>::BYTES);
         tile = b < tile ? b : tile;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1, NT, Smem<ST>::BYTES);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1, GeoOf<ST>::NT, Smem<ST>::BYTES);
         tile = b < tile ? b : tile;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kp, NT_PIPE, Smem<ST>::BYTES_PIPE);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kp, nt_pipe<ST>(), Smem<ST>::BYTES_PIPE);
         pipe = b < pipe ? b : pipe;
         return e;
     };
@@ -115,12 +126,12 @@ template <int ST>
 cudaError_t launch_batch_impl(const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t stream) {
     cudaLaunchAttribute attr[1];
     if (b.ws_ctas > 0) {
-        cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)b.ws_ctas), Smem<ST>::BYTES_BWS, stream, attr, NT_PIPE);
+        cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)b.ws_ctas), Smem<ST>::BYTES_BWS, stream, attr, nt_pipe<ST>());
         return dispatch_variant(v, [&]<bool W, bool L, int F>() {
-            return cudaLaunchKernelEx(&cfg, batch_step_kernel_ws<ST, W, L, F>, b);
+            return cudaLaunchKernelEx(&cfg, batch_ws_kernel<ST, W, L, F>(), b);
         });
     }
-    cudaLaunchConfig_t cfg = pdl_config(dim3(ntiles), Smem<ST>::BYTES_BATCH, stream, attr);
+    cudaLaunchConfig_t cfg = pdl_config(dim3(ntiles), Smem<ST>::BYTES_BATCH, stream, attr, GeoOf<ST>::NT);
     return dispatch_variant(v, [&]<bool W, bool L, int F>() {
         return cudaLaunchKernelEx(&cfg, batch_step_kernel<ST, W, L, F>, b);
     });
@@ -136,11 +147,11 @@ cudaError_t prepare_batch_impl(int* ws_blocks_per_sm) {
         e = dispatch_variant(variant_of(k), [&]<bool W, bool L, int F>() {
             cudaError_t r = cudaFuncSetAttribute(batch_step_kernel<ST, W, L, F>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES_BATCH);
-            auto kw = batch_step_kernel_ws<ST, W, L, F>;
+            auto kw = batch_ws_kernel<ST, W, L, F>();
             if (r == cudaSuccess)
                 r = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<ST>::BYTES_BWS);
             int bl = 0;
-            if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, kw, NT_PIPE, Smem<ST>::BYTES_BWS);
+            if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, kw, nt_pipe<ST>(), Smem<ST>::BYTES_BWS);
             ws = bl < ws ? bl : ws;
             return r;
         });

@@ -294,7 +294,8 @@ int lbm_server_submit(lbm_server* s, const lbm_params* p, const double* phi, con
     j.steps = steps;
     j.cells = (int64_t)p->nx * p->ny;
     j.bytes = bytes;
-    const int64_t tiles = (int64_t)((p->nx + lbm::TX - 1) / lbm::TX) * ((p->ny + lbm::TY - 1) / lbm::TY);
+    const lbm::TileDims td = lbm::tile_dims(p->storage);
+    const int64_t tiles = (int64_t)((p->nx + td.tx - 1) / td.tx) * ((p->ny + td.ty - 1) / td.ty);
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->fatal) return fail(s->fatal, "server failed: %s", s->fatal_msg.c_str());
     if (s->stop) return fail(LBM_ESTATE, "server is stopping");

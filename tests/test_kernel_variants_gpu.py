@@ -1,7 +1,8 @@
-"""The two step kernels (one CTA per tile; persistent CTAs with a double-buffered TMA pipeline,
-whose 16-bit variants write the own cells with bulk tensor stores) compute the same step bit for
-bit, in every storage mode and flow variant, on ragged and full-size grids; the comparison covers
-the whole state, ghost frame included."""
+"""The two step kernels (one CTA per tile; persistent CTAs with a double-buffered TMA pipeline)
+compute the same step bit for bit, in every storage mode and flow variant, on ragged and full-size
+grids; the comparison covers the whole state, ghost frame included.  The 16-bit modes update two
+horizontally adjacent cells per thread, so odd widths (a thread whose second cell lies beyond the
+grid) are among the cases, with walls and with periodic images in y."""
 import pytest
 
 from paper_2408_15654_gb300 import lbm
@@ -28,10 +29,12 @@ def cases():
     yield "walls_45x19_perturbed", p, W.perturbed(p, f, seed=2)
     p, f = W.shear_drop(20, 6, R=2.5)
     yield "below_one_tile", p, f
-    # widths that are multiples of the tile width: every tile column is whole, so the FP16_FG and
-    # BF16_FG persistent kernel writes every row with bulk tensor stores
+    # a width that is a multiple of the tile width: every tile column is whole
     p, f = W.stationary_drop(64, 37, R=10)
     yield "periodic_64x37_perturbed", p, W.perturbed(p, f, seed=5)
+    # odd width, periodic in y: the last thread of a row has one cell, and its images wrap in y
+    p, f = W.stationary_drop(45, 21, R=7)
+    yield "periodic_45x21_perturbed", p, W.perturbed(p, f, seed=7)
     p, f = W.rising_bubble(7.0)
     yield "density_ratio_walls_28x56_perturbed", p, W.perturbed(p, f, seed=3)
     p, f = W.rising_bubble(8.0)
@@ -86,9 +89,9 @@ def test_default_kernel_per_storage(torch):
         g.kernel = "auto"
         assert g.kernel == got[st]
         g.close()
-    # the one-tile kernel for FP32 (bandwidth-bound), the warp-specialised one for 16-bit storage
-    assert got == {"fp32": "tile", "fp16": "pipelined", "bf16": "pipelined", "fp16_fg": "pipelined",
-                   "bf16_fg": "pipelined"}
+    # at uniform density the one-tile kernel in every storage mode: FP32 is bandwidth-bound either
+    # way, and the 16-bit modes' two-cell tiles run six CTAs per SM
+    assert got == {"fp32": "tile", "fp16": "tile", "bf16": "tile", "fp16_fg": "tile", "bf16_fg": "tile"}
     # a density ratio != 1 takes the warp-specialised kernel in every storage mode
     p, f = W.rising_bubble(8.0)
     for st in ("fp32", "fp16", "bf16_fg"):
