@@ -8,11 +8,17 @@ one lbm_step(1): one launch of the fused collide-stream kernel over the whole gr
 MLUPS (million lattice updates per second; one update advances f, g and h of one cell).  The
 populations (436 MB) exceed the 129 MB L2, so no flush is needed between steps.
 
+Timing: after W untimed steps, windows of exactly K steps are timed with CUDA events on the
+lattice's stream, back to back, until at least one second of steps has been timed; the value is
+the median window.  nvidia-smi samples the SM clock and throttle reasons over all timed legs.
+
 Printed (one JSON line on rank 0): the device-timed throughput, the end-to-end throughput through
 the C ABI with host buffers, the roofline of the step kernel against the measured HBM bandwidth,
-the FP64 CPU oracle on the host cores as a baseline, and the SM clocks sampled during the run.
-With --gpus N > 1 (under torchrun) every rank runs its own replica; the value is the sum of the
-lattice updates of all ranks over the slowest rank's time.
+the FP64 CPU oracle on the host cores as a baseline (every configuration, all cores and one), the
+other legs (square grid, 16-bit storage, prescribed velocity, density ratio, many lattices,
+serving) and the storage errors against the oracle.  With --gpus N > 1 (under torchrun) every rank
+runs its own replica; the value is the sum of the lattice updates of all ranks over the slowest
+rank's time.
 """
 from __future__ import annotations
 
@@ -31,6 +37,9 @@ sys.path.insert(0, ROOT)
 
 NX, NY = 2048, 1024
 BYTES_PER_LUP = 26 * 4 * 2 + 2 * 4 * 2  # 26 live float populations and 2 history floats, read + written
+# the survey's count, which also stores phi and psi of the previous level (this design recovers
+# them from the cell's own post-collision pairs, which it reads anyway)
+BYTES_PER_LUP_SURVEY = 26 * 4 * 2 + 4 * 4 * 2
 BYTES_PER_LUP_16 = 26 * 2 * 2 + 2 * 4 * 2  # the same populations stored in 16 bits
 BYTES_PER_LUP_FG = 18 * 2 * 2 + 8 * 4 * 2 + 2 * 4 * 2  # f, g in 16 bits, h in FP32
 BYTES_PER_LUP_PRESCRIBED = {"fp32": 9 * 8 * 2 + 2 * 4 * 2, "fp16": 9 * 4 * 2 + 2 * 4 * 2}  # f, g and u only
@@ -42,6 +51,8 @@ METRIC = "MLUPS (3 lattices) and % HBM roofline, FP32 vs half-store; serving p50
 WORKLOAD = "sheared drop 2048x1024 (R=160, Re=1, Ca=0.2, Langmuir E0=0.2, psi0=0.3), FP32 storage"
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_2048x1024_fp32.json")
 KERNEL_SRC = os.path.join(ROOT, "paper_2408_15654_gb300", "csrc", "lbm_kernels.cuh")
+MIN_TIMED_S = 1.0        # each device-timed leg times K-step windows until this much has passed
+SERVING_MARGIN = 8 << 30  # device memory left free beside the serving arena
 
 
 def kernel_hash() -> str:
@@ -75,8 +86,16 @@ def profiled_traffic():
     return prof.get("dram_bytes_per_launch")
 
 
+def sig(x, n=4):
+    """x rounded to n significant digits (keeps the JSON line short)."""
+    if x is None or isinstance(x, (bool, int)):
+        return x
+    return float(f"{x:.{n}g}")
+
+
 class ClockSampler:
-    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    """nvidia-smi clock / throttle-reason samples while the timed legs run, plus one query when it
+    starts and one when it stops, so that the record exists however short the legs are."""
 
     QUERY = ("index,utilization.gpu,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -84,9 +103,11 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int):
         self.proc = None
+        self.gpu = gpu_index
         # the samples go to LBM_RECORD_DIR if it is set, else to a temporary file
         rec = os.environ.get("LBM_RECORD_DIR") or tempfile.gettempdir()
         self.path = os.path.join(rec, f"clocks_bench_{os.getpid()}.csv")
+        self.edges = [self.query()]
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
@@ -96,17 +117,18 @@ class ClockSampler:
         except (OSError, FileNotFoundError):
             self.proc = None
 
-    def stop(self):
-        if self.proc is None:
-            return None
-        self.proc.terminate()
+    def query(self):
         try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.fh.close()
+            r = subprocess.run(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-i",
+                                str(self.gpu)], capture_output=True, text=True, timeout=10)
+            return r.stdout.strip()
+        except (OSError, subprocess.SubprocessError):
+            return ""
+
+    @staticmethod
+    def parse(lines):
         rows = []
-        for line in open(self.path):
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 10:
                 continue
@@ -115,6 +137,23 @@ class ClockSampler:
                                  hw=parts[6], hwt=parts[7], swt=parts[8], pcap=parts[9]))
             except ValueError:
                 continue
+        return rows
+
+    def stop(self):
+        self.edges.append(self.query())
+        rows = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+            rows = self.parse(open(self.path))
+        source = "samples every 200 ms during the timed legs"
+        if not rows:
+            rows = self.parse(self.edges)
+            source = "one query before and one after the timed legs"
         if not rows:
             return None
         loaded = [r for r in rows if r["util"] >= 50] or rows
@@ -125,7 +164,7 @@ class ClockSampler:
                 if r[k].lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(r["sm"] for r in loaded), "sm_max_mhz": max(r["smmax"] for r in loaded),
-                "reasons": sorted(reasons), "samples": len(loaded)}
+                "reasons": sorted(reasons), "samples": len(loaded), "source": source}
 
 
 def dist_setup(n_gpus: int, backend: str = "nccl"):
@@ -172,38 +211,78 @@ def barrier(world: int):
         dist.barrier()
 
 
-def cpu_baseline(budget_s: float = 12.0):
-    """The FP64 oracle on the host cores, on a bounded sample of the same workload: whole steps of
-    the 2048 x 1024 grid until about budget_s seconds of CPU time have been spent."""
-    import oracle
-    from paper_2408_15654_gb300 import workloads as W
-    p, f = W.shear_drop_large(NX, NY)
-    cores = oracle.set_threads(0)
+def timed_windows(torch, stream, advance, k: int, min_s: float = MIN_TIMED_S, max_windows: int = 2000):
+    """Device time of windows of exactly k steps (advance(k) enqueues them on `stream`), recorded
+    back to back with CUDA events until about min_s of steps has been timed.  Returns the median
+    window in ms and the number of windows."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    advance(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    first = e0.elapsed_time(e1)
+    n = max(0, min(max_windows - 1, int(min_s * 1e3 / max(first, 1e-3)) - 1))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for a, b in ev:
+        a.record(stream)
+        advance(k)
+        b.record(stream)
+    torch.cuda.synchronize()
+    times = [first] + [a.elapsed_time(b) for a, b in ev]
+    return statistics.median(times), len(times)
+
+
+def oracle_mlups(oracle, p, f, threads: int, budget_s: float, max_steps: int = 200):
+    """The FP64 oracle on `threads` host threads: whole steps of one lattice (after 1 untimed step)
+    until about budget_s seconds; returns (MLUPS, steps timed)."""
+    oracle.set_threads(threads)
     s = oracle.Sim(p)
     s.init(**f)
     t0 = time.perf_counter()
     s.step(1)
     t1 = time.perf_counter() - t0
-    n = max(1, min(200, int(budget_s / max(t1, 1e-6))))
+    n = max(1, min(max_steps, int(budget_s / max(t1, 1e-6))))
     t0 = time.perf_counter()
     s.step(n)
     dt = time.perf_counter() - t0
-    # the same oracle on one core, a few steps of the same run
-    oracle.set_threads(1)
-    t0 = time.perf_counter()
-    s.step(1)
-    t1c = time.perf_counter() - t0
-    n1 = max(1, min(20, int(budget_s / 2 / max(t1c, 1e-6))))
-    t0 = time.perf_counter()
-    s.step(n1)
-    dt1 = time.perf_counter() - t0
-    oracle.set_threads(cores)
     s.close()
-    return {"value": NX * NY * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{n} FP64 oracle steps of the 2048x1024 sheared drop after 1 untimed step, "
-                      f"OpenMP over rows ({cores} threads)",
-            "single_core": {"value": NX * NY * n1 / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
-                            "sample": f"{n1} further steps of the same run on one thread, after 1 untimed step"}}
+    return p["nx"] * p["ny"] * n / dt / 1e6, n
+
+
+def cpu_baselines(budget_s: float = 4.0):
+    """The FP64 oracle on the host cores for every configuration: all cores and one core, a bounded
+    number of whole steps each; the 64-lattice set as one step of each member in turn until the
+    budget is spent."""
+    import oracle
+    from paper_2408_15654_gb300 import workloads as W
+    cores = oracle.set_threads(0)
+    cfgs = {"stationary_drop_128x128": W.stationary_drop(), "surface_diffusion_256x256": W.surface_diffusion(),
+            "shear_drop_512x256": W.shear_drop(), "shear_drop_2048x1024": W.shear_drop_large(NX, NY)}
+    out = {"cores": cores, "unit": "MLUPS"}
+    for name, (p, f) in cfgs.items():
+        v, n = oracle_mlups(oracle, p, f, cores, budget_s * (3 if name.endswith("2048x1024") else 1))
+        v1, n1 = oracle_mlups(oracle, p, f, 1, budget_s)
+        out[name] = {"all_cores": sig(v), "steps": n, "one_core": sig(v1), "steps_one_core": n1}
+    # the 64-lattice set: members stepped once each, in order, until the budget is spent
+    for label, threads in (("all_cores", cores), ("one_core", 1)):
+        oracle.set_threads(threads)
+        cells, t_total, stepped = 0, 0.0, 0
+        for p, f in W.batch_instances(64, seed=0):
+            s = oracle.Sim(p)
+            s.init(**f)
+            t0 = time.perf_counter()
+            s.step(1)
+            t_total += time.perf_counter() - t0
+            s.close()
+            cells += p["nx"] * p["ny"]
+            stepped += 1
+            if t_total > budget_s:
+                break
+        out.setdefault("batch_mix64", {})[label] = sig(cells / t_total / 1e6)
+        out["batch_mix64"]["members_" + label] = stepped
+    oracle.set_threads(cores)
+    return out
 
 
 def batch_leg(torch, lbm, W, storage: str, steps: int, alone_steps: int = 0):
@@ -231,10 +310,10 @@ def batch_leg(torch, lbm, W, storage: str, steps: int, alone_steps: int = 0):
     if any(g.status != lbm.LBM_OK for g in lats):
         raise RuntimeError(f"unstable member in the {storage} batch: {lbm.lbm_last_error()}")
     bpl = BYTES_PER_LUP if storage == "fp32" else HALF_MODES[storage]
-    out = {"value": cells * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "storage": storage, "steps": steps,
-           "ms_per_step": ms / steps, "schedule": sched, "graph_steps": k, "gpu_launches": b.launches - n0,
-           "achieved_gbs": cells * bpl * steps / (ms * 1e-3) / 1e9,
-           "frac_of_measured_hbm": cells * bpl * steps / (ms * 1e-3) / 1e9 / measured_peak()[0]}
+    out = {"value": sig(cells * steps / (ms * 1e-3) / 1e6), "unit": "MLUPS", "storage": storage, "steps": steps,
+           "ms_per_step": sig(ms / steps), "schedule": sched, "graph_steps": k, "gpu_launches": b.launches - n0,
+           "achieved_gbs": sig(cells * bpl * steps / (ms * 1e-3) / 1e9),
+           "frac_of_measured_hbm": sig(cells * bpl * steps / (ms * 1e-3) / 1e9 / measured_peak()[0])}
     if alone_steps:
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(bstream)
@@ -242,22 +321,24 @@ def batch_leg(torch, lbm, W, storage: str, steps: int, alone_steps: int = 0):
             g.step(alone_steps)
         a1.record(bstream)
         torch.cuda.synchronize()
-        out["one_at_a_time"] = {"value": cells * alone_steps / (a0.elapsed_time(a1) * 1e-3) / 1e6, "unit": "MLUPS",
-                                "steps": alone_steps, "gpu_launches": 64 * alone_steps}
+        out["one_at_a_time"] = {"value": sig(cells * alone_steps / (a0.elapsed_time(a1) * 1e-3) / 1e6),
+                                "unit": "MLUPS", "steps": alone_steps, "gpu_launches": 64 * alone_steps}
     b.close()
     for g in lats:
         g.close()
     return out, cells
 
 
-def serving_leg(torch, lbm, W, reqs, jobs, policy: str, max_jobs: int, force_fp32: bool = False):
+def serving_leg(torch, lbm, W, reqs, jobs, policy: str, max_jobs: int, arena_bytes: int, force_fp32: bool = False):
     """Replay the request stream against a lattice server: each job is submitted at its arrival
-    time; time to solution = final fields copied out - submission, on the server's clock."""
+    time; time to solution = final fields copied out - submission, on the server's clock.  Jobs
+    are admitted while their workspaces fit the arena (sized from the device's free memory) and the
+    job cap allows."""
     import numpy as np
 
     stream = torch.cuda.Stream()
-    srv = lbm.Server(8 << 30 if max_jobs > 1 else 1 << 30, stream, policy=policy, max_jobs=max_jobs,
-                     max_cells=8 << 20, chunk_steps=200, graph_steps=16)
+    srv = lbm.Server(arena_bytes, stream, policy=policy, max_jobs=max_jobs, max_cells=1 << 40,
+                     chunk_steps=200, graph_steps=16)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for r, (p, f) in zip(reqs, jobs):
@@ -273,40 +354,42 @@ def serving_leg(torch, lbm, W, reqs, jobs, policy: str, max_jobs: int, force_fp3
         res += got
     st = srv.stats()
     srv.close()
+    del srv
+    torch.cuda.empty_cache()
     bad = [r for r in res if r["status"] != lbm.LBM_OK]
     if bad:
         raise RuntimeError(f"serving job failed: {bad[0]['message']}")
     tts = np.array([r["t_done"] - r["t_submit"] for r in res])
     makespan = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
     lup = sum(r["nx"] * r["ny"] * r["steps"] for r in res)
-    return {"policy": policy, "max_jobs": max_jobs, "storage": "fp32" if force_fp32 else "fp32/fp16 as requested",
-            "p50_s": float(np.percentile(tts, 50)), "p99_s": float(np.percentile(tts, 99)),
-            "mean_s": float(tts.mean()), "makespan_s": makespan, "value": lup / makespan / 1e6, "unit": "MLUPS",
-            "lattice_updates": lup, "gpu_launches": st["kernel_launches"], "rounds": st["rounds"]}
+    return {"policy": policy, "max_jobs": max_jobs, "jobs": len(res),
+            "storage": "fp32" if force_fp32 else "fp32/fp16 as requested",
+            "p50_s": sig(float(np.percentile(tts, 50))), "p99_s": sig(float(np.percentile(tts, 99))),
+            "mean_s": sig(float(tts.mean())), "makespan_s": sig(makespan), "value": sig(lup / makespan / 1e6),
+            "unit": "MLUPS", "lattice_updates": lup, "gpu_launches": st["kernel_launches"], "rounds": st["rounds"]}
 
 
-def timed_leg(torch, lbm, p, f, args, stream, world, what: str, bytes_per_lup: int):
-    """Warm-up, then exactly args.steps steps of one lattice timed with CUDA events on its stream."""
+def lattice_leg(torch, lbm, p, f, args, stream, world, what: str, bytes_per_lup):
+    """Warm-up, then median K-step windows of one lattice (CUDA events on its stream)."""
     sim = lbm.Lattice(p, stream=stream)
     sim.init(**f)
     sim.step(args.warmup)
     torch.cuda.synchronize()
     barrier(world)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sim.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms, nwin = timed_windows(torch, stream, sim.step, args.steps)
     ms_max = barrier_max(ms, world)
     if sim.status != lbm.LBM_OK:
         raise RuntimeError(f"unstable state in the {what} benchmark: {lbm.lbm_last_error()}")
+    kernel = sim.kernel
     sim.close()
     cells = p["nx"] * p["ny"]
-    ach = cells * bytes_per_lup / (ms / args.steps * 1e-3) / 1e9
-    return {"value": cells * args.steps * world / (ms_max * 1e-3) / 1e6, "unit": "MLUPS",
-            "ms_per_step": ms_max / args.steps, "achieved_gbs": ach,
-            "frac_of_measured_hbm": ach / measured_peak()[0], "algorithmic_bytes_per_lup": bytes_per_lup}
+    out = {"value": sig(cells * args.steps * world / (ms_max * 1e-3) / 1e6), "unit": "MLUPS",
+           "us_per_step": sig(ms_max / args.steps * 1e3), "windows": nwin, "kernel": kernel}
+    if bytes_per_lup:
+        ach = cells * bytes_per_lup / (ms / args.steps * 1e-3) / 1e9
+        out.update({"achieved_gbs": sig(ach), "frac_of_measured_hbm": sig(ach / measured_peak()[0]),
+                    "algorithmic_bytes_per_lup": bytes_per_lup})
+    return out
 
 
 GOLDEN = os.path.join(ROOT, "tests", "golden", "shear_drop_2048x1024_10000_samples.txt")
@@ -335,7 +418,7 @@ def precision_leg(torch, lbm, W, stream):
     a = np.array(rows)
     xs, ys = a[:, 0].astype(int), a[:, 1].astype(int)
     steps = int(head["steps"])
-    out = {"steps": steps, "sample_cells": len(xs), "n_eps": head["n_eps"]}
+    out = {"steps": steps, "cells": len(xs), "n_eps": head["n_eps"]}
     p, f = W.shear_drop_large(NX, NY)
     for st in ("fp32",) + tuple(HALF_MODES):
         sim = lbm.Lattice(dict(p, storage=st, n_eps=head["n_eps"]), stream=stream)
@@ -344,15 +427,17 @@ def precision_leg(torch, lbm, W, stream):
         m = sim.moments()
         rel = lambda g, o: float(np.linalg.norm(g - o) / np.linalg.norm(o))  # noqa: E731
         du = np.hypot(m["ux"][ys, xs] - a[:, 4], m["uy"][ys, xs] - a[:, 5])
-        out[st] = {"phi": rel(m["phi"][ys, xs], a[:, 2]), "psi": rel(m["psi"][ys, xs], a[:, 3]),
-                   "u": float(np.linalg.norm(du) / np.linalg.norm(np.hypot(a[:, 4], a[:, 5]))),
-                   "total_phi": abs(sim.total("phi") - head["total_phi"]) / head["total_phi"]}
+        out[st] = {"phi": sig(rel(m["phi"][ys, xs], a[:, 2]), 2), "psi": sig(rel(m["psi"][ys, xs], a[:, 3]), 2),
+                   "u": sig(float(np.linalg.norm(du) / np.linalg.norm(np.hypot(a[:, 4], a[:, 5]))), 2),
+                   "sum_phi": sig(abs(sim.total("phi") - head["total_phi"]) / head["total_phi"], 2)}
         sim.close()
     return out
 
 
 def run_reference(args):
-    """--impl reference: the FP64 oracle as it stands on the host cores (rank 0 only)."""
+    """--impl reference: the FP64 oracle as it stands on the host cores (rank 0 only), on the same
+    workload; W untimed steps (at most 3, each takes seconds), then up to K timed steps bounded to
+    about 90 s."""
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
         return
@@ -362,9 +447,10 @@ def run_reference(args):
     cores = oracle.set_threads(0)
     s = oracle.Sim(p)
     s.init(**f)
+    warm = max(1, min(args.warmup, 3))
     t0 = time.perf_counter()
-    s.step(min(args.warmup, 1) or 1)
-    t_step = time.perf_counter() - t0
+    s.step(warm)
+    t_step = (time.perf_counter() - t0) / warm
     budget = 90.0
     k = max(1, min(args.steps, int(budget / max(t_step, 1e-6))))
     t0 = time.perf_counter()
@@ -372,12 +458,13 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     value = NX * NY * k / dt / 1e6
     sample = (f"{k} of the {args.steps} requested FP64 oracle steps of the 2048x1024 sheared drop "
-              f"(bounded to ~{budget:.0f} s), {cores} OpenMP threads")
+              f"(bounded to ~{budget:.0f} s) after {warm} untimed, {cores} OpenMP threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
-        "steps": k, "warmup": 1, "ms_per_step": dt / k * 1e3, "higher_is_better": True, "scaling": "weak",
+        "steps": k, "warmup": warm, "ms_per_step": dt / k * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [NX, NY], "parallelism": "host cores (OpenMP)"},
+        "config": {"workload": "FP64 CPU oracle (the reference arm) on " + WORKLOAD.replace(", FP32 storage", ""),
+                   "grid": [NX, NY], "parallelism": f"host cores (OpenMP, {cores} threads)"},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -394,75 +481,62 @@ def run_ours(args):
     lbm.load()
     p, f = W.shear_drop_large(NX, NY)
     stream = torch.cuda.current_stream()
+    cells = NX * NY
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+
+    # ---- headline: FP32 storage, 2048 x 1024, inputs resident in HBM ----
     sim = lbm.Lattice(p, stream=stream)
     sim.init(**f)
-    cells = NX * NY
-
-    # warm-up
     sim.step(args.warmup)
     torch.cuda.synchronize()
-
-    # device-timed region: exactly K steps, inputs already resident in HBM
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     barrier(world)
     torch.cuda.synchronize()
-    start.record(stream)
-    sim.step(args.steps)
-    stop.record(stream)
+    ms, nwin = timed_windows(torch, stream, sim.step, args.steps)
     torch.cuda.synchronize()
     barrier(world)
-    clocks = sampler.stop() if sampler else None
-    ms = start.elapsed_time(stop)
     ms_max = barrier_max(ms, world)
-    st = sim.status
-    if st != lbm.LBM_OK:
+    if sim.status != lbm.LBM_OK:
         raise RuntimeError(f"unstable state during the benchmark: {lbm.lbm_last_error()}")
     value = aggregate_mlups(cells, args.steps, world, ms_max)
+    timed_steps = args.steps * nwin
 
-    # the same workload with 16-bit population storage (FP32 arithmetic)
+    # ---- the same workload with 16-bit population storage (FP32 arithmetic) ----
     half = {}
     for st, bpl in HALF_MODES.items():
-        hs = lbm.Lattice(dict(p, storage=st), stream=stream)
-        hs.init(**f)
-        hs.step(args.warmup)
-        torch.cuda.synchronize()
-        barrier(world)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        hs.step(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        hms = barrier_max(e0.elapsed_time(e1), world)
-        if hs.status != lbm.LBM_OK:
-            raise RuntimeError(f"unstable state in the {st} benchmark: {lbm.lbm_last_error()}")
-        hv = cells * args.steps * world / (hms * 1e-3) / 1e6
-        hach = cells * bpl / (e0.elapsed_time(e1) / args.steps * 1e-3) / 1e9
-        half[st] = {"value": hv, "unit": "MLUPS", "ratio_vs_fp32": hv / (cells * args.steps * world / (ms_max * 1e-3) / 1e6),
-                    "ms_per_step": hms / args.steps, "achieved_gbs": hach,
-                    "frac_of_measured_hbm": hach / measured_peak()[0], "algorithmic_bytes_per_lup": bpl}
-        hs.close()
+        r = lattice_leg(torch, lbm, dict(p, storage=st), f, args, stream, world, st, bpl)
+        half[st] = {"MLUPS": r["value"], "x_fp32": sig(r["value"] / value, 3), "us": r["us_per_step"],
+                    "hbm_frac": r["frac_of_measured_hbm"], "B_per_lup": bpl}
 
-    # prescribed velocity (f and g only): the convection test's drop at 2048 x 1024
+    # ---- the square 2048 x 2048 grid (the second roofline lattice), FP32 and FP16 ----
+    sp, sf = W.shear_drop(NX, NX, R=160.0)
+    square = {st: lattice_leg(torch, lbm, dict(sp, storage=st), sf, args, stream, world, f"2048^2 {st}",
+                              BYTES_PER_LUP if st == "fp32" else BYTES_PER_LUP_16) for st in ("fp32", "fp16")}
+    square["workload"] = "sheared drop 2048x2048 (walls +/-0.01, R=160, Re=1, Ca=0.2, Langmuir E0=0.2)"
+
+    # ---- the small configurations, FP32 (L2-resident, launch-bound: MLUPS only) ----
+    small = {}
+    for name, (cp, cf) in {"stationary_drop_128x128": W.stationary_drop(),
+                           "surface_diffusion_256x256": W.surface_diffusion(),
+                           "shear_drop_512x256": W.shear_drop()}.items():
+        small[name] = lattice_leg(torch, lbm, cp, cf, args, stream, world, name, None)
+
+    # ---- prescribed velocity (f and g only): the convection test's drop at 2048 x 1024 ----
     prescribed = {}
     pp, pf = W.convected_drop(NX, NY, R=160.0)
     for st, bpl in BYTES_PER_LUP_PRESCRIBED.items():
-        prescribed[st] = timed_leg(torch, lbm, dict(pp, storage=st), pf, args, stream, world, f"prescribed {st}", bpl)
+        prescribed[st] = lattice_leg(torch, lbm, dict(pp, storage=st), pf, args, stream, world, f"prescribed {st}", bpl)
     prescribed["workload"] = ("drop R=160 carried by an imposed u = (0.05, 0) on 2048x1024, periodic, "
                               "M_phi=1, D=2 (the convection test of Sec. 4 scaled up); f, g only")
 
-    # density ratio 10: the rising bubble of Sec. 4 at R = 256 (1024 x 2048, the same cell count)
+    # ---- density ratio 10: the rising bubble of Sec. 4 at R = 256 (1024 x 2048) ----
     var_rho = {}
     bp, bf = W.rising_bubble(256.0)
     for st, bpl in BYTES_PER_LUP_VAR_RHO.items():
-        var_rho[st] = timed_leg(torch, lbm, dict(bp, storage=st), bf, args, stream, world, f"density-ratio {st}", bpl)
+        var_rho[st] = lattice_leg(torch, lbm, dict(bp, storage=st), bf, args, stream, world, f"density-ratio {st}", bpl)
     var_rho["workload"] = ("rising bubble R=256 on 1024x2048 (Sec. 4: rho and mu ratio 10, Re=35, Bo=10, Pe=10, "
                            "E0=0.5, linear EOS, walls below and above, gravity); mass-flux history included")
 
-    # errors of every storage mode against the oracle after 10 000 steps (untimed)
-    precision = precision_leg(torch, lbm, W, stream) if (rank == 0 and not args.no_precision) else None
-
-    # many lattices at once: the 64-lattice mix, FP32 and FP16 storage
+    # ---- many lattices at once: the 64-lattice mix, FP32 and FP16 storage ----
     batch = {}
     if args.batch_steps > 0:
         for st in ("fp32", "fp16"):
@@ -470,28 +544,19 @@ def run_ours(args):
                                           alone_steps=100 if st == "fp32" else 0)
         batch["workload"] = (f"64 seeded drops (seed 0), sizes uniform over 128^2, 256^2, 512x256, 1024x512 "
                              f"({bcells} cells), walls at +/-U with U ~ U[0, 0.02], linear EOS")
+    clocks = sampler.stop() if sampler else None
 
-    # serving: a seeded Poisson stream of sheared-drop jobs against the lattice server
-    serving = {}
-    if args.serving_requests > 0:
-        reqs = W.serving_requests(200, 20.0, seed=0)[:args.serving_requests]
-        jobs = [W.serving_job(r) for r in reqs]
-        serving = {"workload": (f"the first {len(reqs)} of 200 seeded requests (seed 0): Poisson arrivals at 20/s, "
-                                f"sheared drops nx = side ~ U{{256..2048 step 64}}, ny = side/2, R = 40 side/512, "
-                                f"steps ~ U[5000, 50000], storage FP32 or FP16 with p = 1/2; p99 over "
-                                f"{len(reqs)} jobs")}
-        for pol in args.serving_policies.split(","):
-            serving[pol] = serving_leg(torch, lbm, W, reqs, jobs, pol, max_jobs=64)
-        serving["one_at_a_time_fp32"] = serving_leg(torch, lbm, W, reqs, jobs, "fcfs", max_jobs=1, force_fp32=True)
-        del jobs
+    # ---- errors of every storage mode against the oracle after 10 000 steps (untimed) ----
+    precision = precision_leg(torch, lbm, W, stream) if (rank == 0 and not args.no_precision) else None
 
-    # roofline of the step kernel (one launch per step, so launch duration = step time)
+    # ---- roofline of the step kernel (one launch per step, so launch duration = step time) ----
     peak, peak_kind = measured_peak()
     launch_s = ms / args.steps * 1e-3
     achieved = cells * BYTES_PER_LUP / launch_s / 1e9
+    achieved_survey = cells * BYTES_PER_LUP_SURVEY / launch_s / 1e9
     traffic = profiled_traffic()
 
-    # end to end through the C ABI with pinned host buffers: upload the fields, K steps, read back
+    # ---- end to end through the C ABI with pinned host buffers: upload the fields, K steps, read back ----
     host_in = {k: torch.from_numpy(np.array(v, dtype=np.float64)).pin_memory().numpy() for k, v in f.items()}
     host_out = [torch.empty((NY, NX), dtype=torch.float64).pin_memory().numpy() for _ in range(5)]
     torch.cuda.synchronize()
@@ -503,38 +568,73 @@ def run_ours(args):
     e2e_s = barrier_max(time.perf_counter() - t0, world)
     e2e = cells * args.steps * world / e2e_s / 1e6
     io_bytes = 5 * cells * 8
+    sim.close()
+    del sim, host_in, host_out
+    torch.cuda.empty_cache()
+
+    # ---- serving: a seeded Poisson stream of sheared-drop jobs against the lattice server ----
+    serving = {}
+    if args.serving_requests > 0:
+        reqs = W.serving_requests(200, 20.0, seed=0)[:args.serving_requests]
+        jobs = [W.serving_job(r) for r in reqs]
+        free, total = torch.cuda.mem_get_info()
+        arena = max(1 << 30, free - SERVING_MARGIN)
+        serving = {"workload": (f"the first {len(reqs)} of 200 seeded requests (seed 0): Poisson arrivals at 20/s, "
+                                f"sheared drops on square grids side ~ U{{256..2048 step 64}}, R = 40 side/512, "
+                                f"steps ~ U[5000, 50000], storage FP32 or FP16 with p = 1/2"),
+                   "admission": (f"job workspaces from an arena of {arena >> 20} MiB, the device's free memory at "
+                                 f"start less {SERVING_MARGIN >> 30} GiB; at most 64 jobs at once")}
+        for pol in args.serving_policies.split(","):
+            serving[pol] = serving_leg(torch, lbm, W, reqs, jobs, pol, 64, arena)
+        # one job at a time, on the first requests of the same stream: with the storage each job
+        # asked for (what continuous batching adds) and all in FP32 (the plain path)
+        n1 = min(len(reqs), args.serving_alone) if args.serving_alone > 0 else len(reqs)
+        serving["one_at_a_time"] = serving_leg(torch, lbm, W, reqs[:n1], jobs[:n1], "fcfs", 1, arena)
+        serving["one_at_a_time_fp32"] = serving_leg(torch, lbm, W, reqs[:n1], jobs[:n1], "fcfs", 1, arena,
+                                                     force_fp32=True)
+        del jobs
 
     if rank == 0:
-        base = cpu_baseline() if (world == 1 and not args.no_cpu_baseline) else None
+        base = cpu_baselines() if (world == 1 and not args.no_cpu_baseline) else None
+        head = base["shear_drop_2048x1024"] if base else None
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [NX, NY], "storage": "fp32",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (2 x 218 MB population buffers), no flush"},
+                       "l2": "inputs larger than L2 (2 x 218 MB population buffers), no flush",
+                       "timing": f"median of {nwin} back-to-back windows of {args.steps} steps ({timed_steps} steps)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                         "algorithmic_bytes_per_lup": BYTES_PER_LUP},
-            "half_store": half,
-            "precision_vs_oracle": precision,
-            "prescribed_velocity": prescribed,
-            "density_ratio": var_rho,
-            "batch": batch,
-            "serving": serving,
-            "cpu_baseline": base,
+                         "algorithmic_bytes_per_lup": BYTES_PER_LUP,
+                         "survey_bytes_per_lup": BYTES_PER_LUP_SURVEY,
+                         "frac_at_survey_bytes": achieved_survey / peak},
+            "cpu_baseline": ({"value": head["all_cores"], "unit": "MLUPS", "cores": base["cores"], "kind": "oracle",
+                              "sample": f"{head['steps']} FP64 oracle steps of the 2048x1024 sheared drop after 1 "
+                                        f"untimed step, OpenMP over rows ({base['cores']} threads); every "
+                                        f"configuration on all cores and one core in cpu_baselines"}
+                             if base else None),
             "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": io_bytes / args.steps,
                     "d2h_bytes_per_step": io_bytes / args.steps,
                     "job": f"lbm_init_fields(host) + lbm_step({args.steps}) + lbm_get_moments(host, all 5)"},
-            "gpu_launches": args.steps,
+            "gpu_launches": timed_steps,
+            "serving": serving,
+            "batch": batch,
+            "density_ratio": var_rho,
+            "prescribed_velocity": prescribed,
+            "small_configs_fp32": small,
+            "cpu_baselines": base,
+            "square_2048x2048": square,
             "gpu_launches_half_store": len(HALF_MODES) * args.steps,
-            "gpu_launches_prescribed": len(BYTES_PER_LUP_PRESCRIBED) * args.steps,
-            "gpu_launches_density_ratio": len(BYTES_PER_LUP_VAR_RHO) * args.steps,
             "clocks": clocks,
+            # last, so that a reader of the line's tail sees them: each 16-bit mode against FP32 at
+            # 2048 x 1024, and every storage mode's error against the oracle after 10 000 steps
+            "half_store": half,
+            "precision_vs_oracle": precision,
         }
         print(json.dumps(line), flush=True)
-    sim.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -549,9 +649,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the untimed storage-error leg")
     ap.add_argument("--batch-steps", type=int, default=1000, help="steps of the 64-lattice batch legs (0: skip)")
-    ap.add_argument("--serving-requests", type=int, default=24,
+    ap.add_argument("--serving-requests", type=int, default=100,
                     help="requests of the seeded serving stream to replay (at most 200; 0: skip)")
-    ap.add_argument("--serving-policies", default="fcfs,shortest_first")
+    ap.add_argument("--serving-policies", default="fcfs", help="comma-separated: fcfs, shortest_first")
+    ap.add_argument("--serving-alone", type=int, default=24,
+                    help="requests replayed one job at a time for comparison (0: all of them)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -226,7 +226,7 @@ SERVING_SIDES = tuple(range(256, 2049, 64))
 
 def serving_requests(count=200, rate=20.0, seed=0):
     """Seeded job stream for the lattice server: Poisson arrivals at `rate` per second; each job a
-    sheared drop (as shear_drop) of nx = side ~ U{256, 320, ..., 2048}, ny = side / 2 and
+    sheared drop (as shear_drop) on a square grid of side ~ U{256, 320, ..., 2048} with
     R = 40 side / 512; steps ~ U[5000, 50000]; storage FP32 or FP16 with probability 1/2 each.
     Returns dicts with the arrival time `t` (seconds from the first), nx, ny, R, steps, storage;
     serving_job builds a job's parameters and fields."""
@@ -239,7 +239,7 @@ def serving_requests(count=200, rate=20.0, seed=0):
         side = int(SERVING_SIDES[rng.integers(0, len(SERVING_SIDES))])
         steps = int(rng.integers(5000, 50001))
         storage = "fp16" if rng.random() < 0.5 else "fp32"
-        out.append({"t": t, "nx": side, "ny": side // 2, "R": 40.0 * side / 512.0, "steps": steps,
+        out.append({"t": t, "nx": side, "ny": side, "R": 40.0 * side / 512.0, "steps": steps,
                     "storage": storage})
     return out
 
