@@ -68,11 +68,42 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
-def _load():
+def build_variant(name: str, substitutions) -> str:
+    """Compile a copy of the oracle with text substitutions [(old, new), ...] into
+    ``oracle/_build/variants/<name>`` and return its path.  Tests use it to plant a mistake in the
+    oracle and show that a pin catches it; nothing else loads a variant."""
+    src = open(_SRC).read()
+    for old, new in substitutions:
+        if old not in src:
+            raise ValueError(f"variant {name}: text to replace not found: {old!r}")
+        src = src.replace(old, new)
+    d = os.path.join(_BUILD_DIR, "variants", name)
+    os.makedirs(d, exist_ok=True)
+    with open(os.path.join(d, "lbm_oracle.c"), "w") as fh:
+        fh.write(src)
+    out = os.path.join(d, "liboracle.so")
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-I", os.path.dirname(_HDR), "-o", out, os.path.join(d, "lbm_oracle.c"), "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
+_variants = {}
+
+
+def _load(path: str | None = None):
     global _lib
+    if path is not None:
+        if path not in _variants:
+            _variants[path] = _bind(C.CDLL(path))
+        return _variants[path]
     if _lib is not None:
         return _lib
-    lib = C.CDLL(build())
+    _lib = _bind(C.CDLL(build()))
+    return _lib
+
+
+def _bind(lib):
     dp = C.POINTER(C.c_double)
     lib.orc_create.restype = C.c_void_p
     lib.orc_create.argtypes = [C.POINTER(_Params)]
@@ -92,7 +123,6 @@ def _load():
     lib.orc_operators.argtypes = [dp, dp, dp]
     lib.orc_moment_matrix.argtypes = [dp]
     lib.orc_lattice.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
-    _lib = lib
     return lib
 
 
@@ -160,8 +190,8 @@ def cell_distributions(p: dict, **cell) -> dict:
 class Sim:
     """One oracle simulation: populations on an (ny, nx) grid in FP64."""
 
-    def __init__(self, params: dict):
-        self._lib = _load()
+    def __init__(self, params: dict, lib_path: str | None = None):
+        self._lib = _load(lib_path)
         self.params = dict(params)
         self._p = make_params(params)
         self.nx, self.ny = self._p.nx, self._p.ny

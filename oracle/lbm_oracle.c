@@ -60,10 +60,11 @@
  * is parallel to u) and of a relaxing drop (which fixes the sign of S), and hydrostatic layers.
  * Dropping S from h_eq, the grad rho part of m2H or u.grad rho from P, flipping the sign of S,
  * taking nu = mu instead of mu / rho, or taking u = sum c h + F/2 without 1/rho, each fails one
- * of them.
- * Parity unpinned: the time derivative of S (the S history).  Taking the previous S equal to the
- * current one changes none of the pinned flows by more than a few parts in 1e4 of their deviation,
- * and no closed form isolates the term.
+ * of them.  The time derivative of S (the S history) is pinned by the same translating relaxing
+ * slab refined in the acoustic scaling (velocity, M_phi / W and nu / W fixed in lattice units),
+ * where u d_t S is as large as the fluxes it corrects: the deviation from uniform translation
+ * falls at about second order, and with the previous S taken equal to the current one it stops
+ * falling (a copy of this file with that mistake is built and checked by the tests).
  */
 #include <math.h>
 #include <stdlib.h>
