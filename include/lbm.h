@@ -193,8 +193,10 @@ int lbm_selftest_wait(unsigned* d_word, void* cuda_stream);
  * Limit: ny <= LBM_NOALLOC_MAX_ROWS (one partial sum per row); larger grids return LBM_EINVAL
  * with a message.  nx >= 2, ny >= 2, nx * ny <= 2^30.
  * The fixed array (LBM_NOALLOC_MAX_ROWS + 1 doubles, about 64 KB) exists once per GPU that loads
- * the library and stays there until the process exits.  The first call on each device looks up
- * its address (with that device current), so make that first call before any stream capture.
+ * the library and stays there until the process exits.  Its address is looked up by the first
+ * call in each CUDA context (normally the primary context of the current device; a caller that
+ * makes its own context current gets that context's copy), so make that first call before any
+ * stream capture.
  * All calls share the array: calls that overlap on the GPU (other streams, other threads) race and
  * must be serialised by the caller.  Each call writes every entry it reads, so nothing carries over
  * from the previous call.  No device memory is allocated or freed. */

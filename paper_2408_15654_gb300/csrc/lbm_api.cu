@@ -12,6 +12,8 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "lbm_internal.h"
 
@@ -319,23 +321,48 @@ static __device__ __align__(256) double g_noalloc_partials[LBM_NOALLOC_MAX_ROWS 
 
 namespace {
 
-constexpr int kMaxDevices = 64;
+// The scratch's device address differs per CUDA context (the library's module is loaded into each
+// context that uses it), so the cache is keyed by the context current at the call: the primary
+// context of each device, or any context the caller has made current.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
 std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[kMaxDevices] = {};
+std::vector<std::pair<CUcontext, double*>> g_noalloc_ptr;
 
-// Device address of the fixed scratch on the current device, looked up once per device.
-int noalloc_scratch(double** out) {
-    int dev = 0;
-    LBM_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(LBM_EINVAL, "device index %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+int current_context(CUcontext* ctx) {
+    static CtxGetCurrentFn fn = nullptr;
+    if (!fn) {
         void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
-        if (e != cudaSuccess) return fail(LBM_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !ptr)
+            return fail(LBM_ECUDA, "cuCtxGetCurrent is not available from the driver");
+        fn = reinterpret_cast<CtxGetCurrentFn>(ptr);
     }
-    *out = g_noalloc_ptr[dev];
+    *ctx = nullptr;
+    if (fn(ctx) != CUDA_SUCCESS) return fail(LBM_ECUDA, "cuCtxGetCurrent failed");
+    return LBM_OK;
+}
+
+// Device address of the fixed scratch in the current context, looked up once per context (the
+// lookup makes the device's primary context current if no context is).
+int noalloc_scratch(double** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    CUcontext ctx = nullptr;
+    int rc = current_context(&ctx);
+    if (rc) return rc;
+    if (ctx)
+        for (const auto& e : g_noalloc_ptr)
+            if (e.first == ctx) {
+                *out = e.second;
+                return LBM_OK;
+            }
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    rc = current_context(&ctx);
+    if (rc) return rc;
+    g_noalloc_ptr.emplace_back(ctx, static_cast<double*>(ptr));
+    *out = static_cast<double*>(ptr);
     return LBM_OK;
 }
 

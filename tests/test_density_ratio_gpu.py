@@ -26,8 +26,9 @@ def rel_l2(a, b):
 
 def case(name, n_eps=1e-4):
     """The rising bubble of Sec. 4 at R = 16 (64 x 128, walls, gravity, ratio 10 in density and
-    viscosity); a relaxing slab translating along its normal (S parallel to u); a perturbed drop of
-    ratio 5 with the Langmuir EOS on a ragged grid between moving walls.  These runs take the unit
+    viscosity) and at the paper's resolution R = 60 (240 x 480, 1000 steps); a relaxing slab
+    translating along its normal (S parallel to u); a perturbed drop of ratio 5 with the Langmuir
+    EOS on a ragged grid between moving walls.  These runs take the unit
     normal only where |grad phi| > 1e-4: with the default threshold (n wherever grad phi is not
     zero) the bulk normal is a rounding artifact and the FP64 oracle itself moves by 5e-5 under a
     single-precision jitter of its inputs (tests/test_conditioning.py).  The arithmetic is the same
@@ -35,6 +36,9 @@ def case(name, n_eps=1e-4):
     if name == "bubble_R16":
         p, f = W.rising_bubble(16.0)
         return (dict(p, n_eps=n_eps), f), 400
+    if name == "bubble_R60":
+        p, f = W.rising_bubble(60.0)
+        return (dict(p, n_eps=n_eps), f), 1000
     if name == "slab_70x6":
         n = 70
         x = np.arange(n) + 0.5
@@ -48,7 +52,7 @@ def case(name, n_eps=1e-4):
     return (p, W.perturbed(p, f, seed=7)), 200
 
 
-NAMES = ["bubble_R16", "slab_70x6", "langmuir_45x19"]
+NAMES = ["bubble_R16", "bubble_R60", "slab_70x6", "langmuir_45x19"]
 _oracle = {}
 
 
@@ -73,19 +77,35 @@ def errors(m, om):
 
 @pytest.mark.parametrize("name", NAMES)
 def test_density_ratio_matches_oracle(torch, name):
+    """phi and psi within 1e-5 (relative L2) in every case; u within 1e-5 relative L2, except for the
+    bubble at R = 60.  After 1000 steps that bubble has run for 0.05 of its time scale R / U_c
+    (U_c = 0.175 / R, the velocity scale of the paper's diffusive scaling) and |u| is about 1 % of
+    U_c, so a relative L2 of u compares FP32 rounding with a flow that has barely started: its u
+    error is held to 1e-5 of U_c (measured 3.4e-7) and to 1e-4 relative L2 (measured 3.9e-5).  The
+    same ratio of about 10 between the GPU-oracle difference and the GPU's own spread under a
+    single-precision jitter of the inputs holds at R = 16 (4.5e-6 against 5.6e-7) and at R = 60
+    (3.9e-5 against 2-3.5e-6), while the FP64 oracle moves by 1.9e-7 under that jitter."""
     (p, f), steps = case(name)
     om = oracle_moments(name)
     g = lbm.Lattice(p)
     g.init(**f)
     g.step(steps)
-    e = errors(g.moments(), om)
+    m = g.moments()
+    e = errors(m, om)
     print(name, {k: f"{v:.2e}" for k, v in e.items()})
     assert e["phi"] <= 1e-5 and e["psi"] <= 1e-5, e
-    assert e["u"] <= 1e-4 and e["P"] <= 1e-3, e
+    if name == "bubble_R60":
+        du = np.hypot(m["ux"] - om["ux"], m["uy"] - om["uy"])
+        u_scale = float(np.sqrt((du ** 2).mean()) / (0.175 / 60.0))
+        print(name, f"rms |du| / U_c {u_scale:.2e}")
+        assert u_scale <= 1e-5 and e["u"] <= 1e-4, (u_scale, e)
+    else:
+        assert e["u"] <= 1e-5, e
+    assert e["P"] <= 1e-3, e
     assert g.status == 0
 
 
-@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("name", ["bubble_R16", "slab_70x6", "langmuir_45x19"])
 def test_density_ratio_default_normal_threshold_short_run(torch, name):
     """The same cases for 40 steps with n taken wherever grad phi is not zero."""
     (p, f), _ = case(name, n_eps=1e-12)
@@ -97,8 +117,8 @@ def test_density_ratio_default_normal_threshold_short_run(torch, name):
     g.step(40)
     e = errors(g.moments(), o.moments())
     print(name, "n_eps 1e-12, 40 steps", {k: f"{v:.2e}" for k, v in e.items()})
-    assert e["phi"] <= 1e-5 and e["psi"] <= 1e-5, e
-    assert e["u"] <= 1e-4 and e["P"] <= 1e-3, e
+    assert e["phi"] <= 1e-5 and e["psi"] <= 1e-5 and e["u"] <= 1e-5, e
+    assert e["P"] <= 1e-3, e
 
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16_fg"])
