@@ -211,10 +211,11 @@ def barrier(world: int):
         dist.barrier()
 
 
-def timed_windows(torch, stream, advance, k: int, min_s: float = MIN_TIMED_S, max_windows: int = 2000):
+def timed_windows(torch, stream, advance, k: int, min_s: float = None, max_windows: int = 2000):
     """Device time of windows of exactly k steps (advance(k) enqueues them on `stream`), recorded
     back to back with CUDA events until about min_s of steps has been timed.  Returns the median
     window in ms and the number of windows."""
+    min_s = MIN_TIMED_S if min_s is None else min_s
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -646,6 +647,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--timed-seconds", type=float, default=1.0,
+                    help="device time each timed leg spends in K-step windows (0: one window)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the untimed storage-error leg")
     ap.add_argument("--batch-steps", type=int, default=1000, help="steps of the 64-lattice batch legs (0: skip)")
@@ -655,6 +658,8 @@ def main():
     ap.add_argument("--serving-alone", type=int, default=24,
                     help="requests replayed one job at a time for comparison (0: all of them)")
     args = ap.parse_args()
+    global MIN_TIMED_S
+    MIN_TIMED_S = max(0.0, args.timed_seconds)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
