@@ -157,10 +157,10 @@ Layout layout_of(const lbm_params* p) {
 // else the one-tile kernel.
 int default_kernel(int storage, bool var_rho, int pipe_blocks_per_sm) {
     // Measured on GB300 (us per step, one-tile / warp-specialised), sheared drop 2048 x 1024: FP32
-    // 72.8 / 73.6 (HBM-bound either way); two cells per thread in 32 x 8 tiles: FP16 53.5 / 64.2,
-    // BF16 54.2 / 64.7, FP16_FG 54.9 / 57.7, BF16_FG 55.4 / 58.6 (six 128-thread CTAs per SM hide
+    // 72.8 / 73.6 (HBM-bound either way); two cells per thread in 32 x 8 tiles: FP16 52.1 / 64.2,
+    // BF16 52.9 / 64.7, FP16_FG 56.3 / 57.7, BF16_FG 56.3 / 58.6 (five 128-thread CTAs per SM hide
     // the copy latency that the copy warp hid for the one-cell kernels); rising bubble 1024 x 2048
-    // (density ratio 10): FP32 83.9 / 80.1, FP16 64.9 / 64.6, whose larger cell update leaves room
+    // (density ratio 10): FP32 83.9 / 79.8, FP16 64.9 / 59.0, whose larger cell update leaves room
     // for fewer CTAs per SM, so the copy warp pays.
     (void)storage;
     if (var_rho && pipe_blocks_per_sm >= 1) return LBM_KERNEL_PIPELINED;

@@ -757,7 +757,10 @@ __device__ __forceinline__ C load_h(const unsigned char* sm, const float2* Hist,
 // (m*_0 = phi exactly, Sec. 3.1), so only u of the previous level is stored.
 // WS: called by the compute warps of a warp-specialised CTA, which synchronise among themselves
 // with named barrier 1 only (the copy warp has staged the tile and waits on its own barriers).
-template <int ST, bool WALLS, bool LANGMUIR, int MODE, int FLOW, bool WS = false>
+// EDGE = false: the tile is interior (tile_is_interior): every cell and every ring cell lies in
+// the grid away from its edges, so no cell writes ghost-frame copies, meets a wall or lies beyond
+// the grid, and those tests compile away.  The arithmetic is the same on both paths.
+template <int ST, bool WALLS, bool LANGMUIR, int MODE, int FLOW, bool WS = false, bool EDGE = true>
 __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsigned char* sm, float2* PP,
                                           unsigned long long* mbar, uint32_t parity, int x0, int y0) {
     using T = Traits<ST>;
@@ -777,8 +780,8 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
 
     const int tx = (t % G::TPR) * CPT, ty = t / G::TPR;
     const int x = x0 + tx, y = y0 + ty;
-    const bool active = (x < p.nx) && (y < p.ny);
-    const bool act1 = CPT == 2 && active && x + 1 < p.nx;  // the thread's second cell
+    const bool active = !EDGE || ((x < p.nx) && (y < p.ny));
+    const bool act1 = CPT == 2 && (!EDGE || (active && x + 1 < p.nx));  // the thread's second cell
     const long long cell = p.org + (long long)y * p.pitch + x;
     // mass flux of the previous step (density ratio != 1 only; the own cells', read early so that
     // its latency overlaps the stencil work)
@@ -810,7 +813,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     // the pulled pairs: summed here, and loaded again from the staged boxes for the collision, so
     // that they hold no registers through the rest of the cell update
     PV pp;  // (phi, psi)
-    const P* pull = FG + ((WALLS && y >= p.ny) ? p.ny - y0 : ty + 1) * G::BW + tx + 4;
+    const P* pull = FG + ((EDGE && WALLS && y >= p.ny) ? p.ny - y0 : ty + 1) * G::BW + tx + 4;
     {
         PV q[9];
 #pragma unroll
@@ -830,7 +833,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         else if (t < 2 * G::EX + G::TY) { ex = 0; ey = 1 + t - 2 * G::EX; }
         else { ex = G::EX - 1; ey = 1 + t - 2 * G::EX - G::TY; }
         int row = ey;
-        if (WALLS) {
+        if (EDGE && WALLS) {
             const int gy = y0 - 1 + ey;
             if (gy < 0) row = 1 - y0;
             else if (gy >= p.ny) row = p.ny - y0;
@@ -944,8 +947,8 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
 #pragma unroll
     for (int i = 0; i < 9; ++i) h[i] = bcv<C>(0.f);
     if constexpr (FLOW) {
-        const bool bb_up = WALLS && y == 0;           // links 2, 5, 6 come from below the bottom wall
-        const bool bb_dn = WALLS && y == p.ny - 1;    // links 4, 7, 8 come from above the top wall
+        const bool bb_up = EDGE && WALLS && y == 0;           // links 2, 5, 6 come from below the bottom wall
+        const bool bb_dn = EDGE && WALLS && y == p.ny - 1;    // links 4, 7, 8 come from above the top wall
         h[1] = load_h<ST, 1>(sm, Hist, p, tx, ty, false, uox, uoy);
         h[2] = load_h<ST, 2>(sm, Hist, p, tx, ty, bb_up, uox, uoy);
         h[3] = load_h<ST, 3>(sm, Hist, p, tx, ty, false, uox, uoy);
@@ -1065,8 +1068,8 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
         //      the bounce-back ghosts of the links that cross it.  putv(c) writes all of the
         //      thread's cells at index c (c even with two cells), put1(c, l) cell l alone, and
         //      putbb(d, i, o, l) the opposite slot o of cell l into link i's plane at index d ----
-        const bool yl = !WALLS && y <= 1, yr = !WALLS && y >= p.ny - 2;
-        const bool xedge = x <= 1 || x + CPT - 1 >= p.nx - 2;
+        const bool yl = EDGE && !WALLS && y <= 1, yr = EDGE && !WALLS && y >= p.ny - 2;
+        const bool xedge = EDGE && (x <= 1 || x + CPT - 1 >= p.nx - 2);
         const long long DX = p.nx, DY = (long long)p.ny * p.pitch;
         auto each_dest = [&](auto&& putv, auto&& put1, auto&& putbb) {
             putv(cell);
@@ -1090,7 +1093,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
                     }
                 }
             }
-            if (WALLS && (y == 0 || y == p.ny - 1)) {
+            if (EDGE && WALLS && (y == 0 || y == p.ny - 1)) {
                 // the pull of link i across the wall, at (x - c_ix, -1) or (x - c_ix, ny) in plane i,
                 // reads this cell's post-collision opposite slot (half-way bounce-back, Sec. 4)
 #pragma unroll
@@ -1195,7 +1198,7 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
             Y = vfma(half, vsub(BD, AC), Y);     // h3 += (B - A)/2, h4 += (D - C)/2
             U = vfma(quarter, vadd(EF, GH), U);  // h5 += (E + G)/4, h6 += (F + H)/4
             V = vfma(quarter, vsub(EF, GH), V);  // h7 += (E - G)/4, h8 += (F - H)/4
-            if (WALLS) {
+            if (EDGE && WALLS) {
                 // moving-wall term for the links that leave through a wall, folded in before storing:
                 // h_ibar(x_b, t+1) = h*_i(x_b, t) - 2 w_i rho c_i.u_w / cs2
                 if (y == 0)
@@ -1378,17 +1381,31 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     return false;
 }
 
+// A tile whose cells and ring all lie in the grid, at least two cells from every edge: none of its
+// cells writes a ghost-frame copy, meets a wall or lies beyond the grid (95 % of the tiles of a
+// 2048 x 1024 grid).
+template <int ST> __device__ __forceinline__ bool tile_is_interior(const Phys& p, int x0, int y0) {
+    using G = GeoOf<ST>;
+    return x0 >= 2 && x0 + G::TX + 2 <= p.nx && y0 >= 2 && y0 + G::TY + 2 <= p.ny;
+}
+// step_tile on the interior or the edge path (the choice is uniform over the tile).
+template <int ST, bool WALLS, bool LANGMUIR, int MODE, int FLOW, bool WS = false>
+__device__ __forceinline__ bool step_tile_any(const Phys& p, const TileIO& io, unsigned char* sm, float2* PP,
+                                              unsigned long long* mbar, uint32_t parity, int x0, int y0) {
+    if (tile_is_interior<ST>(p, x0, y0))
+        return step_tile<ST, WALLS, LANGMUIR, MODE, FLOW, WS, false>(p, io, sm, PP, mbar, parity, x0, y0);
+    return step_tile<ST, WALLS, LANGMUIR, MODE, FLOW, WS, true>(p, io, sm, PP, mbar, parity, x0, y0);
+}
+
 // Resident CTAs per SM that the one-tile kernels (step_kernel, batch_step_kernel) are compiled for.
 // FP32 storage: four; with a prescribed velocity (no h) the cell update fits 48 registers without
 // spills and the boxes 33 KB, so five (convection test 2048 x 1024: 54.3 -> 52.5 us per step).
-// Two cells per thread (128-thread CTAs): six, at 80 registers, which the update of two cells fits
-// once the pulled pairs are reloaded for the collision; the density-ratio update needs more, so
-// four (128 registers).
-// The batched kernels read the lattice's constants from shared memory and hold more of them in
-// registers: five CTAs (96 registers) for the two-cell per-tile kernel.
+// Two cells per thread (128-thread CTAs): five, at 96 registers (FP16 at 2048 x 1024: 51.8 us,
+// against 52.7 at six CTAs and 80 registers, where the interior path spills); the density-ratio
+// update needs more, so four (128 registers).
 template <int ST>
-__host__ __device__ constexpr int tile_min_blocks(int flow, bool batch = false) {
-    return cpt_of(ST) == 2 ? (flow == kFlowVarRho ? 4 : (batch ? 5 : 6)) : (flow == kFlowPrescribed ? 5 : 4);
+__host__ __device__ constexpr int tile_min_blocks(int flow) {
+    return cpt_of(ST) == 2 ? (flow == kFlowVarRho ? 4 : 5) : (flow == kFlowPrescribed ? 5 : 4);
 }
 template <int ST, bool WALLS, bool LANGMUIR, int MODE, int FLOW>
 __global__ void __launch_bounds__(GeoOf<ST>::NT, tile_min_blocks<ST>(FLOW)) step_kernel(const __grid_constant__ StepArgs a) {
@@ -1409,8 +1426,8 @@ __global__ void __launch_bounds__(GeoOf<ST>::NT, tile_min_blocks<ST>(FLOW)) step
     cudaTriggerProgrammaticLaunchCompletion();
     cudaGridDependencySynchronize();
     if (threadIdx.x == 0) issue_tile_loads<ST, FLOW>(sm, &a.tm_fg, &a.tm_h, &a.tm_hist, x0, y0, mbar);
-    step_tile<ST, WALLS, LANGMUIR, MODE, FLOW>(a.p, a.io, sm, reinterpret_cast<float2*>(sm + Smem<ST>::PP), mbar, 0, x0,
-                                               y0);
+    step_tile_any<ST, WALLS, LANGMUIR, MODE, FLOW>(a.p, a.io, sm, reinterpret_cast<float2*>(sm + Smem<ST>::PP), mbar, 0,
+                                                   x0, y0);
 }
 
 // Tile k of a grid of ntx x nty tiles: rows in the order first, last, then the interior (the two
@@ -1516,7 +1533,8 @@ __device__ __forceinline__ void step_pipe_body(const StepArgs& a, int ntx, int n
         const int x0 = slot[2 * b], y0 = slot[2 * b + 1];
         if (x0 < 0) break;  // uniform: every compute thread reads the same slot
         float2* PP = reinterpret_cast<float2*>(sm + S::PIPE_PP + b * S::PP_BYTES);
-        if (step_tile<ST, WALLS, LANGMUIR, kStep, FLOW, true>(a.p, a.io, sm + b * S::STAGE, PP, &full[b], parity, x0, y0))
+        if (step_tile_any<ST, WALLS, LANGMUIR, kStep, FLOW, true>(a.p, a.io, sm + b * S::STAGE, PP, &full[b], parity, x0,
+                                                                  y0))
             break;  // uniform (decided by the OR barrier inside)
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[b]);  // this warp is done with buffer b
@@ -1572,7 +1590,7 @@ __device__ __forceinline__ void flag_batch_timeout(const BatchArgs& b) {
 }
 
 template <int ST, bool WALLS, bool LANGMUIR, int FLOW>
-__global__ void __launch_bounds__(GeoOf<ST>::NT, tile_min_blocks<ST>(FLOW, true)) batch_step_kernel(const __grid_constant__ BatchArgs b) {
+__global__ void __launch_bounds__(GeoOf<ST>::NT, tile_min_blocks<ST>(FLOW)) batch_step_kernel(const __grid_constant__ BatchArgs b) {
     using S = Smem<ST>;
     using G = GeoOf<ST>;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -1583,11 +1601,13 @@ __global__ void __launch_bounds__(GeoOf<ST>::NT, tile_min_blocks<ST>(FLOW, true)
     const InstDesc& d = b.descs[te.x];
     const int x0 = (int)(te.y & 0xFFFFu) * G::TX, y0 = (int)(te.y >> 16) * G::TY;
     const int cur = (d.cur + b.s) & 1;
-    // the lattice's constants in shared memory (made visible by the first barrier of step_tile)
+    // the lattice's constants in shared memory, complete before any thread reads them (the
+    // choice of the interior path reads the grid size)
     Phys* sp = reinterpret_cast<Phys*>(sm + S::PHYS);
     static_assert(sizeof(Phys) % 4 == 0, "Phys is copied as words");
     for (int k = threadIdx.x; k < (int)(sizeof(Phys) / 4); k += G::NT)
         reinterpret_cast<uint32_t*>(sp)[k] = reinterpret_cast<const uint32_t*>(&d.p)[k];
+    __syncthreads();
     if (threadIdx.x == 0) {
         mbar_init(mbar, 1);
         fence_mbar_init();
@@ -1604,7 +1624,7 @@ __global__ void __launch_bounds__(GeoOf<ST>::NT, tile_min_blocks<ST>(FLOW, true)
     io.out[0] = io.out[1] = io.out[2] = io.out[3] = io.out[4] = nullptr;
     io.seed = step_seed(d.steps + b.s);
     io.first = d.first && b.s == 0;
-    step_tile<ST, WALLS, LANGMUIR, kStep, FLOW>(*sp, io, sm, reinterpret_cast<float2*>(sm + S::PP), mbar, 0, x0, y0);
+    step_tile_any<ST, WALLS, LANGMUIR, kStep, FLOW>(*sp, io, sm, reinterpret_cast<float2*>(sm + S::PP), mbar, 0, x0, y0);
 }
 
 // One step of many lattices by a persistent, warp-specialised grid (the design of step_kernel_pipe).
@@ -1717,7 +1737,7 @@ __device__ __forceinline__ void batch_ws_body(const BatchArgs& b) {
         io.first = d.first && b.s == 0;
         const Phys& p = *reinterpret_cast<const Phys*>(sm + S::BWS_PHYS + q * S::PHYS_BYTES);
         float2* PP = reinterpret_cast<float2*>(sm + S::PIPE_PP + q * S::PP_BYTES);
-        if (step_tile<ST, WALLS, LANGMUIR, kStep, FLOW, true>(p, io, sm + q * S::STAGE, PP, &full[q], parity, x0, y0))
+        if (step_tile_any<ST, WALLS, LANGMUIR, kStep, FLOW, true>(p, io, sm + q * S::STAGE, PP, &full[q], parity, x0, y0))
             return;
         __syncwarp();
         if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[q]);

@@ -222,3 +222,28 @@ def test_config4_batch_sampled_members(torch):
     for k in (0, 17, 63):
         assert lats[k].state() == alone_states(torch, [inst[k]], 20, stream)[0]
     b.close()
+
+
+@pytest.mark.parametrize("kernel", ["tile", "pipelined"])
+def test_batch_interior_tiles_of_uneven_members(torch, kernel):
+    """Members of different sizes with interior tiles (cells and ring at least two cells from every
+    edge, which take the kernels' interior path): a CTA must decide the path from its own member's
+    grid, whichever member an SM ran before.  Every member equals the lattice stepped alone."""
+    cases = []
+    for (nx, ny), st in (((256, 128), "fp32"), ((96, 64), "fp32"), ((160, 48), "fp32"), ((200, 72), "fp16"),
+                         ((128, 96), "fp16"), ((64, 40), "fp32")):
+        p, f = W.shear_drop(nx, ny, R=min(nx, ny) / 5)
+        cases.append((dict(p, storage=st), W.perturbed(p, f, seed=nx + ny)))
+    stream = torch.cuda.Stream()
+    ref = alone_states(torch, cases, 6, stream)
+    lats = make(torch, cases, stream)
+    b = lbm.Batch(lats, stream)
+    b.kernel = kernel
+    b.step(6)
+    torch.cuda.synchronize()
+    for k, g in enumerate(lats):
+        assert g.status == lbm.LBM_OK, k
+        assert g.state() == ref[k], k
+    b.close()
+    for g in lats:
+        g.close()
