@@ -542,7 +542,7 @@ def run_ours(args):
     if args.batch_steps > 0:
         for st in ("fp32", "fp16"):
             batch[st], bcells = batch_leg(torch, lbm, W, st, args.batch_steps,
-                                          alone_steps=100 if st == "fp32" else 0)
+                                          alone_steps=args.batch_alone_steps if st == "fp32" else 0)
         batch["workload"] = (f"64 seeded drops (seed 0), sizes uniform over 128^2, 256^2, 512x256, 1024x512 "
                              f"({bcells} cells), walls at +/-U with U ~ U[0, 0.02], linear EOS")
     clocks = sampler.stop() if sampler else None
@@ -652,6 +652,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the untimed storage-error leg")
     ap.add_argument("--batch-steps", type=int, default=1000, help="steps of the 64-lattice batch legs (0: skip)")
+    ap.add_argument("--batch-alone-steps", type=int, default=100,
+                    help="steps of each batch lattice run alone, one launch per lattice and step (0: skip)")
     ap.add_argument("--serving-requests", type=int, default=100,
                     help="requests of the seeded serving stream to replay (at most 200; 0: skip)")
     ap.add_argument("--serving-policies", default="fcfs", help="comma-separated: fcfs, shortest_first")

@@ -228,9 +228,9 @@ int lbm_destroy(lbm_handle* h);
  *   LBM_KERNEL_PIPELINED  persistent, warp-specialised CTAs (as many as fit on all SMs, at most
  *                         one per tile): a copy warp claims tiles and stages each with TMA into
  *                         one of two buffers while the compute warps work on the other;
- *   LBM_KERNEL_AUTO       (lbm_set_kernel only) the library's choice: TILE at uniform density,
- *                         PIPELINED for a density ratio != 1 (the faster ones on GB300 at
- *                         2048 x 1024 cells).
+ *   LBM_KERNEL_AUTO       (lbm_set_kernel only) the library's choice, the faster one on GB300
+ *                         at 2048 x 1024 cells: PIPELINED for 16-bit storage and for a density
+ *                         ratio != 1, TILE for FP32 storage at uniform density.
  * A new handle uses the library's choice.  LBM_EINVAL if the pipelined kernel does not fit. */
 #define LBM_KERNEL_AUTO 0
 #define LBM_KERNEL_TILE 1

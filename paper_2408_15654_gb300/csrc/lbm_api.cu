@@ -84,8 +84,14 @@ int encode_map(CUtensorMap* tm, void* base, int es, int nx, int ny, int planes, 
 
 // Opt the step-kernel instances of storage mode st into their shared memory; CTAs per SM of the
 // one-tile and of the pipelined kernels.
-int prepare_kernels(int st, int* blocks_per_sm, int* pipe_blocks_per_sm) {
-    cudaError_t e = lbm::prepare_step(st, blocks_per_sm, pipe_blocks_per_sm);
+// The kernel variant of a lattice's parameters (the EOS is unused with a prescribed velocity).
+lbm::Variant variant_of(const lbm_params& p, bool var_rho) {
+    const bool flow = p.velocity == LBM_VELOCITY_SOLVED;
+    return lbm::Variant{p.bc_y == LBM_BC_WALLS, flow && p.eos == LBM_EOS_LANGMUIR, flow, var_rho};
+}
+
+int prepare_kernels(int st, const lbm::Variant& v, int* blocks_per_sm, int* pipe_blocks_per_sm) {
+    cudaError_t e = lbm::prepare_step(st, v, blocks_per_sm, pipe_blocks_per_sm);
     if (e != cudaSuccess) return fail(LBM_ECUDA, "kernel setup: %s", cudaGetErrorString(e));
     if (*blocks_per_sm < 1) return fail(LBM_ECUDA, "the step kernel does not fit on an SM");
     return LBM_OK;
@@ -153,17 +159,17 @@ Layout layout_of(const lbm_params* p) {
     return L;
 }
 
-// Step kernel of a new handle: the warp-specialised persistent kernel with a density ratio != 1,
-// else the one-tile kernel.
-int default_kernel(int storage, bool var_rho, int pipe_blocks_per_sm) {
+// Step kernel of a new handle: the warp-specialised persistent kernel where it is faster (16-bit
+// storage, and any storage with a density ratio != 1), else the one-tile kernel.
+int default_kernel(int storage, const lbm::Variant& v, int pipe_blocks_per_sm) {
     // Measured on GB300 (us per step, one-tile / warp-specialised), sheared drop 2048 x 1024: FP32
-    // 72.8 / 73.6 (HBM-bound either way); two cells per thread in 32 x 8 tiles: FP16 52.1 / 64.2,
-    // BF16 52.9 / 64.7, FP16_FG 56.3 / 57.7, BF16_FG 56.3 / 58.6 (five 128-thread CTAs per SM hide
-    // the copy latency that the copy warp hid for the one-cell kernels); rising bubble 1024 x 2048
-    // (density ratio 10): FP32 83.9 / 79.8, FP16 64.9 / 59.0, whose larger cell update leaves room
-    // for fewer CTAs per SM, so the copy warp pays.
-    (void)storage;
-    if (var_rho && pipe_blocks_per_sm >= 1) return LBM_KERNEL_PIPELINED;
+    // 72.8 / 73.7 (HBM-bound either way); two cells per thread in 32 x 8 tiles: FP16 51.5 / 50.6,
+    // BF16 52.0 / 50.7, FP16_FG 55.8 / 54.9, BF16_FG 55.9 / 54.9 (one-tile kernel: five CTAs per
+    // SM; warp-specialised: four CTAs of four compute warps and a copy warp, which stages one tile
+    // ahead); prescribed velocity, the same grid: FP32 52.5 / 55.1, FP16 40.1 / 37.5; rising bubble
+    // 1024 x 2048 (density ratio 10): FP32 81.0 / 80.1, FP16 62.6 / 57.9.
+    if (pipe_blocks_per_sm < 1) return LBM_KERNEL_TILE;
+    if (v.var_rho || storage != LBM_STORE_FP32) return LBM_KERNEL_PIPELINED;
     return LBM_KERNEL_TILE;
 }
 
@@ -261,7 +267,6 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
     if (out)
         for (int k = 0; k < 5; ++k) a.io.out[k] = out[k];
     const dim3 grid(h->tiles_x, h->tiles_y);
-    const bool walls = h->prm.bc_y == LBM_BC_WALLS, lang = h->prm.eos == LBM_EOS_LANGMUIR;
     const int pipe = (mode == lbm::kStep && h->kernel == LBM_KERNEL_PIPELINED) ? h->pipe_ctas : 0;
     if (pipe) {
         // tile counters: launch s counts on counter s mod 2 and zeroes the other for launch s + 1;
@@ -272,9 +277,8 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
         a.tile_ctr_next = h->tile_ctr + ((h->steps + 1) & 1);
         h->last_pipe_step = h->steps;
     }
-    const bool flow = h->prm.velocity == LBM_VELOCITY_SOLVED;
-    const lbm::Variant v{walls, flow && lang, flow, h->phys.var_rho != 0};  // EOS unused if prescribed
-    cudaError_t e = lbm::launch_step(h->prm.storage, a, mode, v, grid, pipe, h->stream);
+    cudaError_t e = lbm::launch_step(h->prm.storage, a, mode, variant_of(h->prm, h->phys.var_rho != 0), grid, pipe,
+                                     h->stream);
     if (e != cudaSuccess) return fail(LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
@@ -453,7 +457,7 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
     h->last_pipe_step = -2;
     h->partials = reinterpret_cast<double*>(h->ws + L.off_partials);
     int bps = 0, bps_pipe = 0, sms = 0;
-    rc = prepare_kernels(p->storage, &bps, &bps_pipe);
+    rc = prepare_kernels(p->storage, variant_of(*p, h->phys.var_rho != 0), &bps, &bps_pipe);
     if (!rc && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, attr.device) != cudaSuccess)
         rc = fail(LBM_ECUDA, "cudaDeviceGetAttribute failed");
     const bool pair16 = lbm::pair_is_16bit(p->storage), h16 = lbm::h_is_16bit(p->storage);
@@ -485,7 +489,7 @@ int lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_
     {
         const long long ntiles = (long long)h->tiles_x * h->tiles_y, slots = (long long)bps_pipe * sms;
         h->pipe_ctas = (int)(ntiles < slots ? ntiles : slots);
-        h->kernel = default_kernel(p->storage, h->phys.var_rho != 0, bps_pipe);
+        h->kernel = default_kernel(p->storage, variant_of(*p, h->phys.var_rho != 0), bps_pipe);
     }
     cudaError_t e = cudaMemsetAsync(h->ws, 0, L.total, h->stream);
     if (e != cudaSuccess) {
@@ -693,9 +697,9 @@ int lbm_set_kernel(lbm_handle* h, int variant) {
     if (!h) return fail(LBM_EINVAL, "handle is NULL");
     if (variant == LBM_KERNEL_AUTO) {
         int bps = 0, bps_pipe = 0;
-        int rc = prepare_kernels(h->prm.storage, &bps, &bps_pipe);
+        int rc = prepare_kernels(h->prm.storage, variant_of(h->prm, h->phys.var_rho != 0), &bps, &bps_pipe);
         if (rc) return rc;
-        h->kernel = default_kernel(h->prm.storage, h->phys.var_rho != 0, bps_pipe);
+        h->kernel = default_kernel(h->prm.storage, variant_of(h->prm, h->phys.var_rho != 0), bps_pipe);
         return LBM_OK;
     }
     if (variant != LBM_KERNEL_TILE && variant != LBM_KERNEL_PIPELINED) return fail(LBM_EINVAL, "bad kernel variant");

@@ -42,6 +42,7 @@
 //   0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -400,19 +401,65 @@ template <int ST, int I, typename PV> __device__ __forceinline__ PV kenc(double 
     using T = Traits<ST>;
     return pvk<PV>((float)(c * T::SF / wgt_d(I)), (float)(c * T::SG / wgt_d(I)));
 }
-// (phi, psi) of a cell (or cell pair) from its nine stored pairs, converted to FP32 (r): FP32
-// storage sums the values; 16-bit storage sums the raw values of each weight class and scales
-// each class sum once
-template <int ST, typename PV> __device__ __forceinline__ PV pair_sum(const PV (&r)[9], PV ref) {
+
+// c + h for a 16-bit storage value h: h is widened exactly and the sum rounded once (one
+// mixed-precision add, no separate conversion)
+__device__ __forceinline__ float addh(float c, __half h) {
+    float d;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(h)), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float addh(float c, __nv_bfloat16 h) {
+    float d;
+    asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(h)), "f"(c));
+    return d;
+}
+__device__ __forceinline__ __half lo16(__half2 v) { return __low2half(v); }
+__device__ __forceinline__ __half hi16(__half2 v) { return __high2half(v); }
+__device__ __forceinline__ __nv_bfloat16 lo16(__nv_bfloat162 v) { return __low2bfloat16(v); }
+__device__ __forceinline__ __nv_bfloat16 hi16(__nv_bfloat162 v) { return __high2bfloat16(v); }
+// ((a + b) + c) + d in FP32 of the f (HI = false) or the g halves (HI = true) of four stored pairs
+template <bool HI, typename P> __device__ __forceinline__ float class_sum(P a, P b, P c, P d) {
+    if constexpr (HI) return addh(addh(addh(raw1(hi16(a)), hi16(b)), hi16(c)), hi16(d));
+    else return addh(addh(addh(raw1(lo16(a)), lo16(b)), lo16(c)), lo16(d));
+}
+// (phi, psi) of one cell from its nine stored pairs v[i] (link i): FP32 storage sums the values;
+// 16-bit storage sums the raw values of each weight class (links 1-4, links 5-8) and scales each
+// class sum, and link 0, once by its decode constant
+template <int ST> __device__ __forceinline__ float2 pair_sum1(const typename Traits<ST>::P (&v)[9], float2 ref) {
     if constexpr (!Traits<ST>::kPair16) {
-        PV s = ref;
+        float2 s = ref;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) s = vadd(s, r[i]);
+        for (int i = 0; i < 9; ++i) s = vadd(s, v[i]);
         return s;
     } else {
-        const PV ax = vadd(vadd(r[1], r[3]), vadd(r[2], r[4]));
-        const PV dg = vadd(vadd(r[5], r[7]), vadd(r[6], r[8]));
-        return vfma(dg, kdec<ST, 5, PV>(), vfma(ax, kdec<ST, 1, PV>(), vfma(r[0], kdec<ST, 0, PV>(), ref)));
+        const float2 ax = make_float2(class_sum<false>(v[1], v[3], v[2], v[4]), class_sum<true>(v[1], v[3], v[2], v[4]));
+        const float2 dg = make_float2(class_sum<false>(v[5], v[7], v[6], v[8]), class_sum<true>(v[5], v[7], v[6], v[8]));
+        return vfma(dg, kdec<ST, 5, float2>(),
+                    vfma(ax, kdec<ST, 1, float2>(), vfma(raw2(v[0]), kdec<ST, 0, float2>(), ref)));
+    }
+}
+// The same for the thread's cells, v[i][l] link i of cell l: the lanes of each (phi, psi) pair are
+// the cells, with the arithmetic of pair_sum1 per cell
+template <int ST>
+__device__ __forceinline__ typename CellT<cpt_of(ST)>::PV pair_sum(const typename Traits<ST>::P (&v)[9][cpt_of(ST)],
+                                                                   typename CellT<cpt_of(ST)>::PV ref) {
+    if constexpr (cpt_of(ST) == 1) {
+        float2 s = ref;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s = vadd(s, raw2(v[i][0]));
+        return s;
+    } else {
+        auto cls = [&](int a, int b, int c, int d, auto hi) {
+            return make_float2(class_sum<decltype(hi)::value>(v[a][0], v[b][0], v[c][0], v[d][0]),
+                               class_sum<decltype(hi)::value>(v[a][1], v[b][1], v[c][1], v[d][1]));
+        };
+        using F = std::false_type;
+        using T = std::true_type;
+        const PV2 ax{cls(1, 3, 2, 4, F{}), cls(1, 3, 2, 4, T{})}, dg{cls(5, 7, 6, 8, F{}), cls(5, 7, 6, 8, T{})};
+        const float2 a0 = raw2(v[0][0]), b0 = raw2(v[0][1]);
+        const PV2 r0{make_float2(a0.x, b0.x), make_float2(a0.y, b0.y)};
+        return vfma(dg, kdec<ST, 5, PV2>(), vfma(ax, kdec<ST, 1, PV2>(), vfma(r0, kdec<ST, 0, PV2>(), ref)));
     }
 }
 
@@ -590,30 +637,7 @@ __device__ __forceinline__ void collide_lanes(float2 q[9], float2 s, float2 sr, 
     }
 }
 
-// The (f, g) pairs of the thread's cells starting at src, in FP32 (16-bit storage: the raw scaled
-// deviations).  AL: the first cell sits at an even index, so two cells are one aligned load.
-template <int ST>
-__device__ __forceinline__ typename CellT<cpt_of(ST)>::PV ld_pairs(const typename Traits<ST>::P* src, bool AL) {
-    if constexpr (cpt_of(ST) == 1) {
-        return raw2(*src);
-    } else {
-        using P = typename Traits<ST>::P;
-        P v0, v1;
-        if (AL) {
-            const Two<P> w = *reinterpret_cast<const Two<P>*>(src);
-            v0 = w.v0;
-            v1 = w.v1;
-        } else {
-            v0 = src[0];
-            v1 = src[1];
-        }
-        const float2 f0 = raw2(v0), f1 = raw2(v1);
-        return PV2{make_float2(f0.x, f1.x), make_float2(f0.y, f1.y)};
-    }
-}
-
-// The stored values of the thread's cells at src (AL: one aligned vector load), and their (f, g)
-// pairs in FP32.
+// The stored (f, g) pairs of the thread's cells at src (AL: one aligned vector load).
 template <int ST>
 __device__ __forceinline__ void ld_raw(const typename Traits<ST>::P* src, bool AL, typename Traits<ST>::P (&v)[cpt_of(ST)]) {
     using P = typename Traits<ST>::P;
@@ -626,15 +650,6 @@ __device__ __forceinline__ void ld_raw(const typename Traits<ST>::P* src, bool A
     } else {
         v[0] = src[0];
         v[1] = src[1];
-    }
-}
-template <int ST>
-__device__ __forceinline__ typename CellT<cpt_of(ST)>::PV to_pv(const typename Traits<ST>::P (&v)[cpt_of(ST)]) {
-    if constexpr (cpt_of(ST) == 1) {
-        return raw2(v[0]);
-    } else {
-        const float2 f0 = raw2(v[0]), f1 = raw2(v[1]);
-        return PV2{make_float2(f0.x, f1.x), make_float2(f0.y, f1.y)};
     }
 }
 
@@ -815,14 +830,10 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     PV pp;  // (phi, psi)
     const P* pull = FG + ((EDGE && WALLS && y >= p.ny) ? p.ny - y0 : ty + 1) * G::BW + tx + 4;
     {
-        PV q[9];
+        P v[9][CPT];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            P v[CPT];
-            ld_raw<ST>(pull + i * SLOT - cx(i), cx(i) == 0, v);
-            q[i] = to_pv<ST>(v);
-        }
-        pp = pair_sum<ST>(q, ref);
+        for (int i = 0; i < 9; ++i) ld_raw<ST>(pull + i * SLOT - cx(i), cx(i) == 0, v[i]);
+        pp = pair_sum<ST>(v, ref);
         if constexpr (CPT == 1) PP[eo] = pp;
         else *reinterpret_cast<float4*>(PP + eo) = make_float4(pp.a.x, pp.b.x, pp.a.y, pp.b.y);
     }
@@ -839,10 +850,10 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
             else if (gy >= p.ny) row = p.ny - y0;
         }
         const P* base = FG + row * G::BW + ex + 3;
-        float2 r[9];
+        P r[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) r[i] = raw2(base[i * SLOT - cx(i)]);
-        PP[ey * G::EXP + ex + G::PPO] = pair_sum<ST>(r, make_float2(T::kPair16 ? p.phi_ref : 0.f, 0.f));
+        for (int i = 0; i < 9; ++i) r[i] = base[i * SLOT - cx(i)];
+        PP[ey * G::EXP + ex + G::PPO] = pair_sum1<ST>(r, make_float2(T::kPair16 ? p.phi_ref : 0.f, 0.f));
     }
     if (WS ? compute_sync_or<G::NT>(abort) : __syncthreads_or(abort)) {
         // a staging copy did not arrive in time: report it, wait (bounded) for it, store nothing
@@ -981,10 +992,10 @@ __device__ __forceinline__ bool step_tile(const Phys& p, const TileIO& io, unsig
     C uxp = ux, uyp = uy;
     if (!io.first) {
         const P* base = FG + (ty + 1) * G::BW + tx + 4;
-        PV r[9];
+        P v[9][CPT];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) r[i] = ld_pairs<ST>(base + i * SLOT + cy(i) * G::BW, true);
-        pprev = pair_sum<ST>(r, ref);
+        for (int i = 0; i < 9; ++i) ld_raw<ST>(base + i * SLOT + cy(i) * G::BW, true, v[i]);
+        pprev = pair_sum<ST>(v, ref);
         uxp = uox;
         uyp = uoy;
     }

@@ -92,10 +92,12 @@ cudaError_t launch_step_impl(const StepArgs& a, int mode, const Variant& v, dim3
 }
 
 // Opt every variant of storage mode ST into its dynamic shared memory; resident CTAs per SM of the
-// one-tile and of the pipelined kernels (the minimum over the variants).
+// one-tile kernels (the minimum over the variants) and of the pipelined kernel of variant `use`
+// (its register use differs between the variants: a minimum would hold every variant to the
+// density-ratio update's 128 registers).
 template <int ST>
-cudaError_t prepare_step_impl(int* blocks_per_sm, int* pipe_blocks_per_sm) {
-    int tile = 1 << 30, pipe = 1 << 30;
+cudaError_t prepare_step_impl(const Variant& use, int* blocks_per_sm, int* pipe_blocks_per_sm) {
+    int tile = 1 << 30, pipe = 0;
     auto one = [&]<bool W, bool L, int F>() -> cudaError_t {
         int b = 0;
         auto k0 = step_kernel<ST, W, L, kStep, F>;
@@ -109,12 +111,15 @@ cudaError_t prepare_step_impl(int* blocks_per_sm, int* pipe_blocks_per_sm) {
         tile = b < tile ? b : tile;
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1, GeoOf<ST>::NT, Smem<ST>::BYTES);
         tile = b < tile ? b : tile;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kp, nt_pipe<ST>(), Smem<ST>::BYTES_PIPE);
-        pipe = b < pipe ? b : pipe;
         return e;
     };
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < kVariants && e == cudaSuccess; ++k) e = dispatch_variant(variant_of(k), one);
+    if (e == cudaSuccess)
+        e = dispatch_variant(use, [&]<bool W, bool L, int F>() {
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pipe, pipe_kernel<ST, W, L, F>(), nt_pipe<ST>(),
+                                                                 Smem<ST>::BYTES_PIPE);
+        });
     *blocks_per_sm = tile;
     *pipe_blocks_per_sm = pipe;
     return e;
@@ -162,14 +167,14 @@ cudaError_t prepare_batch_impl(int* ws_blocks_per_sm) {
 
 // Entry points of the per-storage translation units; st is the storage mode.
 cudaError_t launch_step(int st, const StepArgs& a, int mode, const Variant& v, dim3 grid, int pipe, cudaStream_t s);
-cudaError_t prepare_step(int st, int* blocks_per_sm, int* pipe_blocks_per_sm);
+cudaError_t prepare_step(int st, const Variant& v, int* blocks_per_sm, int* pipe_blocks_per_sm);
 cudaError_t launch_batch(int st, const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t s);
 cudaError_t prepare_batch(int st, int* ws_blocks_per_sm);
 
 #define LBM_DECLARE_STORAGE(name)                                                                                  \
     cudaError_t launch_step_##name(const StepArgs& a, int mode, const Variant& v, dim3 grid, int pipe,              \
                                    cudaStream_t s);                                                                \
-    cudaError_t prepare_step_##name(int* blocks_per_sm, int* pipe_blocks_per_sm);                                   \
+    cudaError_t prepare_step_##name(const Variant& v, int* blocks_per_sm, int* pipe_blocks_per_sm);                 \
     cudaError_t launch_batch_##name(const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t s);         \
     cudaError_t prepare_batch_##name(int* ws_blocks_per_sm);
 LBM_DECLARE_STORAGE(fp32)
@@ -185,8 +190,8 @@ LBM_DECLARE_STORAGE(bf16fg)
                                    cudaStream_t s) {                                                               \
         return launch_step_impl<ST>(a, mode, v, grid, pipe, s);                                                   \
     }                                                                                                              \
-    cudaError_t prepare_step_##name(int* blocks_per_sm, int* pipe_blocks_per_sm) {                                  \
-        return prepare_step_impl<ST>(blocks_per_sm, pipe_blocks_per_sm);                                          \
+    cudaError_t prepare_step_##name(const Variant& v, int* blocks_per_sm, int* pipe_blocks_per_sm) {                \
+        return prepare_step_impl<ST>(v, blocks_per_sm, pipe_blocks_per_sm);                                       \
     }                                                                                                              \
     cudaError_t launch_batch_##name(const BatchArgs& b, const Variant& v, unsigned ntiles, cudaStream_t s) {        \
         return launch_batch_impl<ST>(b, v, ntiles, s);                                                            \

@@ -16,13 +16,13 @@ cudaError_t launch_step(int st, const StepArgs& a, int mode, const Variant& v, d
     }
 }
 
-cudaError_t prepare_step(int st, int* blocks_per_sm, int* pipe_blocks_per_sm) {
+cudaError_t prepare_step(int st, const Variant& v, int* blocks_per_sm, int* pipe_blocks_per_sm) {
     switch (st) {
-        case kFP16: return prepare_step_fp16(blocks_per_sm, pipe_blocks_per_sm);
-        case kBF16: return prepare_step_bf16(blocks_per_sm, pipe_blocks_per_sm);
-        case kFP16FG: return prepare_step_fp16fg(blocks_per_sm, pipe_blocks_per_sm);
-        case kBF16FG: return prepare_step_bf16fg(blocks_per_sm, pipe_blocks_per_sm);
-        default: return prepare_step_fp32(blocks_per_sm, pipe_blocks_per_sm);
+        case kFP16: return prepare_step_fp16(v, blocks_per_sm, pipe_blocks_per_sm);
+        case kBF16: return prepare_step_bf16(v, blocks_per_sm, pipe_blocks_per_sm);
+        case kFP16FG: return prepare_step_fp16fg(v, blocks_per_sm, pipe_blocks_per_sm);
+        case kBF16FG: return prepare_step_bf16fg(v, blocks_per_sm, pipe_blocks_per_sm);
+        default: return prepare_step_fp32(v, blocks_per_sm, pipe_blocks_per_sm);
     }
 }
 

@@ -89,9 +89,16 @@ def test_default_kernel_per_storage(torch):
         g.kernel = "auto"
         assert g.kernel == got[st]
         g.close()
-    # at uniform density the one-tile kernel in every storage mode: FP32 is bandwidth-bound either
-    # way, and the 16-bit modes' two-cell tiles run six CTAs per SM
-    assert got == {"fp32": "tile", "fp16": "tile", "bf16": "tile", "fp16_fg": "tile", "bf16_fg": "tile"}
+    # at uniform density: FP32 is bandwidth-bound either way and keeps the one-tile kernel; the
+    # 16-bit modes take the warp-specialised kernel, which stages one tile ahead
+    assert got == {"fp32": "tile", "fp16": "pipelined", "bf16": "pipelined", "fp16_fg": "pipelined",
+                   "bf16_fg": "pipelined"}
+    # with a prescribed velocity (no flow populations) the same choice
+    p, f = W.convected_drop(64, 64, R=10.0)
+    for st, kn in (("fp32", "tile"), ("fp16", "pipelined"), ("bf16_fg", "pipelined")):
+        g = lbm.Lattice(dict(p, storage=st))
+        assert g.kernel == kn, st
+        g.close()
     # a density ratio != 1 takes the warp-specialised kernel in every storage mode
     p, f = W.rising_bubble(8.0)
     for st in ("fp32", "fp16", "bf16_fg"):
