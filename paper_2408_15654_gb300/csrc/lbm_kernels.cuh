@@ -1408,15 +1408,21 @@ __device__ __forceinline__ bool step_tile_any(const Phys& p, const TileIO& io, u
     return step_tile<ST, WALLS, LANGMUIR, MODE, FLOW, WS, true>(p, io, sm, PP, mbar, parity, x0, y0);
 }
 
-// Resident CTAs per SM that the one-tile kernels (step_kernel, batch_step_kernel) are compiled for.
-// FP32 storage: four; with a prescribed velocity (no h) the cell update fits 48 registers without
-// spills and the boxes 33 KB, so five (convection test 2048 x 1024: 54.3 -> 52.5 us per step).
-// Two cells per thread (128-thread CTAs): five, at 96 registers (FP16 at 2048 x 1024: 51.8 us,
-// against 52.7 at six CTAs and 80 registers, where the interior path spills); the density-ratio
-// update needs more, so four (128 registers).
+// Resident CTAs per SM that the one-tile kernels (step_kernel, and batch_step_kernel but for the
+// case below) are compiled for.  FP32 storage: four; with a prescribed velocity (no h) the cell
+// update fits 48 registers without spills and the boxes 33 KB, so five (convection test
+// 2048 x 1024: 54.3 -> 52.5 us per step).  Two cells per thread (128-thread CTAs): five, at 96
+// registers (FP16 at 2048 x 1024: 51.5 us, against 52.3 at six CTAs and 80 registers, where the
+// interior path spills); the density-ratio update needs more, so four (128 registers).
 template <int ST>
 __host__ __device__ constexpr int tile_min_blocks(int flow) {
     return cpt_of(ST) == 2 ? (flow == kFlowVarRho ? 4 : 5) : (flow == kFlowPrescribed ? 5 : 4);
+}
+// The per-tile batch kernel reads the lattice's constants from shared memory, which takes more
+// registers: with FP32 storage and a prescribed velocity, five CTAs per SM would spill 128 B, so four.
+template <int ST>
+__host__ __device__ constexpr int batch_min_blocks(int flow) {
+    return cpt_of(ST) == 1 && flow == kFlowPrescribed ? 4 : tile_min_blocks<ST>(flow);
 }
 template <int ST, bool WALLS, bool LANGMUIR, int MODE, int FLOW>
 __global__ void __launch_bounds__(GeoOf<ST>::NT, tile_min_blocks<ST>(FLOW)) step_kernel(const __grid_constant__ StepArgs a) {
@@ -1601,7 +1607,7 @@ __device__ __forceinline__ void flag_batch_timeout(const BatchArgs& b) {
 }
 
 template <int ST, bool WALLS, bool LANGMUIR, int FLOW>
-__global__ void __launch_bounds__(GeoOf<ST>::NT, tile_min_blocks<ST>(FLOW)) batch_step_kernel(const __grid_constant__ BatchArgs b) {
+__global__ void __launch_bounds__(GeoOf<ST>::NT, batch_min_blocks<ST>(FLOW)) batch_step_kernel(const __grid_constant__ BatchArgs b) {
     using S = Smem<ST>;
     using G = GeoOf<ST>;
     extern __shared__ __align__(1024) unsigned char sm[];
