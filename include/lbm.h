@@ -164,8 +164,10 @@ int lbm_get_moments(lbm_handle* h, unsigned mask, double* const out[5], int mem)
 
 /* Sum over the grid of phi (LBM_SUM_PHI) or psi (LBM_SUM_PSI) in FP64: each cell's populations
  * are summed in FP64 by warp shuffles, then blocks, then one final block (deterministic order).
- * Both sums are conserved by the method (sum F_i = sum G_i = 0).  *out is host memory.
- * Synchronous. */
+ * Both sums are conserved by the method (sum F_i = sum G_i = 0).  Before the first step after
+ * lbm_init_fields the populations are staged where the first step pulls them (next to a wall, in
+ * the wall's ghost row), and the sum is taken over the values each cell pulls; afterwards over
+ * each cell's own post-collision values.  *out is host memory.  Synchronous. */
 int lbm_reduce(lbm_handle* h, int what, double* out);
 
 /* Failure-detection self-test.  Launches one warp on cuda_stream that waits, with the bounded
@@ -184,8 +186,10 @@ int lbm_selftest_wait(unsigned* d_word, void* cuda_stream);
  * workspace of lbm_create, but it may hold a population buffer in this library's layout (see
  * lbm_workspace_bytes), e.g. the current buffer of another component's handle or a checkpoint
  * already in device memory.  This call sums phi (LBM_SUM_PHI) or psi (LBM_SUM_PSI) of that buffer
- * in FP64 exactly like lbm_reduce, with its partial sums in a fixed device array compiled into the
- * library instead of a workspace.
+ * in FP64 exactly like lbm_reduce does once a step has been taken (each cell's own slots), with its
+ * partial sums in a fixed device array compiled into the library instead of a workspace.  A buffer
+ * that lbm_init_fields has just filled holds, next to a wall, some values in the wall's ghost rows
+ * (staged for the first pull), so its own slots give the total only after a step.
  *   d_pops: device pointer to one FP32-storage population buffer of an nx x ny grid, in the
  *           layout of lbm_workspace_bytes (read only).
  *   out:    host memory, receives the sum.

@@ -285,20 +285,20 @@ int launch_step(lbm_handle* h, int mode, double* const out[5]) {
 
 // FP64 sum of phi (lane 0) or psi (lane 1) of a population buffer into partials[0..blocks),
 // then partials[blocks] ... written to *dres.
-int launch_reduce(int st, const void* pops, int lane, int nx, int ny, int pitch, size_t plane, long long org,
+int launch_reduce(int st, const void* pops, int lane, bool pulled, int nx, int ny, int pitch, size_t plane, long long org,
                   const lbm::Phys& ph,
                   int blocks, double* partials, double* dres, cudaStream_t stream) {
     // the pair planes of the FG modes are stored like those of the all-16-bit modes
     const long long pl = (long long)plane;
     if (st == LBM_STORE_FP16 || st == LBM_STORE_FP16_FG)
-        lbm::reduce_partial_kernel<lbm::kFP16><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch, pl,
-                                                                                           org, ph, partials);
+        lbm::reduce_partial_kernel<lbm::kFP16><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, pulled, nx, ny,
+                                                                                           pitch, pl, org, ph, partials);
     else if (st == LBM_STORE_BF16 || st == LBM_STORE_BF16_FG)
-        lbm::reduce_partial_kernel<lbm::kBF16><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch, pl,
-                                                                                           org, ph, partials);
+        lbm::reduce_partial_kernel<lbm::kBF16><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, pulled, nx, ny,
+                                                                                           pitch, pl, org, ph, partials);
     else
-        lbm::reduce_partial_kernel<lbm::kFP32><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, nx, ny, pitch, pl,
-                                                                                           org, ph, partials);
+        lbm::reduce_partial_kernel<lbm::kFP32><<<blocks, lbm::kReduceThreads, 0, stream>>>(pops, lane, pulled, nx, ny,
+                                                                                           pitch, pl, org, ph, partials);
     LBM_CUDA(cudaGetLastError());
     lbm::reduce_final_kernel<<<1, lbm::kReduceThreads, 0, stream>>>(partials, blocks, dres);
     LBM_CUDA(cudaGetLastError());
@@ -407,7 +407,7 @@ int lbm_reduce_noalloc(const void* d_pops, int nx, int ny, int what, void* cuda_
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     lbm::Phys ph;
     std::memset(&ph, 0, sizeof(ph));
-    rc = launch_reduce(LBM_STORE_FP32, d_pops, what == LBM_SUM_PSI ? 1 : 0, nx, ny, pitch, plane, org, ph, ny,
+    rc = launch_reduce(LBM_STORE_FP32, d_pops, what == LBM_SUM_PSI ? 1 : 0, false, nx, ny, pitch, plane, org, ph, ny,
                        scratch, scratch + LBM_NOALLOC_MAX_ROWS, stream);
     if (rc) return rc;
     LBM_CUDA(cudaMemcpyAsync(out, scratch + LBM_NOALLOC_MAX_ROWS, sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -603,8 +603,9 @@ int lbm_reduce(lbm_handle* h, int what, double* out) {
     if (!out) return fail(LBM_EINVAL, "out is NULL");
     const int blocks = h->prm.ny < lbm::kMaxPartials ? h->prm.ny : lbm::kMaxPartials;
     double* dres = h->partials + lbm::kMaxPartials;
-    int rc = launch_reduce(h->prm.storage, h->pops[h->cur], what == LBM_SUM_PSI ? 1 : 0, h->prm.nx, h->prm.ny,
-                           h->L.pitch, h->L.plane, h->phys.org, h->phys, blocks, h->partials, dres, h->stream);
+    // before the first step the buffer is staged for the first pull (see reduce_partial_kernel)
+    int rc = launch_reduce(h->prm.storage, h->pops[h->cur], what == LBM_SUM_PSI ? 1 : 0, h->first != 0, h->prm.nx,
+                           h->prm.ny, h->L.pitch, h->L.plane, h->phys.org, h->phys, blocks, h->partials, dres, h->stream);
     if (rc) return rc;
     LBM_CUDA(cudaMemcpyAsync(out, dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     unsigned st = 0;

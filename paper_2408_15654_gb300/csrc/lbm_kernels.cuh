@@ -1890,8 +1890,11 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
     }
 }
 
-// ---- FP64 sums of phi or psi: every population slot is pulled exactly once per step, so the
-// total of a field is the plain sum of one lane of the 9 pair planes over the valid cells ----
+// ---- FP64 sums of phi or psi.  After a step every cell holds its nine post-collision values in
+// its own slots, so the total of a field is the plain sum of one lane of the 9 pair planes over
+// the cells.  Before the first step the buffer holds what lbm_init_fields staged for the first
+// pull (each cell's equilibrium value of link i at x - c_i, in the wall's ghost row where that
+// lies beyond a wall): the sum is then taken over the values each cell pulls ----
 constexpr int kReduceThreads = 256;
 constexpr int kMaxPartials = 1024;
 
@@ -1910,10 +1913,12 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
     return v;
 }
 
-// lane 0 sums f (phi), lane 1 sums g (psi); 16-bit storage is decoded to its value first
+// lane 0 sums f (phi), lane 1 sums g (psi); 16-bit storage is decoded to its value first;
+// pulled: sum the values at x - c_i (the state before the first step) instead of the own slots
 template <int ST>
 __global__ void __launch_bounds__(kReduceThreads) reduce_partial_kernel(const void* __restrict__ pops, int lane,
-                                                                        int nx, int ny, int pitch, long long plane,
+                                                                        int pulled, int nx, int ny, int pitch,
+                                                                        long long plane,
                                                                         long long org, Phys p,
                                                                         double* __restrict__ partials) {
     using T = Traits<ST>;
@@ -1927,7 +1932,8 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_partial_kernel(const vo
     for (int y = blockIdx.x; y < ny; y += gridDim.x) {
         for (long long k = threadIdx.x; k < nk; k += blockDim.x) {
             const int i = (int)(k / nx), x = (int)(k - (long long)i * nx);
-            const float2 v = raw2(pairs[(size_t)i * plane + (size_t)(org + (long long)y * pitch + x)]);
+            const int sx = pulled ? x - cx(i) : x, sy = pulled ? y - cy(i) : y;
+            const float2 v = raw2(pairs[(size_t)i * plane + (size_t)(org + (long long)sy * pitch + sx)]);
             if constexpr (!T::kPair16) {
                 acc += (double)(lane ? v.y : v.x);
             } else {

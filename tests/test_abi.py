@@ -103,3 +103,22 @@ def test_density_ratio_workspace_has_a_mass_flux_history():
     uni = lbm.lbm_workspace_bytes(lbm.make_params(dict(p, rhoB=p["rhoA"])))
     pitch, rows = (64 + 10 + 31) // 32 * 32, 128 + 4
     assert var - uni == 2 * ((pitch * rows * 8 + 255) // 256 * 256)
+
+
+@pytest.mark.parametrize("storage,pair_bytes", [("fp32", 104), ("fp16", 52), ("bf16_fg", 68)])
+def test_grid_size_limits(storage, pair_bytes):
+    """The smallest grid (2 x 2) and grids of exactly 2^30 cells are accepted, with at least the two
+    population buffers in the workspace (the size query allocates nothing); one cell row or column
+    beyond 2^30 cells, or a dimension below 2, is rejected."""
+    lib = lbm.load()
+    n = C.c_size_t()
+    for nx, ny, ok in ((2, 2, True), (1 << 15, 1 << 15, True), (2, 1 << 29, True), (1 << 29, 2, True),
+                       (1 << 15, (1 << 15) + 1, False), ((1 << 29) + 1, 2, False), (2, 1, False), (1, 2, False)):
+        p, _ = W.stationary_drop(8, 8, R=2)
+        p.update(nx=nx, ny=ny, storage=storage)
+        rc = lib.lbm_workspace_bytes(C.byref(lbm.make_params(p)), C.byref(n))
+        assert (rc == lbm.LBM_OK) == ok, (nx, ny, rc)
+        if ok:
+            assert n.value >= 2 * pair_bytes * nx * ny, (nx, ny, n.value)
+        else:
+            assert lbm.lbm_last_error()

@@ -105,3 +105,64 @@ def test_default_kernel_per_storage(torch):
         g = lbm.Lattice(dict(p, storage=st))
         assert g.kernel == "pipelined", st
         g.close()
+
+
+def smallest_grids():
+    """The smallest grids the library accepts (nx = ny = 2, or two fluid rows between walls), and a
+    width of three: every cell is an edge cell and writes its periodic images or wall ghosts on
+    several sides, and one tile covers the grid many times over."""
+    p, f = W.stationary_drop(2, 2, R=0.6)
+    yield "periodic_2x2", p, W.perturbed(p, f, seed=11)
+    p, f = W.shear_drop(2, 2, R=0.6)
+    yield "walls_2x2", p, W.perturbed(p, f, seed=12)
+    p, f = W.shear_drop(3, 2, R=0.6)
+    yield "walls_3x2", p, W.perturbed(p, f, seed=13)
+    p, f = W.convected_drop(2, 3, R=0.6)
+    yield "prescribed_2x3", p, f
+
+
+@pytest.mark.parametrize("kernel", ["tile", "pipelined"])
+def test_smallest_grids_match_oracle(torch, kernel):
+    """FP32 storage on the smallest grids against the FP64 oracle after 100 steps (the FP32 parity
+    bound of the larger cases), through both kernels.  The unit normal is taken only where
+    |grad phi| > 1e-4, as in the other long parity runs: on the 2 x 2 channel the gradients are of
+    rounding size, and with the default threshold the oracle's own u moves by up to 1.5e-6 when its
+    inputs are perturbed at FP32 rounding size (6e-8 relative), against 2e-10 with this one."""
+    import numpy as np
+    import oracle
+    for name, p, f in smallest_grids():
+        p = dict(p, n_eps=1e-4)
+        g = lbm.Lattice(p)
+        g.kernel = kernel
+        g.init(**f)
+        g.step(100)
+        torch.cuda.synchronize()
+        assert g.status == lbm.LBM_OK, name
+        gm = g.moments()
+        g.close()
+        o = oracle.Sim(p)
+        o.init(**f)
+        o.step(100)
+        om = o.moments()
+        for k in ("phi", "psi"):
+            err = np.linalg.norm(gm[k] - om[k]) / np.linalg.norm(om[k])
+            assert err <= 1e-5, (name, k, err)
+        du = np.hypot(gm["ux"] - om["ux"], gm["uy"] - om["uy"]).max()
+        assert du <= 1e-5 * max(np.hypot(om["ux"], om["uy"]).max(), 1e-3), (name, du)
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16_fg"])
+def test_smallest_grids_16bit_kernels_agree(torch, storage):
+    """16-bit storage on the smallest grids: both kernels give the same state bit for bit, the run
+    stays stable, and the total of phi moves only by the stochastic rounding's random walk."""
+    for name, p, f in smallest_grids():
+        q = dict(p, storage=storage)
+        assert run(torch, q, f, "tile", 50) == run(torch, q, f, "pipelined", 50), name
+        g = lbm.Lattice(q)
+        g.init(**f)
+        t0 = g.total("phi")
+        g.step(50)
+        torch.cuda.synchronize()
+        assert g.status == lbm.LBM_OK, name
+        assert abs(g.total("phi") - t0) <= 1e-2 * abs(t0), name
+        g.close()

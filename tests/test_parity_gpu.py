@@ -167,6 +167,25 @@ def test_reduction_matches_oracle_totals():
         assert g.total(what) == pytest.approx(o.total(what), rel=1e-6)
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16_fg"])
+def test_totals_right_after_init_and_after_a_step(storage):
+    """Before the first step the populations are staged where the first step pulls them, some of
+    them (next to the walls) in the ghost rows: lbm_reduce then sums the pulled values, and the
+    totals equal the sums of the input fields (to the storage's rounding); one step keeps them."""
+    p, f = W.shear_drop(45, 19, R=6)
+    f = W.perturbed(p, f, seed=9)
+    g = lbm.Lattice(dict(p, storage=storage))
+    g.init(**f)
+    tol = 2e-7 if storage == "fp32" else 2e-3
+    ref = {what: float(np.sum(f[what])) for what in ("phi", "psi")}
+    for what in ("phi", "psi"):
+        assert g.total(what) == pytest.approx(ref[what], rel=tol), what
+    g.step(1)
+    for what in ("phi", "psi"):
+        assert g.total(what) == pytest.approx(ref[what], rel=tol), what
+    g.close()
+
+
 def test_checkpoint_restart_is_bitwise():
     """n steps, a checkpoint, n more steps equals 2n steps bit for bit (no atomics in the step)."""
     p, f = W.shear_drop(80, 48, R=9)
