@@ -213,8 +213,9 @@ int lbm_status(lbm_handle* h);
 
 /* Checkpoint: the populations, the velocity history and the step bookkeeping, as an opaque
  * blob of lbm_state_bytes bytes in host memory.  lbm_set_state restores a blob taken from a
- * handle with identical parameters.  Both synchronous.  n steps, a checkpoint, then n more
- * steps give bitwise the same state as 2n steps. */
+ * handle with identical parameters; a blob of another grid, storage mode, velocity mode or density
+ * mode returns LBM_EINVAL.  Both synchronous.  n steps, a checkpoint, then n more steps give
+ * bitwise the same state as 2n steps. */
 int lbm_state_bytes(const lbm_handle* h, size_t* bytes);
 int lbm_get_state(lbm_handle* h, void* host_blob, size_t bytes);
 int lbm_set_state(lbm_handle* h, const void* host_blob, size_t bytes);

@@ -143,7 +143,12 @@ Layout layout_of(const lbm_params* p) {
     Layout L;
     long long org = 0;
     frame_of(p->nx, p->ny, &L.pitch, &L.plane, &org);
-    L.pops_bytes = align_up(L.plane * (size_t)lbm::pop_bytes_per_cell(p->storage, p->velocity == LBM_VELOCITY_SOLVED));
+    // a population buffer also stages, while it is not the current one, the five FP64 fields that
+    // lbm_init_fields and lbm_get_moments move through host memory: 40 bytes per cell, more than
+    // the 36 of 16-bit storage with a prescribed velocity
+    const size_t pops = L.plane * (size_t)lbm::pop_bytes_per_cell(p->storage, p->velocity == LBM_VELOCITY_SOLVED);
+    const size_t stage = (size_t)p->nx * (size_t)p->ny * 5 * sizeof(double);
+    L.pops_bytes = align_up(pops > stage ? pops : stage);
     size_t off = 0;
     L.off_pops[0] = off; off += L.pops_bytes;
     L.off_pops[1] = off; off += L.pops_bytes;
@@ -510,8 +515,7 @@ int lbm_init_fields(lbm_handle* h, const double* phi, const double* psi, const d
     const double* d[5] = {phi, psi, ux, uy, P};
     const int tgt = 0;
     if (mem == LBM_MEM_HOST) {
-        // stage through the buffer that becomes dead (5 doubles per cell fit in a buffer's
-        // 104, 68 or 52 bytes per cell)
+        // stage through the buffer that becomes dead (sized for 5 doubles per cell, see layout_of)
         double* stage = reinterpret_cast<double*>(h->pops[tgt ^ 1]);
         for (int k = 0; k < 5; ++k) {
             LBM_CUDA(cudaMemcpyAsync(stage + k * n, d[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -629,10 +633,11 @@ struct StateHeader {
     uint64_t magic;
     int32_t nx, ny, pitch, first;
     int64_t steps;
+    int32_t storage, velocity, var_rho, pad;  // what the population buffer's bytes mean
 };
-// Names the population layout of the blob ("LBM3STAT": h stored in link pairs); blobs written with
-// another layout are refused by lbm_set_state.
-static const uint64_t kStateMagic = 0x4c424d3353544154ull;  // "LBM3STAT"
+// Names the population layout of the blob ("LBM4STAT": h stored in link pairs, the storage and
+// flow modes in the header); blobs written with another layout are refused by lbm_set_state.
+static const uint64_t kStateMagic = 0x4c424d3453544154ull;  // "LBM4STAT"
 
 int lbm_state_bytes(const lbm_handle* h, size_t* bytes) {
     g_err.clear();
@@ -650,7 +655,8 @@ int lbm_get_state(lbm_handle* h, void* host_blob, size_t bytes) {
     size_t need = 0;
     lbm_state_bytes(h, &need);
     if (bytes < need) return fail(LBM_EINVAL, "blob of %zu bytes < %zu needed", bytes, need);
-    StateHeader hd{kStateMagic, h->prm.nx, h->prm.ny, h->L.pitch, h->first, h->steps};
+    StateHeader hd{kStateMagic, h->prm.nx, h->prm.ny, h->L.pitch, h->first, h->steps,
+                   h->prm.storage, h->prm.velocity, h->phys.var_rho, 0};
     char* b = static_cast<char*>(host_blob);
     std::memcpy(b, &hd, sizeof(hd));
     const size_t pb = h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage, h->prm.velocity == LBM_VELOCITY_SOLVED);
@@ -675,6 +681,8 @@ int lbm_set_state(lbm_handle* h, const void* host_blob, size_t bytes) {
     std::memcpy(&hd, b, sizeof(hd));
     if (hd.magic != kStateMagic || hd.nx != h->prm.nx || hd.ny != h->prm.ny || hd.pitch != h->L.pitch)
         return fail(LBM_EINVAL, "state blob does not match this handle");
+    if (hd.storage != h->prm.storage || hd.velocity != h->prm.velocity || hd.var_rho != h->phys.var_rho)
+        return fail(LBM_EINVAL, "state blob has another storage, velocity or density mode than this handle");
     const size_t pb = h->L.plane * (size_t)lbm::pop_bytes_per_cell(h->prm.storage, h->prm.velocity == LBM_VELOCITY_SOLVED);
     const int cur = (int)(hd.steps & 1);  // the current state after k steps is buffer k mod 2
     LBM_CUDA(cudaMemcpyAsync(h->pops[cur], b + sizeof(hd), pb, cudaMemcpyHostToDevice, h->stream));

@@ -122,3 +122,17 @@ def test_grid_size_limits(storage, pair_bytes):
             assert n.value >= 2 * pair_bytes * nx * ny, (nx, ny, n.value)
         else:
             assert lbm.lbm_last_error()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16", "fp16_fg"])
+def test_population_buffers_hold_the_staged_fields(storage):
+    """Each population buffer also stages the five FP64 fields of lbm_init_fields and
+    lbm_get_moments (40 bytes per cell), also where 16-bit storage with a prescribed velocity needs
+    fewer bytes for its populations."""
+    lib = lbm.load()
+    n = C.c_size_t()
+    for nx, ny in ((512, 512), (2048, 1024), (100, 100)):
+        p, _ = W.convected_drop(nx, ny, R=nx / 8)
+        p["storage"] = storage
+        assert lib.lbm_workspace_bytes(C.byref(lbm.make_params(p)), C.byref(n)) == lbm.LBM_OK
+        assert n.value >= 2 * 40 * nx * ny + 2 * 8 * nx * ny, (nx, ny, n.value)

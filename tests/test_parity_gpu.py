@@ -202,6 +202,23 @@ def test_checkpoint_restart_is_bitwise():
     assert a.state() == b.state()
 
 
+def test_checkpoint_of_another_mode_is_refused():
+    """A blob restores only into a handle whose grid, storage, velocity and density modes match."""
+    p, f = W.shear_drop(40, 24, R=6)
+    a = lbm.Lattice(p)
+    a.init(**f)
+    a.step(2)
+    blob = a.state()
+    for other in (dict(p, storage="fp16"), dict(p, storage="bf16_fg"), dict(p, velocity="prescribed"),
+                  dict(p, rhoA=2.0), dict(p, nx=41)):
+        b = lbm.Lattice(other)
+        b.init(**W.fields(np.zeros((other["ny"], other["nx"])), 0.0))
+        with pytest.raises(lbm.LBMError):
+            b.restore(blob + bytes(1 << 16))  # long enough for any of them: the header decides
+        b.close()
+    a.close()
+
+
 def test_first_moments_reproduce_the_initial_fields():
     """Right after initialisation (no force) the populations are equilibria of the input fields."""
     p, f = W.shear_drop(40, 24, R=6)
