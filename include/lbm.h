@@ -106,9 +106,11 @@ typedef struct lbm_handle lbm_handle;
 
 /* Bytes of device workspace lbm_create needs for these parameters: two population buffers, two
  * velocity-history buffers, a status word and the reduction partials.  Returns LBM_EINVAL for bad
- * parameters.
- * Layout: the workspace starts with the two population buffers, each B * (ny + 4) * pitch bytes
- * rounded up to a multiple of 256, with pitch = nx + 10 rounded up to a multiple of 32 and
+ * parameters (among them a grid outside nx, ny >= 2, nx * ny <= 2^30, ny <= 524280).
+ * Layout: the workspace starts with the two population buffers, each the larger of
+ * B * (ny + 4) * pitch and 40 * nx * ny bytes (a buffer that is not current stages the five FP64
+ * fields of host transfers) rounded up to a multiple of 256, with pitch = nx + 10 rounded up to a
+ * multiple of 32 and
  * B = 104 (FP32 storage), 52 (FP16, BF16) or 68 (FP16_FG, BF16_FG); with
  * LBM_VELOCITY_PRESCRIBED, 72 (FP32) or 36 (16-bit).  A buffer holds 9 planes of (f_i, g_i)
  * pairs followed by 4 planes of (h_1, h_2), (h_3, h_4), (h_5, h_6), (h_7, h_8) pairs (h_0 never

@@ -103,6 +103,9 @@ int validate(const lbm_params* p) {
     if (!p) return fail(LBM_EINVAL, "params is NULL");
     if (p->nx < 2 || p->ny < 2) return fail(LBM_EINVAL, "nx and ny must be >= 2 (got %d x %d)", p->nx, p->ny);
     if ((long long)p->nx * p->ny > (1LL << 30)) return fail(LBM_EINVAL, "grid too large");
+    // the one-tile, moments and initialisation kernels run one CTA row per 8 cell rows, and a
+    // launch has at most 65535 rows of CTAs
+    if (p->ny > 65535 * 8) return fail(LBM_EINVAL, "ny = %d exceeds 524280 rows", p->ny);
     if (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_WALLS) return fail(LBM_EINVAL, "bad bc_y");
     if (p->eos != LBM_EOS_LINEAR && p->eos != LBM_EOS_LANGMUIR) return fail(LBM_EINVAL, "bad eos");
     if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16_FG)

@@ -109,10 +109,12 @@ def test_density_ratio_workspace_has_a_mass_flux_history():
 def test_grid_size_limits(storage, pair_bytes):
     """The smallest grid (2 x 2) and grids of exactly 2^30 cells are accepted, with at least the two
     population buffers in the workspace (the size query allocates nothing); one cell row or column
-    beyond 2^30 cells, or a dimension below 2, is rejected."""
+    beyond 2^30 cells, more than 524280 rows (65535 rows of 8-row tiles), or a dimension below 2,
+    is rejected."""
     lib = lbm.load()
     n = C.c_size_t()
-    for nx, ny, ok in ((2, 2, True), (1 << 15, 1 << 15, True), (2, 1 << 29, True), (1 << 29, 2, True),
+    for nx, ny, ok in ((2, 2, True), (1 << 15, 1 << 15, True), (1 << 12, 1 << 18, True), (1 << 29, 2, True),
+                       (2048, 524280, True), (2048, 524281, False), (2, 1 << 29, False),
                        (1 << 15, (1 << 15) + 1, False), ((1 << 29) + 1, 2, False), (2, 1, False), (1, 2, False)):
         p, _ = W.stationary_drop(8, 8, R=2)
         p.update(nx=nx, ny=ny, storage=storage)
