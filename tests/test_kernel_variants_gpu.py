@@ -119,6 +119,12 @@ def smallest_grids():
     yield "walls_3x2", p, W.perturbed(p, f, seed=13)
     p, f = W.convected_drop(2, 3, R=0.6)
     yield "prescribed_2x3", p, f
+    # density ratio 10 with gravity (the rising bubble's parameters at R = 8) on the smallest grids
+    pb, _ = W.rising_bubble(8.0)
+    for nx, ny, walls in ((2, 4, True), (3, 2, True), (2, 2, False)):
+        q = dict(pb, nx=nx, ny=ny, walls=walls)
+        _, g0 = W.stationary_drop(nx, ny, R=0.6)
+        yield f"density_ratio_{'walls' if walls else 'periodic'}_{nx}x{ny}", q, W.perturbed(q, g0, seed=14 + nx + ny)
 
 
 @pytest.mark.parametrize("kernel", ["tile", "pipelined"])
@@ -166,3 +172,35 @@ def test_smallest_grids_16bit_kernels_agree(torch, storage):
         assert g.status == lbm.LBM_OK, name
         assert abs(g.total("phi") - t0) <= 1e-2 * abs(t0), name
         g.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_smallest_grids_in_a_batch_equal_alone(torch, storage):
+    """The smallest grids as members of one batch (one launch per group and step, both batch
+    kernels): every member equals the lattice stepped alone, bit for bit."""
+    cases = [(dict(p, storage=storage), f) for _, p, f in smallest_grids()]
+    ref = []
+    for p, f in cases:
+        g = lbm.Lattice(p)
+        g.init(**f)
+        g.step(20)
+        torch.cuda.synchronize()
+        ref.append(g.state())
+        g.close()
+    for kernel in ("tile", "pipelined"):
+        stream = torch.cuda.Stream()
+        lats = []
+        for p, f in cases:
+            g = lbm.Lattice(p, stream=stream)
+            g.init(**f)
+            lats.append(g)
+        b = lbm.Batch(lats, stream)
+        b.kernel = kernel
+        b.step(20)
+        torch.cuda.synchronize()
+        for k, g in enumerate(lats):
+            assert g.status == lbm.LBM_OK, (kernel, k)
+            assert g.state() == ref[k], (kernel, k)
+        b.close()
+        for g in lats:
+            g.close()
