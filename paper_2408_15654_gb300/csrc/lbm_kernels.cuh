@@ -1816,15 +1816,14 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
     // local density (the equilibrium is taken without the mass-flux terms, S = 0)
     const double rho = p.var_rho ? (double)p.rhoB + (phi - (double)p.phiB) * (double)p.drho : (double)p.rho;
     const double uu = ux * ux + uy * uy;
+    // FP32 storage takes the equilibria in FP32, the precision it stores them in (FP64 arithmetic
+    // is slow on this GPU); 16-bit storage rounds them from FP64 through FP32 to 16 bits
+    const float phf = (float)phi, psf = (float)psi, uxf = (float)ux, uyf = (float)uy;
+    const float rhf = (float)rho, uuf3 = (float)uu * (1.f / 3.f), P3f = 3.f * (float)P_;
     P* fg = static_cast<P*>(a.dst);
     Hv* hp = reinterpret_cast<Hv*>(fg + (size_t)kPairs * p.plane);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const double cu = cx(i) * ux + cy(i) * uy;
-        const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
-        const double feq = w * phi * (1.0 + 3.0 * cu);
-        const double geq = w * psi * (1.0 + 3.0 * cu);
-        const double heq = w * (3.0 * P_ + 3.0 * rho * cu + 4.5 * rho * (cu * cu - uu / 3.0));
         // The first pull at x for direction i reads plane i at x - c_i: there, and at every
         // periodic image of that position in the ghost frame, store this cell's equilibrium value.
         // Across a wall x - c_i is in the wall's ghost row, which holds this cell's bounce-back
@@ -1838,21 +1837,32 @@ __global__ void init_kernel(const __grid_constant__ InitArgs a) {
             sy = (sy + p.ny) % p.ny;
         }
         P vfg;
-        if constexpr (!T::kPair16)
-            vfg = make_float2((float)feq, (float)geq);
-        else
-            vfg = pack2<P>(make_float2((float)((feq / w - p.phi_ref) * T::SF), (float)(geq / w * T::SG)));
         Hv vh{};
-        if (i > 0 && a.flow) {
-            if constexpr (!T::kH16) {
-                vh = (Hv)heq;
-            } else {
-                // stored relative to the storing cell's velocity, as the step will read it back:
-                // the source cell for a plain link, this cell (slot opp(i)) across a wall
-                const size_t so = wall_ghost ? o : (size_t)sy * p.nx + sx;
-                const double sux = (float)a.ux[so], suy = (float)a.uy[so];
-                const double vel = 3.0 * rho * (cx(enc) * sux + cy(enc) * suy);
-                vh = pack1<Hv>((float)((heq / w - vel) * T::SH));
+        if constexpr (ST == kFP32) {
+            const float cu = (float)cx(i) * uxf + (float)cy(i) * uyf;  // sums of +-ux, +-uy: exact
+            const float w = (float)wgt_d(i), b = __fmaf_rn(3.f, cu, 1.f);
+            vfg = make_float2(w * phf * b, w * psf * b);
+            // w (3 P + 3 rho c.u + 4.5 rho ((c.u)^2 - u.u/3))
+            if (i > 0 && a.flow)
+                vh = (Hv)(w * __fmaf_rn(3.f * rhf, cu, __fmaf_rn(4.5f * rhf, __fmaf_rn(cu, cu, -uuf3), P3f)));
+        } else {
+            const double cu = cx(i) * ux + cy(i) * uy;
+            const double w = wgt_d(i);
+            const double feq = w * phi * (1.0 + 3.0 * cu);
+            const double geq = w * psi * (1.0 + 3.0 * cu);
+            const double heq = w * (3.0 * P_ + 3.0 * rho * cu + 4.5 * rho * (cu * cu - uu / 3.0));
+            vfg = pack2<P>(make_float2((float)((feq / w - p.phi_ref) * T::SF), (float)(geq / w * T::SG)));
+            if (i > 0 && a.flow) {
+                if constexpr (!T::kH16) {
+                    vh = (Hv)heq;
+                } else {
+                    // stored relative to the storing cell's velocity, as the step will read it
+                    // back: the source cell for a plain link, this cell (slot opp(i)) across a wall
+                    const size_t so = wall_ghost ? o : (size_t)sy * p.nx + sx;
+                    const double sux = (float)a.ux[so], suy = (float)a.uy[so];
+                    const double vel = 3.0 * rho * (cx(enc) * sux + cy(enc) * suy);
+                    vh = pack1<Hv>((float)((heq / w - vel) * T::SH));
+                }
             }
         }
         auto at = [&](int c, int r) {
