@@ -61,7 +61,9 @@ extern "C" {
                                      and the flow parameters are unused (the convection test of
                                      Sec. 4)                                                   */
 
-#define LBM_MEM_HOST 0      /* pointer arguments are host memory (pageable or pinned)        */
+#define LBM_MEM_HOST 0      /* pointer arguments are host memory (pageable or pinned; pinned
+                               arrays are read and written by the kernels directly, pageable
+                               ones are staged in device memory)                              */
 #define LBM_MEM_DEVICE 1    /* pointer arguments are device memory on the handle's device    */
 
 #define LBM_PHI 1u          /* moment masks for lbm_get_moments                              */

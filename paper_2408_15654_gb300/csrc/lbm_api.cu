@@ -313,6 +313,19 @@ int launch_reduce(int st, const void* pops, int lane, bool pulled, int nx, int n
     return LBM_OK;
 }
 
+// The address by which a kernel reaches host memory p, or nullptr: page-locked host memory
+// (cudaHostAlloc, cudaHostRegister) is mapped into the device's address space, so the
+// initialisation and moments kernels read and write it directly over the CPU-GPU link instead of
+// through a staging copy.  Pageable memory returns nullptr and is staged.
+const void* mapped_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the error of an unknown pointer
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int read_status(lbm_handle* h, unsigned* st) {
     LBM_CUDA(cudaMemcpyAsync(st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(cudaStreamSynchronize(h->stream));
@@ -518,11 +531,19 @@ int lbm_init_fields(lbm_handle* h, const double* phi, const double* psi, const d
     const double* d[5] = {phi, psi, ux, uy, P};
     const int tgt = 0;
     if (mem == LBM_MEM_HOST) {
-        // stage through the buffer that becomes dead (sized for 5 doubles per cell, see layout_of)
-        double* stage = reinterpret_cast<double*>(h->pops[tgt ^ 1]);
-        for (int k = 0; k < 5; ++k) {
-            LBM_CUDA(cudaMemcpyAsync(stage + k * n, d[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-            d[k] = stage + k * n;
+        const void* m[5];
+        bool mapped = true;
+        for (int k = 0; k < 5; ++k) mapped = mapped && (m[k] = mapped_host(d[k])) != nullptr;
+        if (mapped) {
+            // page-locked: the initialisation kernel reads the fields where they are
+            for (int k = 0; k < 5; ++k) d[k] = static_cast<const double*>(m[k]);
+        } else {
+            // stage through the buffer that becomes dead (sized for 5 doubles per cell, see layout_of)
+            double* stage = reinterpret_cast<double*>(h->pops[tgt ^ 1]);
+            for (int k = 0; k < 5; ++k) {
+                LBM_CUDA(cudaMemcpyAsync(stage + k * n, d[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+                d[k] = stage + k * n;
+            }
         }
     }
     LBM_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
@@ -585,14 +606,24 @@ int lbm_get_moments(lbm_handle* h, unsigned mask, double* const out[5], int mem)
     const size_t n = (size_t)h->prm.nx * h->prm.ny;
     double* dev_out[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     double* stage = reinterpret_cast<double*>(h->pops[h->cur ^ 1]);
+    bool mapped = mem == LBM_MEM_HOST;  // every requested output page-locked: written where it is
     for (int k = 0; k < 5; ++k) {
         if (!(mask & (1u << k))) continue;
         if (!out[k]) return fail(LBM_EINVAL, "out[%d] is NULL but requested by mask", k);
-        dev_out[k] = mem == LBM_MEM_DEVICE ? out[k] : stage + k * n;
+        if (mem == LBM_MEM_HOST) {
+            void* m = const_cast<void*>(mapped_host(out[k]));
+            mapped = mapped && m != nullptr;
+            dev_out[k] = m ? static_cast<double*>(m) : stage + k * n;
+        } else {
+            dev_out[k] = out[k];
+        }
     }
+    if (mem == LBM_MEM_HOST && !mapped)
+        for (int k = 0; k < 5; ++k)
+            if (mask & (1u << k)) dev_out[k] = stage + k * n;
     int rc = launch_step(h, lbm::kMoments, dev_out);
     if (rc) return rc;
-    if (mem == LBM_MEM_HOST)
+    if (mem == LBM_MEM_HOST && !mapped)
         for (int k = 0; k < 5; ++k)
             if (mask & (1u << k))
                 LBM_CUDA(cudaMemcpyAsync(out[k], dev_out[k], n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
